@@ -1,0 +1,24 @@
+/* ora_internal.h -- helpers shared by the oracle's own source files only. */
+#ifndef LGT_ORA_INTERNAL_H
+#define LGT_ORA_INTERNAL_H
+#include "oracle.h"
+
+/* Philox counter word 3: which field a random number belongs to */
+enum { ORA_FIELD_MOMENTA = 1, ORA_FIELD_XI = 2, ORA_FIELD_LINKS = 3, ORA_FIELD_METROPOLIS = 4,
+       ORA_FIELD_SOURCE = 5 };
+
+void ora_coords(const int d[4], long s, int x[4]);
+long ora_index(const int d[4], const int x[4]);
+long ora_neighbour(const int d[4], long s, int mu, int dir);
+double ora_fermion_bc(const int d[4], long s, int mu, int dir);
+
+void su3_mul(const ocplx *A, const ocplx *B, ocplx *C);
+void su3_dag(const ocplx *A, ocplx *B);
+void su3_from_coeffs(const double *h, ocplx *H);
+void su3_expi(const ocplx *H, double eps, ocplx *out);
+
+/* inner products over sites whose parity bit is in mask */
+ocplx ora_dot(const int d[4], const ocplx *a, const ocplx *b, int mask);
+double ora_norm2(const int d[4], const ocplx *a, int mask);
+
+#endif

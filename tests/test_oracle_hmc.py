@@ -1,0 +1,89 @@
+"""HMC pins of the oracle: reversibility, Delta H ~ dt^2 (the validation of the
+paper's dynamical test, Sec. III B), energy conservation and heatbath identities."""
+import numpy as np
+import pytest
+
+from paper_2602_20516_b300 import synth
+from tests import helpers as H
+
+D4 = (4, 4, 4, 4)
+
+
+def _setup(seed=1, alpha=0.3):
+    U = synth.random_links(D4, alpha, seed)
+    mom = synth.gaussian_momenta(D4, seed + 100)
+    return U, mom
+
+
+@pytest.mark.parametrize("integrator,eo", [("leapfrog", False), ("omelyan", True)])
+def test_reversibility(ora, integrator, eo):
+    U, mom = _setup()
+    phi = synth.gaussian_spinor(D4, 3, parity_mask=1 if eo else 3)
+    p = ora.hmc_params(5.7, 0.15, eo=eo, integrator=integrator, n_steps=5, tau=0.5,
+                       tol_md=1e-14)
+    U1, m1, _ = ora.md_integrate(D4, U, mom, phi, p)
+    U2, m2, _ = ora.md_integrate(D4, U1, -m1, phi, p)
+    assert H.rel(U2, U) < 1e-11
+    assert H.rel(-m2, mom) < 1e-10
+
+
+def _dH(U, mom, phi, p):
+    H0 = ora_energy(U, mom, phi, p)
+    U1, m1, _ = ORA.md_integrate(D4, U, mom, phi, p)
+    return ora_energy(U1, m1, phi, p) - H0
+
+
+ORA = None
+
+
+def ora_energy(U, mom, phi, p):
+    S = ORA.gauge_action(D4, U, p.beta) + ORA.momentum_energy(D4, mom)
+    if p.fermions:
+        S += ORA.pf_action(D4, U, p.kappa, phi, eo=bool(p.eo), tol=1e-14)[0]
+    return S
+
+
+@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
+def test_delta_h_scales_as_dt_squared(ora, integrator):
+    global ORA
+    ORA = ora
+    U, mom = _setup(seed=2)
+    phi = synth.gaussian_spinor(D4, 4)
+    dh = []
+    ns = [8, 16, 32]
+    for n in ns:
+        p = ora.hmc_params(5.7, 0.15, integrator=integrator, n_steps=n, tau=1.0, tol_md=1e-14)
+        dh.append(abs(_dH(U, mom, phi, p)))
+    slope = np.polyfit(np.log(1.0 / np.array(ns)), np.log(dh), 1)[0]
+    assert abs(slope - 2) < 0.2, (dh, slope)
+
+
+def test_pure_gauge_energy_conservation(ora):
+    global ORA
+    ORA = ora
+    U, mom = _setup(seed=5)
+    phi = np.zeros((256, 4, 3), np.complex128)
+    p1 = ora.hmc_params(5.7, 0.0, fermions=False, n_steps=20, tau=1.0)
+    p2 = ora.hmc_params(5.7, 0.0, fermions=False, n_steps=40, tau=1.0)
+    d1, d2 = abs(_dH(U, mom, phi, p1)), abs(_dH(U, mom, phi, p2))
+    # halving the step divides Delta H by ~4 for a second-order integrator
+    assert 3.2 < d1 / d2 < 4.8
+
+
+def test_trajectory_heatbath_and_metropolis(ora):
+    U = synth.random_links(D4, 0.3, 7)
+    p = ora.hmc_params(5.7, 0.15, n_steps=10, tau=1.0, tol_md=1e-12, tol_action=1e-12)
+    U1, r = ora.hmc_trajectory(D4, U, p, 1, 0)
+    # the pseudofermion heatbath phi = D^+ xi gives S_f(old) = xi^+ xi exactly; check it
+    # against an independent action evaluation on the starting field
+    xi = ora.gaussian_spinor(D4, 1, 0, ora.FIELD_XI, 3)
+    phi = ora.dirac(D4, U, 0.15, xi, dagger=True)
+    S, _ = ora.pf_action(D4, U, 0.15, phi, tol=1e-13)
+    assert abs(S - r["Sf_old"]) / S < 1e-11
+    assert abs(r["K_old"] - 0.5 * (ora.gaussian_momenta(D4, 1, 0) ** 2).sum()) < 1e-9
+    assert r["force_evals"] == 11
+    u = ora.uniform(1, 0, 0, 0, ora.FIELD_METROPOLIS)
+    assert r["accepted"] == int(u < np.exp(-r["dH"]))
+    if not r["accepted"]:
+        assert H.rel(U1, U) < 1e-14
+    assert np.abs(U1 @ np.conj(np.swapaxes(U1, -1, -2)) - np.eye(3)).max() < 1e-14

@@ -1,0 +1,368 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms, library routines, algebraic identities,
+dense brute force on tiny lattices, finite differences and symmetries.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from paper_2602_20516_b300 import synth
+from tests import helpers as H
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ random numbers
+def test_philox_known_answers(ora):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = ora.philox4x32_10(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_gaussian_moments(ora):
+    g = np.array([ora.gauss_pair(7, i, 0, 0, 1) for i in range(20000)]).ravel()
+    assert abs(g.mean()) < 0.03 and abs(g.var() - 1) < 0.03
+    # fourth moment of N(0,1) is 3
+    assert abs((g ** 4).mean() - 3) < 0.15
+
+
+# ------------------------------------------------------------------ small matrices
+def test_gamma_algebra(ora):
+    g = [ora.gamma(m) for m in range(4)]
+    g5 = ora.gamma(4)
+    for m in range(4):
+        assert np.allclose(g[m], g[m].conj().T)
+        for n in range(4):
+            assert np.allclose(g[m] @ g[n] + g[n] @ g[m], 2 * (m == n) * np.eye(4))
+        assert np.allclose(g5 @ g[m] + g[m] @ g5, 0)
+    assert np.allclose(g5, np.diag([1, 1, -1, -1]))
+
+
+def test_gellmann(ora):
+    T = [ora.gellmann_T(a) for a in range(8)]
+    for a in range(8):
+        assert np.allclose(T[a], T[a].conj().T) and abs(np.trace(T[a])) < 1e-15
+        for b in range(8):
+            assert abs(np.trace(T[a] @ T[b]) - 0.5 * (a == b)) < 1e-15
+    # structure constants f_123 = 1, f_458 = sqrt(3)/2
+    assert np.allclose(T[0] @ T[1] - T[1] @ T[0], 1j * T[2])
+    assert np.allclose(T[3] @ T[4] - T[4] @ T[3], 1j * (0.5 * T[2] + np.sqrt(3) / 2 * T[7]))
+
+
+@pytest.mark.parametrize("n", [3, 6])
+def test_expm_matches_library(ora, n):
+    rng = np.random.default_rng(n)
+    for scale in (1e-3, 0.5, 3.0):
+        A = scale * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+        assert H.rel(ora.expm(A), scipy.linalg.expm(A)) < 1e-13
+    assert np.allclose(ora.expm(np.zeros((3, 3))), np.eye(3), atol=0)
+    th = np.array([0.3, -1.1, 0.8])
+    assert np.allclose(ora.expm(np.diag(1j * th)), np.diag(np.exp(1j * th)), atol=1e-15)
+
+
+# ------------------------------------------------------------------ seeded links
+def test_random_links_distribution(ora):
+    d = (8, 8, 8, 8)
+    U = ora.random_links(d, 11, 0.3)
+    I3 = np.eye(3)
+    assert np.abs(U @ np.conj(np.swapaxes(U, -1, -2)) - I3).max() < 1e-14
+    assert np.abs(np.linalg.det(U) - 1).max() < 1e-14
+    # independent links from an Ad-invariant law: <plaq> = c^4, c = E[Re tr U / 3],
+    # with c estimated from an independent generator (numpy + eigh)
+    W = synth.random_links((4, 4, 4, 4), 0.3, 5).reshape(-1, 3, 3)
+    c = np.real(np.trace(W, axis1=-2, axis2=-1)).mean() / 3
+    assert abs(ora.plaquette(d, U) - c ** 4) < 0.01
+
+
+# ------------------------------------------------------------------ Wilson-Dirac operator
+@pytest.mark.parametrize("n", [(0, 0, 0, 0), (1, 0, 2, 1), (3, 1, 1, 0)])
+def test_free_field_plane_wave(ora, n):
+    d = (4, 4, 4, 4)
+    kappa = 0.15
+    U = np.broadcast_to(np.eye(3), (256, 4, 3, 3)).copy()
+    u = np.random.default_rng(1).standard_normal((4, 3)) + 0j
+    psi, p = H.plane_wave(d, n, u)
+    g = [ora.gamma(m) for m in range(4)]
+    # D e^{ipx} u = [(1 - 2 kappa sum cos p) + 2 i kappa sum gamma sin p] e^{ipx} u
+    M = (1 - 2 * kappa * np.cos(p).sum()) * np.eye(4) + 2j * kappa * sum(
+        g[m] * np.sin(p[m]) for m in range(4))
+    expect = np.einsum("ab,xbc->xac", M, psi)
+    assert H.rel(ora.dirac(d, U, kappa, psi), expect) < 1e-14
+
+
+def test_gamma5_hermiticity_and_adjoint(ora):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 3)
+    kappa = 0.15
+    phi = synth.gaussian_spinor(d, 4)
+    psi = synth.gaussian_spinor(d, 5)
+    g5 = np.diag([1, 1, -1, -1])
+    g5psi = np.einsum("ab,xbc->xac", g5, psi)
+    lhs = np.einsum("ab,xbc->xac", g5, ora.dirac(d, U, kappa, g5psi))
+    assert H.rel(lhs, ora.dirac(d, U, kappa, psi, dagger=True)) < 1e-14
+    a = np.vdot(phi, ora.dirac(d, U, kappa, psi))
+    b = np.vdot(ora.dirac(d, U, kappa, phi, dagger=True), psi)
+    assert abs(a - b) / abs(a) < 1e-13
+
+
+def test_gauge_covariance_of_D(ora):
+    d = (4, 4, 4, 4)
+    V = 256
+    U = synth.random_links(d, 0.5, 6)
+    g = synth.random_su3(V, 7)
+    psi = synth.gaussian_spinor(d, 8)
+    Ug = H.gauge_transform_links(d, U, g)
+    lhs = ora.dirac(d, Ug, 0.13, H.gauge_transform_spinor(psi, g))
+    rhs = H.gauge_transform_spinor(ora.dirac(d, U, 0.13, psi), g)
+    assert H.rel(lhs, rhs) < 1e-14
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 2, 2)])
+def test_even_odd_determinant_and_schur(ora, dims):
+    V = synth.volume(dims)
+    U = synth.random_links(dims, 0.6, 9)
+    kappa = 0.2
+    Dm = H.dense_operator(lambda e: ora.dirac(dims, U, kappa, e), V)
+    even = np.where(synth.parity(dims) == 0)[0]
+    Dh = H.dense_operator(lambda e: ora.dhat(dims, U, kappa, e), V, sites=even)
+    Dh = Dh.reshape(V, 12, -1)[even].reshape(len(even) * 12, -1)
+    s1, l1 = np.linalg.slogdet(Dm)
+    s2, l2 = np.linalg.slogdet(Dh)
+    assert abs(l1 - l2) < 1e-10 and abs(s1 - s2) < 1e-10
+    # full solve equals the even-odd reconstruction
+    b = synth.gaussian_spinor(dims, 10)
+    x_full = np.linalg.solve(Dm, b.ravel()).reshape(V, 4, 3)
+    be = b.copy(); be[synth.parity(dims) == 1] = 0
+    bo = b - be
+    rhs = be + kappa * ora.hop(dims, U, bo, out_mask=1)
+    xe = np.linalg.solve(Dh, rhs[even].ravel()).reshape(-1, 4, 3)
+    x = np.zeros_like(b); x[even] = xe
+    x = x + bo + kappa * ora.hop(dims, U, x, out_mask=2)
+    assert H.rel(x, x_full) < 1e-12
+    # Dhat^+ = gamma5 Dhat gamma5
+    g5 = np.diag([1, 1, -1, -1])
+    psi = synth.gaussian_spinor(dims, 11, parity_mask=1)
+    lhs = np.einsum("ab,xbc->xac", g5, ora.dhat(dims, U, kappa, np.einsum("ab,xbc->xac", g5, psi)))
+    assert H.rel(lhs, ora.dhat(dims, U, kappa, psi, dagger=True)) < 1e-14
+
+
+# ------------------------------------------------------------------ solver and S_F
+@pytest.mark.parametrize("eo", [False, True])
+def test_cg_true_residual(ora, eo):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 12)
+    b = synth.gaussian_spinor(d, 13, parity_mask=1 if eo else 3)
+    x, it, res = ora.cg(d, U, 0.15, b, eo=eo, tol=1e-12)
+    assert it > 0 and res <= 1e-12
+    M = (lambda v, dag=False: ora.dhat(d, U, 0.15, v, dag)) if eo else \
+        (lambda v, dag=False: ora.dirac(d, U, 0.15, v, dag))
+    assert H.rel(M(M(x), True), b) <= 1.5e-12
+
+
+def test_pf_action_free_field_closed_form(ora):
+    d = (4, 4, 4, 6)
+    kappa = 0.12
+    V = synth.volume(d)
+    U = np.broadcast_to(np.eye(3), (V, 4, 3, 3)).copy()
+    phi = synth.gaussian_spinor(d, 14)
+    S, _ = ora.pf_action(d, U, kappa, phi, tol=1e-13)
+    # unitary DFT with antiperiodic time: phi~(p) = V^-1/2 sum_x e^{-ipx} phi(x)
+    c = synth.coords(d)
+    f = phi * np.exp(-1j * np.pi * c[:, 3] / d[3])[:, None, None]
+    f = f.reshape(d[3], d[2], d[1], d[0], 12)
+    ft = np.fft.fftn(f, axes=(0, 1, 2, 3), norm="ortho")
+    k = [2 * np.pi * np.fft.fftfreq(L) for L in (d[3], d[2], d[1], d[0])]
+    p3, p2, p1, p0 = np.meshgrid(k[0] + np.pi / d[3], k[1], k[2], k[3], indexing="ij")
+    cs = np.cos(p0) + np.cos(p1) + np.cos(p2) + np.cos(p3)
+    s2 = np.sin(p0) ** 2 + np.sin(p1) ** 2 + np.sin(p2) ** 2 + np.sin(p3) ** 2
+    lam = (1 - 2 * kappa * cs) ** 2 + 4 * kappa ** 2 * s2
+    S_exact = (np.abs(ft) ** 2 / lam[..., None]).sum()
+    assert abs(S - S_exact) / S_exact < 1e-12
+
+
+@pytest.mark.parametrize("eo", [False, True])
+def test_pf_action_dense_and_heatbath(ora, eo):
+    d = (2, 2, 2, 4)
+    V = synth.volume(d)
+    U = synth.random_links(d, 0.5, 15)
+    kappa = 0.16
+    mask = 1 if eo else 3
+    phi = synth.gaussian_spinor(d, 16, parity_mask=mask)
+    if eo:
+        even = np.where(synth.parity(d) == 0)[0]
+        M = H.dense_operator(lambda e: ora.dhat(d, U, kappa, e), V, sites=even)
+        M = M.reshape(V, 12, -1)[even].reshape(len(even) * 12, -1)
+        pv = phi[even].ravel()
+    else:
+        M = H.dense_operator(lambda e: ora.dirac(d, U, kappa, e), V)
+        pv = phi.ravel()
+    S_dense = np.real(np.vdot(pv, np.linalg.solve(M.conj().T @ M, pv)))
+    S, _ = ora.pf_action(d, U, kappa, phi, eo=eo, tol=1e-13)
+    assert abs(S - S_dense) / S_dense < 1e-12
+    # heatbath identity: phi = M^+ xi gives S_f = xi^+ xi
+    xi = synth.gaussian_spinor(d, 17, parity_mask=mask)
+    ph = ora.dhat(d, U, kappa, xi, True) if eo else ora.dirac(d, U, kappa, xi, True)
+    S2, _ = ora.pf_action(d, U, kappa, ph, eo=eo, tol=1e-13)
+    assert abs(S2 - np.vdot(xi, xi).real) / S2 < 1e-12
+
+
+def test_gauge_invariance_of_actions(ora):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 18)
+    g = synth.random_su3(256, 19)
+    Ug = H.gauge_transform_links(d, U, g)
+    assert abs(ora.gauge_action(d, U, 5.7) - ora.gauge_action(d, Ug, 5.7)) < 1e-10
+    for eo in (False, True):
+        phi = synth.gaussian_spinor(d, 20, parity_mask=1 if eo else 3)
+        S1, _ = ora.pf_action(d, U, 0.15, phi, eo=eo, tol=1e-13)
+        S2, _ = ora.pf_action(d, Ug, 0.15, H.gauge_transform_spinor(phi, g), eo=eo, tol=1e-13)
+        assert abs(S1 - S2) / abs(S1) < 1e-12
+    # S_G(U = 1) = 0
+    one = np.broadcast_to(np.eye(3), (256, 4, 3, 3)).copy()
+    assert ora.gauge_action(d, one, 5.7) == 0.0
+
+
+# ------------------------------------------------------------------ forces
+LINKS = [(0, 0), (37, 1), (100, 2), (255, 3), (3, 3), (64 + 5, 3)]
+
+
+def test_gauge_force_finite_difference(ora):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 21)
+    beta = 5.7
+    F = ora.gauge_force(d, U, beta)
+    h = 1e-5
+    for (s, mu) in LINKS:
+        for a in (0, 3, 7):
+            Sp = ora.gauge_action(d, H.lie_perturb(U, s, mu, a, h), beta)
+            Sm = ora.gauge_action(d, H.lie_perturb(U, s, mu, a, -h), beta)
+            fd = (Sp - Sm) / (2 * h)
+            assert abs(fd - F[s, mu, a]) < 1e-6 * max(1.0, abs(F[s, mu, a]))
+
+
+@pytest.mark.parametrize("eo", [False, True])
+def test_fermion_force_finite_difference(ora, eo):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 22)
+    kappa = 0.15
+    phi = synth.gaussian_spinor(d, 23, parity_mask=1 if eo else 3)
+    F, _ = ora.pf_force(d, U, kappa, phi, eo=eo, tol=1e-14)
+    h = 1e-5
+    for (s, mu) in LINKS:
+        for a in (1, 4, 7):
+            Sp, _ = ora.pf_action(d, H.lie_perturb(U, s, mu, a, h), kappa, phi, eo=eo, tol=1e-14)
+            Sm, _ = ora.pf_action(d, H.lie_perturb(U, s, mu, a, -h), kappa, phi, eo=eo, tol=1e-14)
+            fd = (Sp - Sm) / (2 * h)
+            assert abs(fd - F[s, mu, a]) < 2e-6 * max(1.0, abs(F[s, mu, a]))
+
+
+def test_force_covariance(ora):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 24)
+    g = synth.random_su3(256, 25)
+    Ug = H.gauge_transform_links(d, U, g)
+    phi = synth.gaussian_spinor(d, 26)
+    F = ora.gauge_force(d, U, 5.7) + ora.pf_force(d, U, 0.15, phi, tol=1e-13)[0]
+    Fg = ora.gauge_force(d, Ug, 5.7) + ora.pf_force(d, Ug, 0.15, H.gauge_transform_spinor(phi, g), tol=1e-13)[0]
+    assert H.rel(Fg, H.gauge_transform_adjoint(F, g)) < 1e-11
+
+
+def test_real_component_gradients(ora):
+    """G = dS/dReU + i dS/dImU (Eq. S2.11) by finite differences on matrix entries,
+    and F_a = Re tr(G^+ i T^a U) reproduces the Lie force."""
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 27)
+    phi = synth.gaussian_spinor(d, 28)
+    # S_f is a global sum of ~1e3: its rounding (~1e-11) over 2h sets the step
+    beta, kappa, h = 5.7, 0.15, 3e-5
+    Gg = ora.gauge_action_grad(d, U, beta)
+    Gf, _ = ora.pf_action_grad(d, U, kappa, phi, tol=1e-14)
+    for (s, mu) in LINKS[:3]:
+        for (i, j) in ((0, 0), (1, 2), (2, 1)):
+            for part, unit in (("re", 1.0), ("im", 1j)):
+                Up = U.copy(); Up[s, mu, i, j] += h * unit
+                Um = U.copy(); Um[s, mu, i, j] -= h * unit
+                fd_g = (ora.gauge_action(d, Up, beta) - ora.gauge_action(d, Um, beta)) / (2 * h)
+                fd_f = (ora.pf_action(d, Up, kappa, phi, tol=1e-14)[0]
+                        - ora.pf_action(d, Um, kappa, phi, tol=1e-14)[0]) / (2 * h)
+                ga = Gg[s, mu, i, j].real if part == "re" else Gg[s, mu, i, j].imag
+                fa = Gf[s, mu, i, j].real if part == "re" else Gf[s, mu, i, j].imag
+                assert abs(fd_g - ga) < 2e-6 * max(1, abs(ga))
+                assert abs(fd_f - fa) < 3e-6 * max(1, abs(fa))
+    assert H.rel(ora.grad_to_force(d, U, Gg), ora.gauge_force(d, U, beta)) < 1e-13
+    assert H.rel(ora.grad_to_force(d, U, Gf), ora.pf_force(d, U, kappa, phi, tol=1e-14)[0]) < 1e-12
+
+
+# ------------------------------------------------------------------ link update
+def test_link_update_unitarity_and_inverse(ora):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 29)
+    mom = synth.gaussian_momenta(d, 30)
+    U1 = ora.update_links(d, U, mom, 0.3)
+    I3 = np.eye(3)
+    assert np.abs(U1 @ np.conj(np.swapaxes(U1, -1, -2)) - I3).max() < 1e-14
+    assert np.abs(np.linalg.det(U1) - 1).max() < 1e-14
+    assert H.rel(ora.update_links(d, U1, mom, -0.3), U) < 1e-14
+    # independent route: scipy expm of i eps Pi
+    P = np.einsum("xma,aij->xmij", mom, H.GELLMANN_T)
+    s, mu = 77, 2
+    assert H.rel(U1[s, mu], scipy.linalg.expm(0.3j * P[s, mu]) @ U[s, mu]) < 1e-14
+
+
+def test_reunitarise(ora):
+    d = (2, 2, 2, 2)
+    U = synth.random_links(d, 0.5, 31)
+    assert H.rel(ora.reunitarise(d, U), U) < 1e-15
+    W = U + 1e-6 * (np.random.default_rng(0).standard_normal(U.shape))
+    R = ora.reunitarise(d, W)
+    assert np.abs(R @ np.conj(np.swapaxes(R, -1, -2)) - np.eye(3)).max() < 1e-15
+    assert np.abs(np.linalg.det(R) - 1).max() < 1e-15
+
+
+# ------------------------------------------------------------------ stout smearing
+def test_stout_identity_at_rho_zero(ora):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 32)
+    G = synth.random_links(d, 1.0, 33)  # any complex matrices
+    assert H.rel(ora.stout_forward(d, U, 0.0), U) < 1e-15
+    assert H.rel(ora.stout_backward(d, U, 0.0, G), G) < 1e-14
+
+
+def test_stout_unitary_and_covariant(ora):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 34)
+    S = ora.stout_forward(d, U, 0.1)
+    assert np.abs(S @ np.conj(np.swapaxes(S, -1, -2)) - np.eye(3)).max() < 1e-14
+    assert np.abs(np.linalg.det(S) - 1).max() < 1e-14
+    g = synth.random_su3(256, 35)
+    lhs = ora.stout_forward(d, H.gauge_transform_links(d, U, g), 0.1)
+    assert H.rel(lhs, H.gauge_transform_links(d, S, g)) < 1e-13
+
+
+def test_stout_backward_finite_difference(ora):
+    """L(U) = Re tr sum A^+ smear(U): its gradient is the backward of G' = A."""
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 36)
+    rho = 0.1
+    A = synth.random_links(d, 1.0, 37) + 0.3 * synth.random_links(d, 1.0, 38)
+
+    def L(W):
+        return np.real(np.vdot(A, ora.stout_forward(d, W, rho)))
+
+    G = ora.stout_backward(d, U, rho, A)
+    h = 1e-4  # central-difference error is smallest here (truncation ~ rounding)
+    for (s, mu) in LINKS[:4]:
+        for (i, j) in ((0, 1), (2, 2)):
+            for unit, part in ((1.0, np.real), (1j, np.imag)):
+                Up = U.copy(); Up[s, mu, i, j] += h * unit
+                Um = U.copy(); Um[s, mu, i, j] -= h * unit
+                fd = (L(Up) - L(Um)) / (2 * h)
+                assert abs(fd - part(G[s, mu, i, j])) < 2e-8 * max(1, abs(fd))
