@@ -1,0 +1,236 @@
+/*
+ * lgt.h -- C ABI of liblgt.so, the sm_103a (B300) implementation of the HMC hot
+ * path of "Lattice Gauge Theory via LLVM-Level Automatic Differentiation"
+ * (arXiv:2602.20516): the SU(3) plaquette gauge action and the two-flavour
+ * Wilson pseudofermion action S_f = phi^+ (D^+D)^{-1} phi (Eq. S3.1), their
+ * molecular-dynamics forces (Eq. 9 / Eq. S2.8 with the fermion variation of
+ * Eq. S3.12), conjugate gradient on D^+D (Eq. S3.4), the left link update
+ * U <- exp(i eps P) U (Eq. 6 / Eq. S2.1), the momentum update (Eq. S2.2) and
+ * HMC trajectories.
+ *
+ * Conventions (the paper prints none of them; one reading each):
+ *   - site s = x0 + L0*(x1 + L1*(x2 + L2*x3)); mu = 3 is time; every extent
+ *     must be even; parity = (x0+x1+x2+x3) mod 2, even = 0.
+ *   - T^a = lambda^a / 2; momenta P = sum_a pi_a T^a are Hermitian and
+ *     traceless; a force F_a is d/de S(exp(i e T^a) U_mu(x)) at e = 0, and the
+ *     MD kick is pi_a <- pi_a - eps F_a.
+ *   - D = 1 - kappa H with
+ *     (H psi)(x) = sum_mu [ b (1 - g_mu) U_mu(x) psi(x+mu) + b (1 + g_mu) U_mu(x-mu)^+ psi(x-mu) ],
+ *     b = -1 on hops that wrap in time (antiperiodic fermions), chiral gammas
+ *     g_k = [[0,-i s_k],[i s_k,0]] (mu = k-1 < 3), g_4 = [[0,1],[1,0]] (mu = 3).
+ *   - Even-odd: Dhat = 1 - kappa^2 H_eo H_oe on even sites, Dhat^+ = g5 Dhat g5.
+ *   - S_G = beta sum_{x, mu<nu} (1 - Re tr U_munu(x) / 3).
+ *   - a real-component gradient ("G form", Eq. S2.11) is dS/dReU + i dS/dImU.
+ *
+ * Device layouts (all buffers below are DEVICE pointers owned by the caller;
+ * Vh = V/2; "half field" = one parity):
+ *   canonical links   complex128 [V][4][3][3]   (interleaved re,im doubles)
+ *   canonical spinor  complex128 [V][4][3]      (spin, colour)
+ *   canonical momenta double [V][4][8]
+ *   FP64 spinor field double2 [parity][12][Vh]  component k = 3*spin + colour;
+ *                     a half field is the [12][Vh] block of one parity
+ *   FP32 spinor field float4  [parity][6][Vh]   float4 k holds components 2k, 2k+1
+ *   momenta / forces  double2 [parity][4 mu][4][Vh]  double2 k holds pi_{2k}, pi_{2k+1}
+ *   G-form gradient   double2 [parity][4 mu][9][Vh]  entry 3*row + col
+ * The handle stores the gauge field as FP64 double2 [parity][4][9][Vh] plus an
+ * FP32 two-row (12-real) copy float4 [parity][4][3][Vh] derived from it.
+ *
+ * Errors: every function returns an lgt_status; nothing aborts, traps or prints.
+ * lgt_last_error() returns a thread-local message for the last failure.
+ * Streams: all work is enqueued on the handle's stream (lgt_set_stream); calls
+ * that return host scalars synchronise that stream before returning.
+ * Thread safety: one handle must not be used by two threads at once.
+ */
+#ifndef LGT_H
+#define LGT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LGT_OK = 0,
+    LGT_EINVAL = 1,   /* bad argument (odd extent, null pointer, unknown enum) */
+    LGT_ENOMEM = 2,   /* allocation failed or over the memory budget */
+    LGT_ENOCONV = 3,  /* solver hit max_iter; stats hold the last true residual */
+    LGT_ENAN = 4,     /* a non-finite residual, action or energy was produced */
+    LGT_ECUDA = 5,    /* a CUDA runtime call or launch failed */
+    LGT_EKERNEL = 6   /* a kernel reported an internal error through its status word */
+} lgt_status;
+
+enum { LGT_FP64 = 0, LGT_MIXED = 1, LGT_FP32 = 2 };      /* precision */
+enum { LGT_EVEN = 0, LGT_ODD = 1, LGT_FULL = 2 };         /* parity selector */
+/* operators of lgt_dslash */
+enum { LGT_OP_HOP = 0,       /* out_p = H_{p,1-p} in_{1-p}, p = out_parity (EVEN|ODD) */
+       LGT_OP_D = 1,         /* out = D in on the full lattice */
+       LGT_OP_DHAT = 2,      /* out_e = Dhat in_e */
+       LGT_OP_DHAT_NORMAL = 3 /* out_e = Dhat^+ Dhat in_e (dagger ignored) */ };
+enum { LGT_LEAPFROG = 0, LGT_OMELYAN2MN = 1 };
+enum { LGT_FORCE_LIE = 0, LGT_GRAD_G = 1 };
+enum { LGT_UPDATE_U = 0, LGT_UPDATE_P = 1 };
+
+typedef struct lgt_lattice *lgt_lattice_t;
+
+/* Device-memory allocator.  alloc returns a device pointer (NULL on failure)
+ * usable on `stream`; free releases it.  A NULL allocator makes the library
+ * use cudaMalloc / cudaFree. */
+typedef struct {
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, void *stream);
+    void *ctx;
+} lgt_allocator;
+
+typedef struct {
+    double beta;      /* gauge coupling of S_G; 0 drops S_G */
+    double kappa;     /* hopping parameter of D */
+    int fermions;     /* 1: include S_f, 0: pure gauge */
+    int even_odd;     /* 1: S_f = phi_e^+ (Dhat^+Dhat)^{-1} phi_e; 0: full lattice */
+    int n_stout;      /* stout levels in front of D (0 .. 4) */
+    double rho;       /* stout parameter */
+} lgt_action_params;
+
+typedef struct {
+    int precision;    /* LGT_FP64 or LGT_MIXED (FP32 inner CG, FP64 reliable updates) */
+    double tol;       /* stop when |b - A x| / |b| <= tol (true residual, FP64) */
+    int max_iter;     /* iteration cap -> LGT_ENOCONV */
+    double delta;     /* mixed: reliable update when |r| < delta * max|r| since the last one */
+    int check_every;  /* iterations enqueued between host checks (0 -> default 16) */
+} lgt_solver_params;
+
+typedef struct {
+    int iters;               /* CG iterations (inner iterations for the mixed solver) */
+    int reliable_updates;    /* FP64 residual replacements */
+    double true_rel_residual;
+    double seconds;          /* host wall time of the call */
+} lgt_solve_stats;
+
+typedef struct {
+    int integrator;          /* LGT_LEAPFROG (PQP) or LGT_OMELYAN2MN */
+    int n_steps;
+    double tau;
+    lgt_solver_params md_solver;      /* solves inside force evaluations */
+    lgt_solver_params action_solver;  /* solve of the final action */
+} lgt_hmc_params;
+
+typedef struct {
+    double dH, Sg_old, Sg_new, Sf_old, Sf_new, K_old, K_new, plaquette;
+    int accepted;
+    int force_evals;
+    lgt_solve_stats total;   /* summed over every solve of the trajectory */
+} lgt_hmc_result;
+
+/* ------------------------------------------------------------------ library */
+/* Thread-local text of the last error (never NULL). */
+const char *lgt_last_error(void);
+/* ABI version (major*100 + minor). */
+int lgt_version(void);
+
+/* ------------------------------------------------------------------ lattice */
+/* Create a lattice of extents dims[0..3] (all even, >= 2) on the current CUDA
+ * device.  Allocates the gauge field and workspace through `alloc` (NULL:
+ * cudaMalloc).  `stream` is a cudaStream_t (NULL: legacy default stream).
+ * Gauge field starts as the unit field. */
+int lgt_create_lattice(const int dims[4], const lgt_allocator *alloc, void *stream,
+                       lgt_lattice_t *out);
+/* Free everything the handle allocated.  NULL is accepted. */
+int lgt_destroy_lattice(lgt_lattice_t lat);
+int lgt_set_stream(lgt_lattice_t lat, void *stream);
+/* V and the bytes of device memory the handle holds. */
+int lgt_lattice_info(lgt_lattice_t lat, int64_t *volume, size_t *device_bytes);
+/* Bytes of one field in the device layout: kind 0 spinor (parity LGT_EVEN/ODD
+ * = half field, LGT_FULL = both), 1 momenta, 2 G-form gradient; precision
+ * LGT_FP64 or LGT_FP32 (spinors only). */
+int lgt_field_bytes(lgt_lattice_t lat, int kind, int parity, int precision, size_t *bytes);
+
+/* ------------------------------------------------------------------ gauge field */
+/* Copy a canonical link field (device, complex128 [V][4][3][3]) into the
+ * handle; derives the FP32 two-row copy.  Links are used as given. */
+int lgt_set_links(lgt_lattice_t lat, const double *links_canonical);
+int lgt_get_links(lgt_lattice_t lat, double *links_canonical);
+/* U_mu(x) = exp(i alpha sum_a h_a T^a), h_a ~ N(0,1) from Philox-4x32-10
+ * (key = seed, counter = (4 s + mu, pair, 0, 3)), Box-Muller on 53-bit uniforms. */
+int lgt_random_links(lgt_lattice_t lat, uint64_t seed, double alpha);
+/* Gram-Schmidt rows 1, 2 and row 3 = conj(row1 x row2) on every link. */
+int lgt_reunitarise(lgt_lattice_t lat);
+/* <P> = sum_{x,mu<nu} Re tr U_munu / (3 * 6 V) (host result). */
+int lgt_plaquette(lgt_lattice_t lat, double *plaq);
+
+/* ------------------------------------------------------------------ layouts */
+/* canonical spinor (device, complex128 [V][4][3]) <-> device field of the given
+ * parity (LGT_EVEN/ODD: only that parity's sites) and precision. */
+int lgt_pack_spinor(lgt_lattice_t lat, const double *canonical, void *field, int parity,
+                    int precision);
+int lgt_unpack_spinor(lgt_lattice_t lat, const void *field, double *canonical, int parity,
+                      int precision);
+/* canonical momenta / forces (device, double [V][4][8]) <-> device layout */
+int lgt_pack_momenta(lgt_lattice_t lat, const double *canonical, double *mom);
+int lgt_unpack_momenta(lgt_lattice_t lat, const double *mom, double *canonical);
+/* canonical gradient (device, complex128 [V][4][3][3]) <-> G-form layout */
+int lgt_pack_links_field(lgt_lattice_t lat, const double *canonical, double *field);
+int lgt_unpack_links_field(lgt_lattice_t lat, const double *field, double *canonical);
+
+/* ------------------------------------------------------------------ operators */
+/* Apply a Wilson-Dirac operator (Sec. III: "Wilson-Dirac operator"; D of
+ * Eq. S3.1) to `in`, writing `out` (distinct buffers, device layout of
+ * `precision`, LGT_FP64 or LGT_FP32).  op/out_parity as in the LGT_OP_* enum;
+ * dagger != 0 applies the adjoint (H^+ = g5 H g5).  Asynchronous. */
+int lgt_dslash(lgt_lattice_t lat, const void *in, void *out, int op, int out_parity,
+               int dagger, double kappa, int precision);
+
+/* Solve A x = b, A = Dhat^+ Dhat on even sites (even_odd = 1; b, x FP64 half
+ * fields) or A = D^+ D (even_odd = 0; full FP64 fields), by CG from x = 0
+ * (Eq. S3.4: the solve is not differentiated).  Synchronous. */
+int lgt_cg_solve(lgt_lattice_t lat, const double *b, double *x, double kappa, int even_odd,
+                 const lgt_solver_params *sp, lgt_solve_stats *stats);
+
+/* ------------------------------------------------------------------ actions */
+/* S_G (beta from ap) and S_f = phi^+ A^{-1} phi evaluated as 2 Re(phi^+ chi) - |M chi|^2
+ * (A chi = phi), phi an FP64 device field (even half for even_odd, else full).
+ * Either output pointer may be NULL.  Synchronous. */
+int lgt_action(lgt_lattice_t lat, const lgt_action_params *ap, const double *phi,
+               const lgt_solver_params *sp, double *S_g, double *S_f, lgt_solve_stats *stats);
+/* Kinetic energy 1/2 sum pi_a^2 of a momentum field (device layout). */
+int lgt_kinetic_energy(lgt_lattice_t lat, const double *mom, double *K);
+
+/* ------------------------------------------------------------------ forces */
+/* F = dS_G + dS_f (Eq. S2.8; fermion part from Eq. S3.12 with chi = A^{-1} phi,
+ * eta = M chi).  form LGT_FORCE_LIE writes Lie components in the momentum
+ * layout; LGT_GRAD_G writes the real-component gradient G in the G-form layout.
+ * With ap->n_stout > 0 the actions are evaluated on the smeared field and the
+ * force is taken back through the smearing (adjoint of each level).
+ * Synchronous (returns after the solve). */
+int lgt_force(lgt_lattice_t lat, const lgt_action_params *ap, const double *phi,
+              const lgt_solver_params *sp, double *F_out, int form, lgt_solve_stats *stats);
+
+/* ------------------------------------------------------------------ molecular dynamics */
+/* which = LGT_UPDATE_U: U <- exp(i eps P) U (Eq. S2.1), P from mom.
+ * which = LGT_UPDATE_P: mom <- mom - eps F(U) (Eq. S2.2), F as in lgt_force. */
+int lgt_md_update(lgt_lattice_t lat, double *mom, double eps, int which,
+                  const lgt_action_params *ap, const double *phi, const lgt_solver_params *sp,
+                  lgt_solve_stats *stats);
+/* pi_a ~ N(0,1) (Philox counter (4 s + mu, pair, traj, 1)). */
+int lgt_gaussian_momenta(lgt_lattice_t lat, double *mom, uint64_t seed, uint32_t traj);
+/* complex Gaussian spinor, Re, Im ~ N(0, 1/2), on the sites of `parity`
+ * (counter (s, component, traj, field)); field = 2 is the HMC heatbath xi. */
+int lgt_gaussian_spinor(lgt_lattice_t lat, double *field, uint64_t seed, uint32_t traj,
+                        uint32_t field_id, int parity);
+/* One HMC trajectory (Sec. III B): momentum and pseudofermion heatbaths
+ * (phi = M^+ xi), integration, Metropolis with u from Philox (counter
+ * (0,0,traj,4)), U restored on reject, then reunitarisation.  Synchronous. */
+int lgt_hmc_trajectory(lgt_lattice_t lat, const lgt_action_params *ap,
+                       const lgt_hmc_params *hp, uint64_t seed, uint32_t traj,
+                       lgt_hmc_result *res);
+
+/* ------------------------------------------------------------------ diagnostics */
+/* Peak FP64 FMA throughput of this device (dependent FMA chains), in FLOP/s. */
+int lgt_measure_fp64_peak(double *flops, double *seconds);
+/* Kernel launches the library enqueued on this thread since the last reset. */
+int64_t lgt_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,877 @@
+// lgt_api.cu -- the C ABI of liblgt (include/lgt.h): lattice handles, the CG
+// drivers (FP64, and mixed FP32-inner / FP64-reliable-update), actions, forces,
+// molecular-dynamics updates and HMC trajectories.  All device work is in the
+// kernels of the other translation units; this file only sequences launches on
+// the handle's stream and reads back the few scalars the control flow needs.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lgt.h"
+#include "lgt_internal.h"
+
+using namespace lgt;
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err = "";
+static thread_local int64_t g_launches = 0;
+
+namespace lgt {
+void count_launch() { ++g_launches; }
+}
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(LGT_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                   \
+    } while (0)
+#define TRY(call)                        \
+    do {                                 \
+        int r_ = (call);                 \
+        if (r_ != LGT_OK) return r_;     \
+    } while (0)
+
+// ---------------------------------------------------------------- host Philox (Metropolis draw)
+static void philox_host(const uint32_t ctr[4], uint64_t seed, uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t a = (uint64_t)0xD2511F53u * c0, b = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(b >> 32) ^ c1 ^ k0, n2 = (uint32_t)(a >> 32) ^ c3 ^ k1;
+        c0 = n0; c1 = (uint32_t)b; c2 = n2; c3 = (uint32_t)a;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// ---------------------------------------------------------------- handle
+struct Links {
+    double2* U;
+    float4* U12;
+};
+
+struct lgt_lattice {
+    int dims[4];
+    Geom g;
+    lgt_allocator alloc;
+    bool custom_alloc;
+    cudaStream_t st;
+    std::vector<void*> blocks;
+    size_t bytes;
+    // gauge field
+    Links thin;
+    // solver workspace (full fields; even-odd solves use the even half)
+    double2 *r, *p, *u, *t, *X, *Y, *b;
+    float4 *r32, *p32, *x32, *u32, *t32;
+    bool have_solver;
+    // HMC / force workspace
+    double2 *mom, *Ubak, *phi, *xi, *F, *G;
+    bool have_md;
+    // stout stack: smeared links of each level and the per-level gradients
+    Links smeared[5];
+    double2* stout_scratch;
+    int n_smeared_alloc;
+    // reductions
+    double* partials;
+    unsigned* counter;
+    Scalars* s;
+    Scalars* hs;   // pinned host mirror
+};
+
+static int lat_alloc(lgt_lattice* L, size_t bytes, void** out) {
+    void* p = nullptr;
+    if (L->custom_alloc) {
+        p = L->alloc.alloc(L->alloc.ctx, bytes, (void*)L->st);
+        if (!p) return fail(LGT_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return fail(LGT_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    L->blocks.push_back(p);
+    L->bytes += bytes;
+    *out = p;
+    return LGT_OK;
+}
+
+template <typename T> static int A(lgt_lattice* L, size_t bytes, T** out) {
+    void* p;
+    int r = lat_alloc(L, bytes, &p);
+    *out = (T*)p;
+    return r;
+}
+
+static size_t spinor64_full(const lgt_lattice* L) { return (size_t)2 * 12 * L->g.Vh * sizeof(double2); }
+static size_t spinor32_full(const lgt_lattice* L) { return (size_t)2 * 6 * L->g.Vh * sizeof(float4); }
+static size_t links64(const lgt_lattice* L) { return (size_t)8 * 9 * L->g.Vh * sizeof(double2); }
+static size_t links12(const lgt_lattice* L) { return (size_t)8 * 3 * L->g.Vh * sizeof(float4); }
+static size_t mom_bytes(const lgt_lattice* L) { return (size_t)8 * 4 * L->g.Vh * sizeof(double2); }
+
+static int ensure_solver(lgt_lattice* L) {
+    if (L->have_solver) return LGT_OK;
+    size_t s64 = spinor64_full(L), s32 = spinor32_full(L);
+    TRY(A(L, s64, &L->r)); TRY(A(L, s64, &L->p)); TRY(A(L, s64, &L->u)); TRY(A(L, s64, &L->t));
+    TRY(A(L, s64, &L->X)); TRY(A(L, s64, &L->Y)); TRY(A(L, s64, &L->b));
+    TRY(A(L, s32, &L->r32)); TRY(A(L, s32, &L->p32)); TRY(A(L, s32, &L->x32)); TRY(A(L, s32, &L->u32));
+    TRY(A(L, s32, &L->t32));
+    L->have_solver = true;
+    return LGT_OK;
+}
+
+static int ensure_md(lgt_lattice* L) {
+    if (L->have_md) return LGT_OK;
+    TRY(A(L, mom_bytes(L), &L->mom));
+    TRY(A(L, links64(L), &L->Ubak));
+    TRY(A(L, spinor64_full(L), &L->phi));
+    TRY(A(L, spinor64_full(L), &L->xi));
+    TRY(A(L, mom_bytes(L), &L->F));
+    TRY(A(L, links64(L), &L->G));
+    L->have_md = true;
+    return LGT_OK;
+}
+
+static int ensure_stout(lgt_lattice* L, int n) {
+    if (n > 4) return fail(LGT_EINVAL, "n_stout = %d > 4", n);
+    if (!L->stout_scratch && n > 0) TRY(A(L, 2 * links64(L), &L->stout_scratch));
+    while (L->n_smeared_alloc < n) {
+        int k = ++L->n_smeared_alloc;
+        TRY(A(L, links64(L), &L->smeared[k].U));
+        TRY(A(L, links12(L), &L->smeared[k].U12));
+    }
+    return LGT_OK;
+}
+
+static RedArgs red(lgt_lattice* L) { return RedArgs{L->s, L->partials, L->counter}; }
+
+static int sync_scalars(lgt_lattice* L) {
+    CK(cudaMemcpyAsync(L->hs, L->s, sizeof(Scalars), cudaMemcpyDeviceToHost, L->st));
+    CK(cudaStreamSynchronize(L->st));
+    return LGT_OK;
+}
+static int push_scalars(lgt_lattice* L) {
+    CK(cudaMemcpyAsync(L->s, L->hs, sizeof(Scalars), cudaMemcpyHostToDevice, L->st));
+    return LGT_OK;
+}
+
+extern "C" const char* lgt_last_error(void) { return g_err.c_str(); }
+extern "C" int lgt_version(void) { return 100; }
+extern "C" int64_t lgt_launch_count(int reset) {
+    int64_t v = g_launches;
+    if (reset) g_launches = 0;
+    return v;
+}
+
+extern "C" int lgt_create_lattice(const int dims[4], const lgt_allocator* alloc, void* stream, lgt_lattice_t* out) {
+    if (!dims || !out) return fail(LGT_EINVAL, "null argument");
+    *out = nullptr;
+    long V = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (dims[m] < 2 || dims[m] % 2) return fail(LGT_EINVAL, "extent %d of direction %d must be even and >= 2", dims[m], m);
+        V *= dims[m];
+    }
+    if (V > (1L << 30)) return fail(LGT_EINVAL, "volume %ld too large", V);
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(LGT_EINVAL, "allocator without alloc/free");
+    lgt_lattice* L = new lgt_lattice();
+    memcpy(L->dims, dims, sizeof L->dims);
+    for (int m = 0; m < 4; ++m) L->g.L[m] = dims[m];
+    L->g.V = (int)V;
+    L->g.Vh = (int)(V / 2);
+    L->g.stride[0] = 1;
+    L->g.stride[1] = dims[0];
+    L->g.stride[2] = dims[0] * dims[1];
+    L->g.stride[3] = dims[0] * dims[1] * dims[2];
+    L->custom_alloc = alloc != nullptr;
+    if (alloc) L->alloc = *alloc;
+    L->st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = A(L, links64(L), &L->thin.U)) || (rc = A(L, links12(L), &L->thin.U12)) ||
+        (rc = A(L, sizeof(double) * (size_t)(2 * L->g.Vh / NT + 4096), &L->partials)) ||
+        (rc = A(L, 64, &L->counter)) || (rc = A(L, sizeof(Scalars), &L->s))) {
+        lgt_destroy_lattice(L);
+        return rc;
+    }
+    if (cudaMallocHost((void**)&L->hs, sizeof(Scalars)) != cudaSuccess) {
+        lgt_destroy_lattice(L);
+        return fail(LGT_ENOMEM, "cudaMallocHost failed");
+    }
+    memset(L->hs, 0, sizeof(Scalars));
+    cudaError_t e = cudaMemsetAsync(L->counter, 0, 64, L->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->s, 0, sizeof(Scalars), L->st);
+    if (e == cudaSuccess) e = gauge_unit(L->thin.U, L->thin.U12, L->g, L->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->st);
+    if (e != cudaSuccess) {
+        lgt_destroy_lattice(L);
+        return fail(LGT_ECUDA, "lattice initialisation: %s", cudaGetErrorString(e));
+    }
+    L->smeared[0] = L->thin;
+    *out = L;
+    return LGT_OK;
+}
+
+extern "C" int lgt_destroy_lattice(lgt_lattice_t L) {
+    if (!L) return LGT_OK;
+    cudaStreamSynchronize(L->st);
+    for (void* p : L->blocks) {
+        if (L->custom_alloc) L->alloc.free(L->alloc.ctx, p, (void*)L->st);
+        else cudaFree(p);
+    }
+    if (L->hs) cudaFreeHost(L->hs);
+    delete L;
+    return LGT_OK;
+}
+
+extern "C" int lgt_set_stream(lgt_lattice_t L, void* stream) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    L->st = (cudaStream_t)stream;
+    return LGT_OK;
+}
+
+extern "C" int lgt_lattice_info(lgt_lattice_t L, int64_t* volume, size_t* bytes) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    if (volume) *volume = L->g.V;
+    if (bytes) *bytes = L->bytes;
+    return LGT_OK;
+}
+
+extern "C" int lgt_field_bytes(lgt_lattice_t L, int kind, int parity, int precision, size_t* bytes) {
+    if (!L || !bytes) return fail(LGT_EINVAL, "null argument");
+    if (kind == 0) {
+        size_t half = (precision == LGT_FP32) ? (size_t)6 * L->g.Vh * 16 : (size_t)12 * L->g.Vh * 16;
+        if (parity == LGT_FULL) half *= 2;
+        *bytes = half;
+    } else if (kind == 1) {
+        *bytes = mom_bytes(L);
+    } else if (kind == 2) {
+        *bytes = links64(L);
+    } else {
+        return fail(LGT_EINVAL, "unknown field kind %d", kind);
+    }
+    return LGT_OK;
+}
+
+// ---------------------------------------------------------------- gauge field
+extern "C" int lgt_set_links(lgt_lattice_t L, const double* canon) {
+    if (!L || !canon) return fail(LGT_EINVAL, "null argument");
+    CK(gauge_pack_links(L->thin.U, L->thin.U12, (const double2*)canon, L->g, L->st));
+    return LGT_OK;
+}
+extern "C" int lgt_get_links(lgt_lattice_t L, double* canon) {
+    if (!L || !canon) return fail(LGT_EINVAL, "null argument");
+    CK(gauge_unpack_links(canon, L->thin.U, L->g, L->st));
+    return LGT_OK;
+}
+extern "C" int lgt_random_links(lgt_lattice_t L, uint64_t seed, double alpha) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    CK(gauge_random(L->thin.U, L->thin.U12, L->g, seed, alpha, L->st));
+    return LGT_OK;
+}
+extern "C" int lgt_reunitarise(lgt_lattice_t L) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    CK(gauge_reunitarise(L->thin.U, L->thin.U12, L->g, L->st));
+    return LGT_OK;
+}
+static int plaquette_sum(lgt_lattice* L, const double2* U, double* out) {
+    CK(gauge_plaquette(U, L->g, red(L), 0, L->st));
+    TRY(sync_scalars(L));
+    *out = L->hs->slot[0];
+    return LGT_OK;
+}
+extern "C" int lgt_plaquette(lgt_lattice_t L, double* plaq) {
+    if (!L || !plaq) return fail(LGT_EINVAL, "null argument");
+    double s;
+    TRY(plaquette_sum(L, L->thin.U, &s));
+    *plaq = s / (6.0 * L->g.V);
+    return LGT_OK;
+}
+
+// ---------------------------------------------------------------- layouts
+static int check_parity(int parity) {
+    if (parity < 0 || parity > 2) return fail(LGT_EINVAL, "parity %d", parity);
+    return LGT_OK;
+}
+extern "C" int lgt_pack_spinor(lgt_lattice_t L, const double* canon, void* field, int parity, int precision) {
+    if (!L || !canon || !field) return fail(LGT_EINVAL, "null argument");
+    TRY(check_parity(parity));
+    CK(spinor_pack(field, (const double2*)canon, L->g, parity, precision != LGT_FP32, L->st));
+    return LGT_OK;
+}
+extern "C" int lgt_unpack_spinor(lgt_lattice_t L, const void* field, double* canon, int parity, int precision) {
+    if (!L || !canon || !field) return fail(LGT_EINVAL, "null argument");
+    TRY(check_parity(parity));
+    CK(spinor_unpack((double2*)canon, field, L->g, parity, precision != LGT_FP32, L->st));
+    return LGT_OK;
+}
+extern "C" int lgt_pack_momenta(lgt_lattice_t L, const double* canon, double* mom) {
+    if (!L || !canon || !mom) return fail(LGT_EINVAL, "null argument");
+    CK(mom_pack((double2*)mom, canon, L->g, L->st));
+    return LGT_OK;
+}
+extern "C" int lgt_unpack_momenta(lgt_lattice_t L, const double* mom, double* canon) {
+    if (!L || !canon || !mom) return fail(LGT_EINVAL, "null argument");
+    CK(mom_unpack(canon, (const double2*)mom, L->g, L->st));
+    return LGT_OK;
+}
+extern "C" int lgt_pack_links_field(lgt_lattice_t L, const double* canon, double* field) {
+    if (!L || !canon || !field) return fail(LGT_EINVAL, "null argument");
+    CK(gauge_pack_field((double2*)field, (const double2*)canon, L->g, L->st));
+    return LGT_OK;
+}
+extern "C" int lgt_unpack_links_field(lgt_lattice_t L, const double* field, double* canon) {
+    if (!L || !canon || !field) return fail(LGT_EINVAL, "null argument");
+    CK(gauge_unpack_field(canon, (const double2*)field, L->g, L->st));
+    return LGT_OK;
+}
+
+// ---------------------------------------------------------------- operators
+static HopArgs hop_base(lgt_lattice* L, const Links& lk, bool fp64) {
+    HopArgs a;
+    memset(&a, 0, sizeof a);
+    a.U = fp64 ? (const void*)lk.U : (const void*)lk.U12;
+    a.g = L->g;
+    a.s = L->s;
+    a.partials = L->partials;
+    a.counter = L->counter;
+    a.a = 1.0;
+    return a;
+}
+static size_t half_elems(const lgt_lattice* L, bool fp64) { return (size_t)(fp64 ? 12 : 6) * L->g.Vh; }
+// pointer to the half field of parity q inside a full field
+static const void* half(const void* f, const lgt_lattice* L, bool fp64, int q) {
+    return (const char*)f + (size_t)q * half_elems(L, fp64) * 16;
+}
+static void* half(void* f, const lgt_lattice* L, bool fp64, int q) {
+    return (char*)f + (size_t)q * half_elems(L, fp64) * 16;
+}
+
+// single-parity hop: out_q = a H_{q,1-q} in (+ y)
+static int hop1(lgt_lattice* L, const Links& lk, bool fp64, bool dag, int q, const void* in_half, void* out_half,
+                double a, int epi = EPI_HOP, const void* y_half = nullptr) {
+    HopArgs A = hop_base(L, lk, fp64);
+    A.parity = q;
+    A.in[1 - q] = in_half;
+    A.out[q] = out_half;
+    A.y[q] = y_half;
+    A.a = a;
+    CK(launch_hop(A, fp64, dag, epi, L->st));
+    return LGT_OK;
+}
+// full-lattice D or D^+: out = in - kappa H in
+static int dfull(lgt_lattice* L, const Links& lk, bool fp64, bool dag, const void* in, void* out, double kappa) {
+    HopArgs A = hop_base(L, lk, fp64);
+    A.parity = 2;
+    for (int q = 0; q < 2; ++q) {
+        A.in[q] = half(in, L, fp64, q);
+        A.out[q] = half(out, L, fp64, q);
+        A.y[q] = half(in, L, fp64, q);
+    }
+    A.a = -kappa;
+    CK(launch_hop(A, fp64, dag, EPI_XPAY, L->st));
+    return LGT_OK;
+}
+// Dhat^(+) on even half fields: out = in - kappa^2 H_eo H_oe in, tmp an odd half field
+static int dhat(lgt_lattice* L, const Links& lk, bool fp64, bool dag, const void* in, void* out, void* tmp,
+                double kappa) {
+    TRY(hop1(L, lk, fp64, dag, 1, in, tmp, 1.0));
+    TRY(hop1(L, lk, fp64, dag, 0, tmp, out, -kappa * kappa, EPI_XPAY, in));
+    return LGT_OK;
+}
+
+extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, int out_parity, int dagger,
+                          double kappa, int precision) {
+    if (!L || !in || !out) return fail(LGT_EINVAL, "null argument");
+    if (in == out) return fail(LGT_EINVAL, "in and out must be distinct buffers");
+    if (precision != LGT_FP64 && precision != LGT_FP32) return fail(LGT_EINVAL, "precision %d", precision);
+    const bool fp64 = precision == LGT_FP64;
+    const bool dag = dagger != 0;
+    switch (op) {
+    case LGT_OP_HOP:
+        if (out_parity != LGT_EVEN && out_parity != LGT_ODD) return fail(LGT_EINVAL, "hop needs EVEN or ODD");
+        return hop1(L, L->thin, fp64, dag, out_parity, in, out, 1.0);
+    case LGT_OP_D:
+        return dfull(L, L->thin, fp64, dag, in, out, kappa);
+    case LGT_OP_DHAT:
+    case LGT_OP_DHAT_NORMAL: {
+        TRY(ensure_solver(L));
+        void* tmp = fp64 ? (void*)L->t : (void*)L->t32;
+        if (op == LGT_OP_DHAT) return dhat(L, L->thin, fp64, dag, in, out, tmp, kappa);
+        void* mid = fp64 ? (void*)L->u : (void*)L->u32;
+        TRY(dhat(L, L->thin, fp64, false, in, mid, tmp, kappa));
+        return dhat(L, L->thin, fp64, true, mid, out, tmp, kappa);
+    }
+    default:
+        return fail(LGT_EINVAL, "unknown operator %d", op);
+    }
+}
+
+// ---------------------------------------------------------------- CG
+// One CG iteration on A = M^+M, enqueued without host synchronisation.  Kernels
+// return at once after the stop flag is raised on the device.
+static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, double kappa, void* x, void* r, void* p,
+                        void* u, void* t) {
+    if (eo) {
+        HopArgs A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 1; A.in[0] = p; A.out[1] = t;
+        CK(launch_hop(A, fp64, false, EPI_HOP, L->st));
+        A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 0; A.in[1] = t; A.out[0] = u; A.y[0] = p; A.a = -kappa * kappa; A.red_op = RED_PAP;
+        CK(launch_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
+        A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 1; A.in[0] = u; A.out[1] = t;
+        CK(launch_hop(A, fp64, true, EPI_HOP, L->st));
+        A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 0; A.in[1] = t; A.y[0] = u; A.a = -kappa * kappa; A.red_op = RED_RR;
+        A.x[0] = x; A.r[0] = r; A.pv[0] = p;
+        CK(launch_hop(A, fp64, true, EPI_CG, L->st));
+        CK(blas_cg_p_update(p, r, L->g.Vh, L->g.Vh, fp64, red(L), L->st));
+    } else {
+        HopArgs A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 2;
+        for (int q = 0; q < 2; ++q) {
+            A.in[q] = half(p, L, fp64, q); A.out[q] = half(u, L, fp64, q); A.y[q] = half(p, L, fp64, q);
+        }
+        A.a = -kappa; A.red_op = RED_PAP;
+        CK(launch_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
+        A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 2;
+        for (int q = 0; q < 2; ++q) {
+            A.in[q] = half(u, L, fp64, q); A.y[q] = half(u, L, fp64, q);
+            A.x[q] = half(x, L, fp64, q); A.r[q] = half(r, L, fp64, q); A.pv[q] = half(p, L, fp64, q);
+        }
+        A.a = -kappa; A.red_op = RED_RR;
+        CK(launch_hop(A, fp64, true, EPI_CG, L->st));
+        CK(blas_cg_p_update(p, r, 2 * L->g.Vh, L->g.Vh, fp64, red(L), L->st));
+    }
+    return LGT_OK;
+}
+
+// FP64 true residual res = b - A x, |res|^2 -> slot 0
+static int true_residual(lgt_lattice* L, const Links& lk, bool eo, double kappa, const double2* b, const double2* x,
+                         double2* res) {
+    if (eo) {
+        TRY(hop1(L, lk, true, false, 1, x, L->t, 1.0));
+        TRY(hop1(L, lk, true, false, 0, L->t, L->u, -kappa * kappa, EPI_XPAY, x));
+        TRY(hop1(L, lk, true, true, 1, L->u, L->t, 1.0));
+        HopArgs A = hop_base(L, lk, true);
+        A.parity = 0; A.in[1] = L->t; A.y[0] = L->u; A.a = -kappa * kappa; A.out[0] = res; A.pv[0] = b;
+        A.red_op = RED_STORE; A.red_slot = 0;
+        CK(launch_hop(A, true, true, EPI_RESID, L->st));
+    } else {
+        TRY(dfull(L, lk, true, false, x, L->u, kappa));
+        HopArgs A = hop_base(L, lk, true);
+        A.parity = 2;
+        for (int q = 0; q < 2; ++q) {
+            A.in[q] = half(L->u, L, true, q); A.y[q] = half(L->u, L, true, q);
+            A.out[q] = half(res, L, true, q); A.pv[q] = half(b, L, true, q);
+        }
+        A.a = -kappa; A.red_op = RED_STORE; A.red_slot = 0;
+        CK(launch_hop(A, true, true, EPI_RESID, L->st));
+    }
+    return LGT_OK;
+}
+
+static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x, double kappa, bool eo,
+                   const lgt_solver_params* sp, lgt_solve_stats* stats) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!sp) return fail(LGT_EINVAL, "null solver parameters");
+    if (sp->precision != LGT_FP64 && sp->precision != LGT_MIXED) return fail(LGT_EINVAL, "solver precision %d", sp->precision);
+    if (!(sp->tol > 0) || sp->max_iter <= 0) return fail(LGT_EINVAL, "tol and max_iter must be positive");
+    TRY(ensure_solver(L));
+    const int n = eo ? L->g.Vh : 2 * L->g.Vh;
+    const int K = sp->check_every > 0 ? sp->check_every : 16;
+    const bool mixed = sp->precision == LGT_MIXED;
+    const size_t b64 = (size_t)n * 12 * sizeof(double2), b32 = (size_t)n * 6 * sizeof(float4);
+    lgt_solve_stats st = {0, 0, 0.0, 0.0};
+
+    CK(blas_norm2(b, n, L->g.Vh, true, red(L), 0, L->st));
+    TRY(sync_scalars(L));
+    const double bb = L->hs->slot[0];
+    CK(cudaMemsetAsync(x, 0, b64, L->st));
+    if (!std::isfinite(bb)) return fail(LGT_ENAN, "right-hand side is not finite");
+    if (bb == 0.0) {
+        CK(cudaStreamSynchronize(L->st));
+        if (stats) *stats = st;
+        return LGT_OK;
+    }
+    const double target = sp->tol * sp->tol * bb;
+    Scalars* hs = L->hs;
+    memset(hs, 0, sizeof(Scalars));
+    hs->rr = bb;
+    hs->rr_max = bb;
+    hs->target = target;
+    hs->delta2 = mixed ? sp->delta * sp->delta : 0.0;
+    CK(cudaMemcpyAsync(L->r, b, b64, cudaMemcpyDeviceToDevice, L->st));
+    if (mixed) {
+        CK(blas_d2f(L->r32, b, n, L->g.Vh, L->st));
+        CK(cudaMemcpyAsync(L->p32, L->r32, b32, cudaMemcpyDeviceToDevice, L->st));
+        CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
+    } else {
+        CK(cudaMemcpyAsync(L->p, b, b64, cudaMemcpyDeviceToDevice, L->st));
+    }
+    TRY(push_scalars(L));
+    double rr_true = bb;
+    int rc = LGT_OK;
+    for (;;) {
+        for (int k = 0; k < K; ++k) {
+            if (mixed) TRY(cg_iteration(L, lk, false, eo, kappa, L->x32, L->r32, L->p32, L->u32, L->t32));
+            else TRY(cg_iteration(L, lk, true, eo, kappa, x, L->r, L->p, L->u, L->t));
+        }
+        TRY(sync_scalars(L));
+        if (hs->nan) { rc = fail(LGT_ENAN, "non-finite value in CG after %d iterations", hs->iters); break; }
+        const bool hit_cap = hs->iters >= sp->max_iter;
+        if (hs->done || hit_cap) {
+            if (mixed) {
+                CK(blas_add_f2d(x, L->x32, n, L->g.Vh, L->st));
+                CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
+            }
+            TRY(true_residual(L, lk, eo, kappa, b, x, L->r));
+            TRY(sync_scalars(L));
+            rr_true = hs->slot[0];
+            st.reliable_updates += 1;
+            if (!std::isfinite(rr_true)) { rc = fail(LGT_ENAN, "non-finite true residual"); break; }
+            if (rr_true <= target) break;
+            if (hit_cap) {
+                rc = fail(LGT_ENOCONV, "CG reached max_iter=%d, true relative residual %.3e", sp->max_iter,
+                          std::sqrt(rr_true / bb));
+                break;
+            }
+            if (mixed) CK(blas_d2f(L->r32, L->r, n, L->g.Vh, L->st));
+            hs->rr = rr_true;
+            hs->rr_max = rr_true;
+            hs->done = 0;
+            TRY(push_scalars(L));
+        }
+    }
+    CK(cudaStreamSynchronize(L->st));
+    st.iters = hs->iters;
+    st.true_rel_residual = std::sqrt(rr_true / bb);
+    st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = st;
+    return rc;
+}
+
+static void add_stats(lgt_solve_stats* acc, const lgt_solve_stats& s) {
+    acc->iters += s.iters;
+    acc->reliable_updates += s.reliable_updates;
+    acc->true_rel_residual = s.true_rel_residual > acc->true_rel_residual ? s.true_rel_residual : acc->true_rel_residual;
+    acc->seconds += s.seconds;
+}
+
+extern "C" int lgt_cg_solve(lgt_lattice_t L, const double* b, double* x, double kappa, int even_odd,
+                            const lgt_solver_params* sp, lgt_solve_stats* stats) {
+    if (!L || !b || !x) return fail(LGT_EINVAL, "null argument");
+    if (b == x) return fail(LGT_EINVAL, "b and x must be distinct");
+    return cg_core(L, L->thin, (const double2*)b, (double2*)x, kappa, even_odd != 0, sp, stats);
+}
+
+// ---------------------------------------------------------------- smearing
+static int check_action(const lgt_action_params* ap) {
+    if (!ap) return fail(LGT_EINVAL, "null action parameters");
+    if (ap->n_stout < 0 || ap->n_stout > 4) return fail(LGT_EINVAL, "n_stout = %d outside 0..4", ap->n_stout);
+    return LGT_OK;
+}
+// links seen by the Dirac operator: thin, or the last stout level (forward pass stored)
+static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out) {
+    if (ap->n_stout == 0) { *out = L->thin; return LGT_OK; }
+    TRY(ensure_stout(L, ap->n_stout));
+    for (int k = 1; k <= ap->n_stout; ++k) {
+        CK(stout_forward(L->smeared[k - 1].U, L->smeared[k].U, L->g, ap->rho, L->st));
+        CK(gauge_make12(L->smeared[k].U12, L->smeared[k].U, L->g, L->st));
+    }
+    *out = L->smeared[ap->n_stout];
+    return LGT_OK;
+}
+
+// ---------------------------------------------------------------- actions
+// S_f pieces after a solve chi = X (even half or full): eta = M chi into Y
+static int pf_action_on(lgt_lattice* L, const Links& lk, const lgt_action_params* ap, const double2* phi,
+                        const lgt_solver_params* sp, double* S_f, lgt_solve_stats* stats) {
+    TRY(ensure_solver(L));
+    const bool eo = ap->even_odd != 0;
+    const int n = eo ? L->g.Vh : 2 * L->g.Vh;
+    TRY(cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats));
+    if (eo) TRY(dhat(L, lk, true, false, L->X, L->Y, L->t, ap->kappa));
+    else TRY(dfull(L, lk, true, false, L->X, L->Y, ap->kappa));
+    CK(blas_action_parts(phi, L->X, L->Y, n, L->g.Vh, red(L), L->st));
+    TRY(sync_scalars(L));
+    *S_f = 2.0 * L->hs->slot[0] - L->hs->slot[1];
+    return LGT_OK;
+}
+
+extern "C" int lgt_action(lgt_lattice_t L, const lgt_action_params* ap, const double* phi,
+                          const lgt_solver_params* sp, double* S_g, double* S_f, lgt_solve_stats* stats) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    TRY(check_action(ap));
+    if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
+    if (S_g) {
+        double s;
+        TRY(plaquette_sum(L, L->thin.U, &s));
+        *S_g = ap->beta * (6.0 * L->g.V - s);
+    }
+    if (S_f) {
+        *S_f = 0.0;
+        if (ap->fermions) {
+            if (!phi) return fail(LGT_EINVAL, "null phi");
+            Links lk;
+            TRY(fermion_links(L, ap, &lk));
+            TRY(pf_action_on(L, lk, ap, (const double2*)phi, sp, S_f, stats));
+            if (!std::isfinite(*S_f)) return fail(LGT_ENAN, "non-finite S_f");
+        }
+    }
+    return LGT_OK;
+}
+
+extern "C" int lgt_kinetic_energy(lgt_lattice_t L, const double* mom, double* K) {
+    if (!L || !mom || !K) return fail(LGT_EINVAL, "null argument");
+    CK(gauge_kinetic((const double2*)mom, L->g, red(L), 0, L->st));
+    TRY(sync_scalars(L));
+    *K = L->hs->slot[0];
+    return LGT_OK;
+}
+
+// ---------------------------------------------------------------- forces
+// Solve and build X, Y of the fermion force on links lk.
+static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_params* ap, const double2* phi,
+                         const lgt_solver_params* sp, lgt_solve_stats* stats) {
+    const bool eo = ap->even_odd != 0;
+    TRY(cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats));
+    if (eo) {
+        double2* Xo = (double2*)half(L->X, L, true, 1);
+        double2* Yo = (double2*)half(L->Y, L, true, 1);
+        // X_o = kappa H_oe chi_e;  eta_e = chi_e - kappa H_eo X_o;  Y_o = kappa (H^+)_oe eta_e
+        TRY(hop1(L, lk, true, false, 1, L->X, Xo, ap->kappa));
+        TRY(hop1(L, lk, true, false, 0, Xo, L->Y, -ap->kappa, EPI_XPAY, L->X));
+        TRY(hop1(L, lk, true, true, 1, L->Y, Yo, ap->kappa));
+    } else {
+        TRY(dfull(L, lk, true, false, L->X, L->Y, ap->kappa));
+    }
+    return LGT_OK;
+}
+
+// out = keep*out + coef * (dS_G + dS_f) in Lie (form 0) or G (form 1) layout, on the
+// links the actions see (no smearing here).
+static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk, const lgt_action_params* ap,
+                    const double2* phi, const lgt_solver_params* sp, double coef, int keep, int form, double2* out,
+                    lgt_solve_stats* stats) {
+    if (ap->fermions) {
+        if (!phi) return fail(LGT_EINVAL, "null phi");
+        TRY(ensure_solver(L));
+        TRY(force_vectors(L, ferm_lk, ap, phi, sp, stats));
+    }
+    if (ap->beta != 0.0) {
+        CK(gauge_force(gauge_lk.U, L->g, ap->beta, coef, keep, form, out, L->st));
+        keep = 1;
+    }
+    if (ap->fermions) {
+        CK(fermion_force(ferm_lk.U, L->X, L->Y, L->g, ap->kappa, coef, keep, form, out, L->st));
+        keep = 1;
+    }
+    if (!keep) CK(cudaMemsetAsync(out, 0, form == 0 ? mom_bytes(L) : links64(L), L->st));
+    return LGT_OK;
+}
+
+// Smeared fermion action: G_fermion w.r.t. the last level, taken back level by
+// level; the gauge action sees the thin links.  Result G in G layout (thin links).
+static int force_grad_stout(lgt_lattice* L, const lgt_action_params* ap, const double2* phi,
+                            const lgt_solver_params* sp, double2* G, lgt_solve_stats* stats) {
+    Links top;
+    TRY(fermion_links(L, ap, &top));
+    double2* ga = L->stout_scratch;                       // gradient ping-pong
+    double2* gb = L->stout_scratch + (size_t)8 * 9 * L->g.Vh;
+    lgt_action_params fa = *ap;
+    fa.beta = 0.0;
+    if (ap->fermions) {
+        TRY(force_on(L, L->thin, top, &fa, phi, sp, 1.0, 0, 1, ga, stats));
+    } else {
+        CK(cudaMemsetAsync(ga, 0, links64(L), L->st));
+    }
+    for (int k = ap->n_stout; k >= 1; --k) {
+        double2* dst = (k == 1) ? G : gb;
+        CK(stout_backward(L->smeared[k - 1].U, ga, dst, L->t /*scratch*/, L->g, ap->rho, L->st));
+        std::swap(ga, gb);
+        if (k == 1) break;
+    }
+    if (ap->beta != 0.0) CK(gauge_force(L->thin.U, L->g, ap->beta, 1.0, 1, 1, G, L->st));
+    return LGT_OK;
+}
+
+extern "C" int lgt_force(lgt_lattice_t L, const lgt_action_params* ap, const double* phi,
+                         const lgt_solver_params* sp, double* F_out, int form, lgt_solve_stats* stats) {
+    if (!L || !F_out) return fail(LGT_EINVAL, "null argument");
+    TRY(check_action(ap));
+    if (form != LGT_FORCE_LIE && form != LGT_GRAD_G) return fail(LGT_EINVAL, "form %d", form);
+    if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
+    if (ap->n_stout == 0) {
+        TRY(force_on(L, L->thin, L->thin, ap, (const double2*)phi, sp, 1.0, 0, form, (double2*)F_out, stats));
+    } else {
+        TRY(ensure_solver(L));
+        TRY(ensure_md(L));
+        double2* G = form == LGT_GRAD_G ? (double2*)F_out : L->G;
+        TRY(force_grad_stout(L, ap, (const double2*)phi, sp, G, stats));
+        if (form == LGT_FORCE_LIE) CK(grad_to_lie((double2*)F_out, G, L->thin.U, L->g, L->st));
+    }
+    CK(cudaStreamSynchronize(L->st));
+    return LGT_OK;
+}
+
+// mom -= eps F
+static int kick(lgt_lattice* L, double2* mom, double eps, const lgt_action_params* ap, const double2* phi,
+                const lgt_solver_params* sp, lgt_solve_stats* stats) {
+    if (ap->n_stout == 0) return force_on(L, L->thin, L->thin, ap, phi, sp, -eps, 1, 0, mom, stats);
+    TRY(ensure_md(L));
+    TRY(force_grad_stout(L, ap, phi, sp, L->G, stats));
+    CK(grad_to_lie(L->F, L->G, L->thin.U, L->g, L->st));
+    CK(gauge_kick(mom, L->F, eps, L->g, L->st));
+    return LGT_OK;
+}
+
+extern "C" int lgt_md_update(lgt_lattice_t L, double* mom, double eps, int which, const lgt_action_params* ap,
+                             const double* phi, const lgt_solver_params* sp, lgt_solve_stats* stats) {
+    if (!L || !mom) return fail(LGT_EINVAL, "null argument");
+    if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
+    if (which == LGT_UPDATE_U) {
+        CK(gauge_update_links(L->thin.U, L->thin.U12, (const double2*)mom, eps, L->g, L->st));
+        return LGT_OK;
+    }
+    if (which != LGT_UPDATE_P) return fail(LGT_EINVAL, "which = %d", which);
+    TRY(check_action(ap));
+    lgt_solve_stats s = {0, 0, 0.0, 0.0};
+    TRY(kick(L, (double2*)mom, eps, ap, (const double2*)phi, sp, &s));
+    CK(cudaStreamSynchronize(L->st));
+    if (stats) *stats = s;
+    return LGT_OK;
+}
+
+extern "C" int lgt_gaussian_momenta(lgt_lattice_t L, double* mom, uint64_t seed, uint32_t traj) {
+    if (!L || !mom) return fail(LGT_EINVAL, "null argument");
+    CK(gauge_momenta_heatbath((double2*)mom, L->g, seed, traj, L->st));
+    return LGT_OK;
+}
+
+extern "C" int lgt_gaussian_spinor(lgt_lattice_t L, double* field, uint64_t seed, uint32_t traj, uint32_t field_id,
+                                   int parity) {
+    if (!L || !field) return fail(LGT_EINVAL, "null argument");
+    TRY(check_parity(parity));
+    CK(spinor_gaussian((double2*)field, L->g, parity, seed, traj, field_id, L->st));
+    return LGT_OK;
+}
+
+// ---------------------------------------------------------------- HMC
+static int integrate(lgt_lattice* L, const lgt_action_params* ap, const lgt_hmc_params* hp, const double2* phi,
+                     lgt_solve_stats* tot, int* evals) {
+    const double eps = hp->tau / hp->n_steps;
+    lgt_solve_stats s;
+    auto K = [&](double e) -> int {
+        s = lgt_solve_stats{0, 0, 0.0, 0.0};
+        int r = kick(L, L->mom, e, ap, phi, &hp->md_solver, &s);
+        add_stats(tot, s);
+        ++*evals;
+        return r;
+    };
+    auto Uup = [&](double e) -> int {
+        CK(gauge_update_links(L->thin.U, L->thin.U12, L->mom, e, L->g, L->st));
+        return LGT_OK;
+    };
+    if (hp->integrator == LGT_LEAPFROG) {
+        TRY(K(0.5 * eps));
+        for (int i = 0; i < hp->n_steps; ++i) {
+            TRY(Uup(eps));
+            TRY(K(i + 1 < hp->n_steps ? eps : 0.5 * eps));
+        }
+    } else if (hp->integrator == LGT_OMELYAN2MN) {
+        const double lam = 0.1931833275037836;
+        TRY(K(lam * eps));
+        for (int i = 0; i < hp->n_steps; ++i) {
+            TRY(Uup(0.5 * eps));
+            TRY(K((1.0 - 2.0 * lam) * eps));
+            TRY(Uup(0.5 * eps));
+            TRY(K(i + 1 < hp->n_steps ? 2.0 * lam * eps : lam * eps));
+        }
+    } else {
+        return fail(LGT_EINVAL, "integrator %d", hp->integrator);
+    }
+    return LGT_OK;
+}
+
+extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, const lgt_hmc_params* hp,
+                                  uint64_t seed, uint32_t traj, lgt_hmc_result* res) {
+    if (!L || !hp || !res) return fail(LGT_EINVAL, "null argument");
+    TRY(check_action(ap));
+    if (hp->n_steps <= 0) return fail(LGT_EINVAL, "n_steps must be positive");
+    TRY(ensure_md(L));
+    TRY(ensure_solver(L));
+    memset(res, 0, sizeof *res);
+    const bool eo = ap->even_odd != 0;
+    CK(cudaMemcpyAsync(L->Ubak, L->thin.U, links64(L), cudaMemcpyDeviceToDevice, L->st));
+    CK(gauge_momenta_heatbath(L->mom, L->g, seed, traj, L->st));
+    TRY(lgt_kinetic_energy(L, (const double*)L->mom, &res->K_old));
+    double ps;
+    TRY(plaquette_sum(L, L->thin.U, &ps));
+    res->Sg_old = ap->beta * (6.0 * L->g.V - ps);
+    if (ap->fermions) {
+        // phi = M^+ xi on the (smeared) links, S_f(old) = xi^+ xi
+        CK(cudaMemsetAsync(L->xi, 0, spinor64_full(L), L->st));
+        CK(spinor_gaussian(L->xi, L->g, eo ? 0 : 2, seed, traj, FIELD_XI, L->st));
+        Links lk;
+        TRY(fermion_links(L, ap, &lk));
+        if (eo) TRY(dhat(L, lk, true, true, L->xi, L->phi, L->t, ap->kappa));
+        else TRY(dfull(L, lk, true, true, L->xi, L->phi, ap->kappa));
+        CK(blas_norm2(L->xi, eo ? L->g.Vh : 2 * L->g.Vh, L->g.Vh, true, red(L), 0, L->st));
+        TRY(sync_scalars(L));
+        res->Sf_old = L->hs->slot[0];
+    }
+    int evals = 0;
+    TRY(integrate(L, ap, hp, L->phi, &res->total, &evals));
+    res->force_evals = evals;
+    TRY(lgt_kinetic_energy(L, (const double*)L->mom, &res->K_new));
+    TRY(plaquette_sum(L, L->thin.U, &ps));
+    res->Sg_new = ap->beta * (6.0 * L->g.V - ps);
+    if (ap->fermions) {
+        Links lk;
+        TRY(fermion_links(L, ap, &lk));
+        lgt_solve_stats s = {0, 0, 0.0, 0.0};
+        TRY(pf_action_on(L, lk, ap, L->phi, &hp->action_solver, &res->Sf_new, &s));
+        add_stats(&res->total, s);
+    }
+    res->dH = (res->K_new + res->Sg_new + res->Sf_new) - (res->K_old + res->Sg_old + res->Sf_old);
+    if (!std::isfinite(res->dH)) return fail(LGT_ENAN, "non-finite Delta H");
+    uint32_t ctr[4] = {0, 0, traj, FIELD_METROPOLIS}, o[4];
+    philox_host(ctr, seed, o);
+    double u = ((double)(o[0] >> 5) * 67108864.0 + (double)(o[1] >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+    res->accepted = u < std::exp(-res->dH);
+    if (!res->accepted) {
+        CK(cudaMemcpyAsync(L->thin.U, L->Ubak, links64(L), cudaMemcpyDeviceToDevice, L->st));
+    }
+    CK(gauge_reunitarise(L->thin.U, L->thin.U12, L->g, L->st));
+    TRY(plaquette_sum(L, L->thin.U, &ps));
+    res->plaquette = ps / (6.0 * L->g.V);
+    return LGT_OK;
+}
+
+// ---------------------------------------------------------------- diagnostics
+extern "C" int lgt_measure_fp64_peak(double* flops, double* seconds) {
+    if (!flops) return fail(LGT_EINVAL, "null argument");
+    double secs = 0;
+    CK(fp64_peak_kernel_run(flops, &secs));
+    if (seconds) *seconds = secs;
+    return LGT_OK;
+}

@@ -1,0 +1,185 @@
+// lgt_blas.cu -- CG vector kernels: norms and inner products with FP64
+// accumulation and a deterministic two-level (block, then last-block) reduction,
+// the search-direction update, precision conversions and axpby.
+// A "field" of n sites is [n/Vh parities][components][Vh]; site t -> (t / Vh, t % Vh).
+#include "lgt_internal.h"
+
+namespace lgt {
+
+static inline int grid_for(long n) { return (int)((n + NT - 1) / NT); }
+
+cudaError_t blas_zero(void* f, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(f, 0, bytes, st); }
+
+template <bool FP64>
+__global__ void __launch_bounds__(NT) norm2_kernel(const void* a, int n, int Vh, RedArgs R, int slot) {
+    const int t = blockIdx.x * NT + threadIdx.x;
+    double acc = 0.0;
+    if (t < n) {
+        const int p = t / Vh, i = t - p * Vh;
+        if (FP64) {
+            const double2* b = (const double2*)a + (size_t)p * 12 * Vh + i;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) { double2 v = __ldg(b + (size_t)k * Vh); acc += v.x * v.x + v.y * v.y; }
+        } else {
+            const float4* b = (const float4*)a + (size_t)p * 6 * Vh + i;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                float4 v = __ldg(b + (size_t)k * Vh);
+                acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+            }
+        }
+    }
+    double bs = block_sum(acc);
+    grid_reduce(bs, R.partials, R.counter, R.s, RED_STORE, slot);
+}
+
+cudaError_t blas_norm2(const void* a, int n, int Vh, bool fp64, const RedArgs& R, int slot, cudaStream_t st) {
+    if (fp64) norm2_kernel<true><<<grid_for(n), NT, 0, st>>>(a, n, Vh, R, slot);
+    else norm2_kernel<false><<<grid_for(n), NT, 0, st>>>(a, n, Vh, R, slot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(NT) redot_kernel(const double2* a, const double2* b, int n, int Vh, RedArgs R,
+                                                   int slot) {
+    const int t = blockIdx.x * NT + threadIdx.x;
+    double acc = 0.0;
+    if (t < n) {
+        const int p = t / Vh, i = t - p * Vh;
+        const size_t o = (size_t)p * 12 * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 u = __ldg(a + o + (size_t)k * Vh), v = __ldg(b + o + (size_t)k * Vh);
+            acc += u.x * v.x + u.y * v.y;
+        }
+    }
+    double bs = block_sum(acc);
+    grid_reduce(bs, R.partials, R.counter, R.s, RED_STORE, slot);
+}
+
+cudaError_t blas_redot(const double2* a, const double2* b, int n, int Vh, const RedArgs& R, int slot,
+                       cudaStream_t st) {
+    redot_kernel<<<grid_for(n), NT, 0, st>>>(a, b, n, Vh, R, slot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// p = r + beta p over the flat element array; the last block moves done 1 -> 2
+__device__ __forceinline__ void xpby(double2& p, double2 r, double b) {
+    p.x = fma(b, p.x, r.x);
+    p.y = fma(b, p.y, r.y);
+}
+__device__ __forceinline__ void xpby(float4& p, float4 r, double bd) {
+    const float b = (float)bd;
+    p.x = fmaf(b, p.x, r.x);
+    p.y = fmaf(b, p.y, r.y);
+    p.z = fmaf(b, p.z, r.z);
+    p.w = fmaf(b, p.w, r.w);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) p_update_kernel(T* p, const T* r, long ne, RedArgs R) {
+    if (R.s->done >= 2) return;
+    const long e = (long)blockIdx.x * NT + threadIdx.x;
+    if (e < ne) {
+        T pv = p[e];
+        xpby(pv, __ldg(r + e), R.s->beta);
+        p[e] = pv;
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned prev = atomicAdd(R.counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        *R.counter = 0u;
+        if (R.s->done == 1) R.s->done = 2;
+    }
+}
+
+cudaError_t blas_cg_p_update(void* p, const void* r, int n, int Vh, bool fp64, const RedArgs& R,
+                             cudaStream_t st) {
+    (void)Vh;
+    if (fp64) {
+        long ne = (long)n * 12;
+        p_update_kernel<double2><<<grid_for(ne), NT, 0, st>>>((double2*)p, (const double2*)r, ne, R);
+    } else {
+        long ne = (long)n * 6;
+        p_update_kernel<float4><<<grid_for(ne), NT, 0, st>>>((float4*)p, (const float4*)r, ne, R);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+// FP64 [P][12][Vh] <-> FP32 [P][6][Vh]: float4 k of a site = double2 components 2k, 2k+1
+__global__ void __launch_bounds__(NT) d2f_kernel(float4* y, const double2* x, int n, int Vh) {
+    const long e = (long)blockIdx.x * NT + threadIdx.x;
+    if (e >= (long)n * 6) return;
+    const int site = (int)(e % n), k = (int)(e / n);
+    const int p = site / Vh, i = site - p * Vh;
+    const double2* b = x + (size_t)p * 12 * Vh + i;
+    double2 u = b[(size_t)(2 * k) * Vh], v = b[(size_t)(2 * k + 1) * Vh];
+    y[(size_t)p * 6 * Vh + (size_t)k * Vh + i] = make_float4((float)u.x, (float)u.y, (float)v.x, (float)v.y);
+}
+
+template <int MODE>  // 0: y = x, 1: y += x
+__global__ void __launch_bounds__(NT) f2d_kernel(double2* y, const float4* x, int n, int Vh) {
+    const long e = (long)blockIdx.x * NT + threadIdx.x;
+    if (e >= (long)n * 6) return;
+    const int site = (int)(e % n), k = (int)(e / n);
+    const int p = site / Vh, i = site - p * Vh;
+    float4 f = x[(size_t)p * 6 * Vh + (size_t)k * Vh + i];
+    double2* b = y + (size_t)p * 12 * Vh + i;
+    double2 u = make_double2(f.x, f.y), v = make_double2(f.z, f.w);
+    if (MODE == 1) {
+        double2 a = b[(size_t)(2 * k) * Vh], c = b[(size_t)(2 * k + 1) * Vh];
+        u.x += a.x; u.y += a.y; v.x += c.x; v.y += c.y;
+    }
+    b[(size_t)(2 * k) * Vh] = u;
+    b[(size_t)(2 * k + 1) * Vh] = v;
+}
+
+cudaError_t blas_d2f(float4* y, const double2* x, int n, int Vh, cudaStream_t st) {
+    d2f_kernel<<<grid_for((long)n * 6), NT, 0, st>>>(y, x, n, Vh);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t blas_add_f2d(double2* y, const float4* x, int n, int Vh, cudaStream_t st) {
+    f2d_kernel<1><<<grid_for((long)n * 6), NT, 0, st>>>(y, x, n, Vh);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t blas_f2d(double2* y, const float4* x, int n, int Vh, cudaStream_t st) {
+    f2d_kernel<0><<<grid_for((long)n * 6), NT, 0, st>>>(y, x, n, Vh);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(NT) axpby_kernel(double2* y, const double2* x, double a, double b, long ne) {
+    const long e = (long)blockIdx.x * NT + threadIdx.x;
+    if (e >= ne) return;
+    double2 u = __ldg(x + e), v = y[e];
+    v.x = fma(a, u.x, b * v.x);
+    v.y = fma(a, u.y, b * v.y);
+    y[e] = v;
+}
+
+cudaError_t blas_axpby(double2* y, const double2* x, double a, double b, int n, int Vh, cudaStream_t st) {
+    (void)Vh;
+    long ne = (long)n * 12;
+    axpby_kernel<<<grid_for(ne), NT, 0, st>>>(y, x, a, b, ne);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t blas_action_parts(const double2* phi, const double2* chi, const double2* eta, int n, int Vh,
+                              const RedArgs& R, cudaStream_t st) {
+    cudaError_t e = blas_redot(phi, chi, n, Vh, R, 0, st);
+    if (e != cudaSuccess) return e;
+    return blas_norm2(eta, n, Vh, true, R, 1, st);
+}
+
+}  // namespace lgt

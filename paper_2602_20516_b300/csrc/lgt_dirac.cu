@@ -1,0 +1,207 @@
+// lgt_dirac.cu -- even-odd Wilson hopping term H (and H^+ = g5 H g5) on sm_103a.
+//
+// One thread per output site.  For each of the 8 neighbours the 4-spinor is
+// projected to a 2-spinor with (1 -/+ g_mu), multiplied by U or U^+ (3x3 colour),
+// and reconstructed into the accumulator; the antiperiodic time sign multiplies
+// the projected spinor.  FP64 links are 18 reals (9 x double2, one 128-bit load
+// each); FP32 links are the first two rows (3 x float4) with row 3 rebuilt as
+// conj(row1 x row2).  Spinor components of one parity are contiguous per
+// component (site-major SoA), so every load and store is a coalesced 128-bit access.
+//
+// Epilogues fuse the CG vector work into the last hop of an operator
+// application: xpay (y + a H in), its squared norm, and the CG update
+// x += alpha p, r -= alpha A p with |r|^2, or the true residual b - A x.
+#include "lgt_internal.h"
+#include "lgt_spin.cuh"
+
+namespace lgt {
+
+template <typename R> struct Prec;
+template <> struct Prec<double> {
+    using T = double2;
+    using S = SpinorD;
+    static __device__ __forceinline__ mat3<double> link(const void* U, int Vh, int p, int mu, int i) {
+        return load_link((const double2*)U, Vh, p, mu, i);
+    }
+};
+template <> struct Prec<float> {
+    using T = float4;
+    using S = SpinorF;
+    static __device__ __forceinline__ mat3<float> link(const void* U, int Vh, int p, int mu, int i) {
+        return load_link12((const float4*)U, Vh, p, mu, i);
+    }
+};
+
+// colour multiply of both half-spinor rows by M or M^+
+template <bool DAGM, typename R>
+__device__ __forceinline__ void mult(const mat3<R>& M, const cx<R> (&h)[2][3], cx<R> (&uh)[2][3]) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<R> s = {0, 0};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) s = DAGM ? cmadc(s, M.e[b][a], h[j][b]) : cmad(s, M.e[a][b], h[j][b]);
+            uh[j][a] = s;
+        }
+}
+
+template <int MU, int SF, int SB, typename R>
+__device__ __forceinline__ void hop_dir(const HopArgs& A, int p, int lex, const int (&x)[4],
+                                        int i, cx<R> (&out)[4][3]) {
+    using P = Prec<R>;
+    const int Vh = A.g.Vh;
+    const typename P::T* in = (const typename P::T*)A.in[1 - p];
+    // forward: b (1 + SF g) U_mu(x) psi(x+mu)
+    {
+        int j = nb_lex(A.g, lex, x, MU, +1) >> 1;
+        typename P::S s = load_spinor(in, Vh, j);
+        cx<R> h[2][3], uh[2][3];
+        project<MU, SF>(s.c, h);
+        if (MU == 3 && x[3] == A.g.L[3] - 1) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { h[0][c] = -h[0][c]; h[1][c] = -h[1][c]; }
+        }
+        mat3<R> M = P::link(A.U, Vh, p, MU, i);
+        mult<false>(M, h, uh);
+        accumulate<MU, SF>(out, uh);
+    }
+    // backward: b (1 + SB g) U_mu(x-mu)^+ psi(x-mu)
+    {
+        int j = nb_lex(A.g, lex, x, MU, -1) >> 1;
+        typename P::S s = load_spinor(in, Vh, j);
+        cx<R> h[2][3], uh[2][3];
+        project<MU, SB>(s.c, h);
+        if (MU == 3 && x[3] == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { h[0][c] = -h[0][c]; h[1][c] = -h[1][c]; }
+        }
+        mat3<R> M = P::link(A.U, Vh, 1 - p, MU, j);
+        mult<true>(M, h, uh);
+        accumulate<MU, SB>(out, uh);
+    }
+}
+
+template <typename R> __device__ __forceinline__ double sq(const cx<R> (&v)[4][3]) {
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc += (double)v[a][c].r * (double)v[a][c].r + (double)v[a][c].i * (double)v[a][c].i;
+    return acc;
+}
+
+template <typename R, bool DAG, int EPI>
+__global__ void __launch_bounds__(NT) hop_kernel(HopArgs A) {
+    using P = Prec<R>;
+    using T = typename P::T;
+    if (A.skip && A.s->done >= 1) return;
+    const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
+    const int t = blockIdx.x * NT + threadIdx.x;
+    const bool valid = t < n;
+    double red = 0.0;
+    if (valid) {
+        int p, i;
+        if (A.parity == 2) { p = t >= A.g.Vh; i = t - p * A.g.Vh; }
+        else { p = A.parity; i = t; }
+        int x[4];
+        int lex = eo_coords(A.g, p, i, x);
+        cx<R> out[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[a][c] = {0, 0};
+        constexpr int SF = DAG ? +1 : -1;
+        constexpr int SB = -SF;
+        hop_dir<0, SF, SB, R>(A, p, lex, x, i, out);
+        hop_dir<1, SF, SB, R>(A, p, lex, x, i, out);
+        hop_dir<2, SF, SB, R>(A, p, lex, x, i, out);
+        hop_dir<3, SF, SB, R>(A, p, lex, x, i, out);
+        const R a = (R)A.a;
+        const int Vh = A.g.Vh;
+        if (EPI == EPI_HOP) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[s][c] = a * out[s][c];
+            typename P::S o;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o.c[s][c] = out[s][c];
+            store_spinor((T*)A.out[p], Vh, i, o);
+        } else {
+            typename P::S yv = load_spinor((const T*)A.y[p], Vh, i);
+            typename P::S o;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    o.c[s][c].r = fma(a, out[s][c].r, yv.c[s][c].r);
+                    o.c[s][c].i = fma(a, out[s][c].i, yv.c[s][c].i);
+                }
+            if (EPI == EPI_XPAY || EPI == EPI_XPAY_NORM) {
+                store_spinor((T*)A.out[p], Vh, i, o);
+                if (EPI == EPI_XPAY_NORM) red = sq<R>(o.c);
+            } else if (EPI == EPI_CG) {
+                // o = A p at this site: x += alpha p, r -= alpha A p, red = |r|^2
+                const R alpha = (R)A.s->alpha;
+                typename P::S xv = load_spinor((const T*)A.x[p], Vh, i);
+                typename P::S rv = load_spinor((const T*)A.r[p], Vh, i);
+                typename P::S pv = load_spinor((const T*)A.pv[p], Vh, i);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        xv.c[s][c].r = fma(alpha, pv.c[s][c].r, xv.c[s][c].r);
+                        xv.c[s][c].i = fma(alpha, pv.c[s][c].i, xv.c[s][c].i);
+                        rv.c[s][c].r = fma(-alpha, o.c[s][c].r, rv.c[s][c].r);
+                        rv.c[s][c].i = fma(-alpha, o.c[s][c].i, rv.c[s][c].i);
+                    }
+                store_spinor((T*)A.x[p], Vh, i, xv);
+                store_spinor((T*)A.r[p], Vh, i, rv);
+                red = sq<R>(rv.c);
+            } else {  // EPI_RESID: out = b - A x, b in pv
+                typename P::S bv = load_spinor((const T*)A.pv[p], Vh, i);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) o.c[s][c] = bv.c[s][c] - o.c[s][c];
+                store_spinor((T*)A.out[p], Vh, i, o);
+                red = sq<R>(o.c);
+            }
+        }
+    }
+    if (EPI == EPI_XPAY_NORM || EPI == EPI_CG || EPI == EPI_RESID) {
+        double b = block_sum(red);
+        grid_reduce(b, A.partials, A.counter, A.s, A.red_op, A.red_slot);
+    }
+}
+
+template <typename R, bool DAG>
+static cudaError_t launch_epi(const HopArgs& A, int epi, cudaStream_t st) {
+    const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
+    const int grid = (n + NT - 1) / NT;
+    switch (epi) {
+    case EPI_HOP: hop_kernel<R, DAG, EPI_HOP><<<grid, NT, 0, st>>>(A); break;
+    case EPI_XPAY: hop_kernel<R, DAG, EPI_XPAY><<<grid, NT, 0, st>>>(A); break;
+    case EPI_XPAY_NORM: hop_kernel<R, DAG, EPI_XPAY_NORM><<<grid, NT, 0, st>>>(A); break;
+    case EPI_CG: hop_kernel<R, DAG, EPI_CG><<<grid, NT, 0, st>>>(A); break;
+    case EPI_RESID: hop_kernel<R, DAG, EPI_RESID><<<grid, NT, 0, st>>>(A); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st) {
+    if (fp64) return dagger ? launch_epi<double, true>(A, epi, st) : launch_epi<double, false>(A, epi, st);
+    return dagger ? launch_epi<float, true>(A, epi, st) : launch_epi<float, false>(A, epi, st);
+}
+
+int hop_grid(const Geom& g, int parity) {
+    const int n = (parity == 2) ? 2 * g.Vh : g.Vh;
+    return (n + NT - 1) / NT;
+}
+
+}  // namespace lgt

@@ -1,0 +1,99 @@
+// lgt_force.cu -- Wilson pseudofermion force on sm_103a.
+//
+// delta S_f = -2 Re[Y^+ (delta D) X] (Eq. S3.12, with chi -> X and eta -> Y; for
+// the even-odd action X = (chi_e, kappa H_oe chi_e), Y = (eta_e, kappa (H^+)_oe eta_e)).
+// U_mu(x) enters Y^+ H X twice, giving the two colour matrices
+//   P1 = b sum_s [(1 - g_mu) X(x+mu)]_s Y(x)_s^+ ,  P2 = b sum_s X(x)_s [(1 + g_mu) Y(x+mu)]_s^+ .
+// Because (1 -+ g)/2 is a Hermitian projector of rank 2, each sum is two outer
+// products of projected colour vectors: sum_s (P X)_s (Y_s)^+ = sum_j h_j(X) h_j(Y)^+.
+// Lie form:  W = U P1 - P2 U^+,  F_a = -2 kappa Im tr(T^a W)  (= i kappa P[W], Eq. 9);
+// G form:    G = dS/dReU + i dS/dImU = 2 kappa (P1^+ + P2)      (Eq. S2.11).
+// One thread per link; X(x), Y(x) are re-read per direction through L1/L2.
+#include "lgt_internal.h"
+#include "lgt_spin.cuh"
+
+namespace lgt {
+
+static inline int grid_for(long n) { return (int)((n + NT - 1) / NT); }
+
+template <int MU>
+__device__ __forceinline__ void outer_terms(const SpinorD& Xx, const SpinorD& Yx, const SpinorD& Xy,
+                                            const SpinorD& Yy, double b, dmat& P1, dmat& P2) {
+    dcx h[2][3], k[2][3];
+    project<MU, -1>(Xy.c, h);
+    project<MU, -1>(Yx.c, k);
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            dcx s = {0, 0};
+            s = cmad_cb(s, h[0][a], k[0][c]);
+            s = cmad_cb(s, h[1][a], k[1][c]);
+            P1.e[a][c] = b * s;
+        }
+    project<MU, +1>(Xx.c, h);
+    project<MU, +1>(Yy.c, k);
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            dcx s = {0, 0};
+            s = cmad_cb(s, h[0][a], k[0][c]);
+            s = cmad_cb(s, h[1][a], k[1][c]);
+            P2.e[a][c] = b * s;
+        }
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(NT) fermion_force_kernel(const double2* U, const double2* X, const double2* Y,
+                                                           Geom g, double kappa, double coef, int keep,
+                                                           double2* out) {
+    const long t = (long)blockIdx.x * NT + threadIdx.x;
+    if (t >= 8L * g.Vh) return;
+    const int mu = (int)(t / (2 * g.Vh));
+    const int rem = (int)(t - (long)mu * 2 * g.Vh);
+    const int p = rem >= g.Vh, i = rem - p * g.Vh;
+    int x[4];
+    const int lex = eo_coords(g, p, i, x);
+    const int j = nb_lex(g, lex, x, mu, +1) >> 1;
+    const double b = (mu == 3 && x[3] == g.L[3] - 1) ? -1.0 : 1.0;
+    const size_t hf = (size_t)12 * g.Vh;
+    SpinorD Xx = load_spinor(X + p * hf, g.Vh, i), Yx = load_spinor(Y + p * hf, g.Vh, i);
+    SpinorD Xy = load_spinor(X + (1 - p) * hf, g.Vh, j), Yy = load_spinor(Y + (1 - p) * hf, g.Vh, j);
+    dmat P1, P2;
+    switch (mu) {
+    case 0: outer_terms<0>(Xx, Yx, Xy, Yy, b, P1, P2); break;
+    case 1: outer_terms<1>(Xx, Yx, Xy, Yy, b, P1, P2); break;
+    case 2: outer_terms<2>(Xx, Yx, Xy, Yy, b, P1, P2); break;
+    default: outer_terms<3>(Xx, Yx, Xy, Yy, b, P1, P2); break;
+    }
+    if (FORM == 0) {
+        dmat Um = load_link(U, g.Vh, p, mu, i);
+        dmat W = mul(Um, P1);
+        dmat B = mul_nd(P2, Um);
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) W.e[a][c] = W.e[a][c] - B.e[a][c];
+        double cl[8], f[8];
+        lie_im_tr(W, cl);
+        if (keep) load_mom(out, g.Vh, p, mu, i, f);
+        const double s = -coef * kappa;
+        for (int a = 0; a < 8; ++a) f[a] = (keep ? f[a] : 0.0) + s * cl[a];
+        store_mom(out, g.Vh, p, mu, i, f);
+    } else {
+        dmat G;
+        if (keep) G = load_link(out, g.Vh, p, mu, i);
+        const double s = 2.0 * kappa * coef;
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                dcx v = s * (conj(P1.e[c][a]) + P2.e[a][c]);
+                G.e[a][c] = keep ? G.e[a][c] + v : v;
+            }
+        store_link(out, g.Vh, p, mu, i, G);
+    }
+}
+
+cudaError_t fermion_force(const double2* U, const double2* X, const double2* Y, const Geom& g, double kappa,
+                          double coef, int keep, int form, double2* out, cudaStream_t st) {
+    if (form == 0) fermion_force_kernel<0><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, X, Y, g, kappa, coef, keep, out);
+    else fermion_force_kernel<1><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, X, Y, g, kappa, coef, keep, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace lgt

@@ -1,0 +1,107 @@
+// lgt_internal.h -- declarations shared by the liblgt translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lgt_common.cuh"
+
+namespace lgt {
+
+enum Epilogue { EPI_HOP = 0, EPI_XPAY = 1, EPI_XPAY_NORM = 2, EPI_CG = 3, EPI_RESID = 4 };
+
+// Arguments of one hopping-term launch.  Field pointers are half fields indexed
+// by parity (double2 [12][Vh] for FP64, float4 [6][Vh] for FP32); the input of
+// output parity p is in[1-p].  parity = 0, 1 or 2 (both parities in one launch).
+struct HopArgs {
+    const void* U;        // FP64 links (double2) or FP32 two-row links (float4)
+    const void* in[2];
+    void* out[2];
+    const void* y[2];     // xpay addend (same parity as the output)
+    void* x[2];           // EPI_CG: solution
+    void* r[2];           // EPI_CG: residual
+    const void* pv[2];    // EPI_CG: search direction;  EPI_RESID: right-hand side
+    double a;             // coefficient of H in
+    Geom g;
+    int parity;
+    Scalars* s;           // solver scalars (nullptr: no skip test, no reduction)
+    double* partials;
+    unsigned* counter;
+    int red_op, red_slot;
+    int skip;             // 1: return at once when the solver scalars say done
+};
+
+cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st);
+int hop_grid(const Geom& g, int parity);
+
+// launch counting (per host thread)
+void count_launch();
+
+// ---------------------------------------------------------------- BLAS (lgt_blas.cu)
+struct RedArgs {
+    Scalars* s;
+    double* partials;
+    unsigned* counter;
+};
+// all operate on n "rows" = sites; FP64 rows are 12 double2, FP32 rows 6 float4
+cudaError_t blas_zero(void* f, size_t bytes, cudaStream_t st);
+// |a|^2 (FP64 accumulate) -> slot
+cudaError_t blas_norm2(const void* a, int n, int Vh, bool fp64, const RedArgs& R, int slot, cudaStream_t st);
+// Re <a, b> -> slot   (FP64 fields)
+cudaError_t blas_redot(const double2* a, const double2* b, int n, int Vh, const RedArgs& R, int slot, cudaStream_t st);
+// p = r + beta p  (beta from scalars), skipped once done >= 2; marks done 1 -> 2
+cudaError_t blas_cg_p_update(void* p, const void* r, int n, int Vh, bool fp64, const RedArgs& R, cudaStream_t st);
+// y = x (FP64 -> FP32 rounding) / y64 += x32 / y = x
+cudaError_t blas_d2f(float4* y, const double2* x, int n, int Vh, cudaStream_t st);
+cudaError_t blas_add_f2d(double2* y, const float4* x, int n, int Vh, cudaStream_t st);
+cudaError_t blas_f2d(double2* y, const float4* x, int n, int Vh, cudaStream_t st);
+// y = a x + b y  (FP64)
+cudaError_t blas_axpby(double2* y, const double2* x, double a, double b, int n, int Vh, cudaStream_t st);
+// S_f = 2 Re<phi, chi> - |eta|^2 pieces: slot0 = Re<phi,chi>, slot1 = |eta|^2 (single kernel)
+cudaError_t blas_action_parts(const double2* phi, const double2* chi, const double2* eta, int n, int Vh,
+                              const RedArgs& R, cudaStream_t st);
+
+// ---------------------------------------------------------------- gauge (lgt_gauge.cu)
+cudaError_t gauge_pack_links(double2* U, float4* U12, const double2* canon, const Geom& g, cudaStream_t st);
+cudaError_t gauge_unpack_links(double* canon, const double2* U, const Geom& g, cudaStream_t st);
+cudaError_t gauge_pack_field(double2* F, const double2* canon, const Geom& g, cudaStream_t st);
+cudaError_t gauge_unpack_field(double* canon, const double2* F, const Geom& g, cudaStream_t st);
+cudaError_t gauge_unit(double2* U, float4* U12, const Geom& g, cudaStream_t st);
+cudaError_t gauge_random(double2* U, float4* U12, const Geom& g, uint64_t seed, double alpha, cudaStream_t st);
+cudaError_t gauge_make12(float4* U12, const double2* U, const Geom& g, cudaStream_t st);
+cudaError_t gauge_reunitarise(double2* U, float4* U12, const Geom& g, cudaStream_t st);
+cudaError_t gauge_plaquette(const double2* U, const Geom& g, const RedArgs& R, int slot, cudaStream_t st);
+// mom (or F) update from the gauge force: F_G -> out = keep*out + coef*F (Lie or G form)
+cudaError_t gauge_force(const double2* U, const Geom& g, double beta, double coef, int keep, int form,
+                        double2* out, cudaStream_t st);
+// U <- exp(i eps P) U, refresh FP32 copy
+cudaError_t gauge_update_links(double2* U, float4* U12, const double2* mom, double eps, const Geom& g,
+                               cudaStream_t st);
+cudaError_t gauge_momenta_heatbath(double2* mom, const Geom& g, uint64_t seed, uint32_t traj, cudaStream_t st);
+cudaError_t gauge_kinetic(const double2* mom, const Geom& g, const RedArgs& R, int slot, cudaStream_t st);
+cudaError_t gauge_kick(double2* mom, const double2* F, double eps, const Geom& g, cudaStream_t st);
+cudaError_t spinor_gaussian(double2* f, const Geom& g, int parity, uint64_t seed, uint32_t traj, uint32_t field,
+                            cudaStream_t st);
+cudaError_t spinor_pack(void* field, const double2* canon, const Geom& g, int parity, bool fp64, cudaStream_t st);
+cudaError_t spinor_unpack(double2* canon, const void* field, const Geom& g, int parity, bool fp64, cudaStream_t st);
+cudaError_t mom_pack(double2* mom, const double* canon, const Geom& g, cudaStream_t st);
+cudaError_t mom_unpack(double* canon, const double2* mom, const Geom& g, cudaStream_t st);
+// Lie components of a G-form field: F_a = Re tr(G^+ i T^a U)
+cudaError_t grad_to_lie(double2* F, const double2* G, const double2* U, const Geom& g, cudaStream_t st);
+
+// ---------------------------------------------------------------- fermion force (lgt_force.cu)
+// X, Y: full FP64 fields [2][12][Vh].  form 0: out = keep*out + coef*F (Lie, momentum
+// layout);  form 1: out = keep*out + coef*G (G-form layout).
+cudaError_t fermion_force(const double2* U, const double2* X, const double2* Y, const Geom& g, double kappa,
+                          double coef, int keep, int form, double2* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- stout (lgt_stout.cu)
+cudaError_t stout_forward(const double2* Uin, double2* Uout, const Geom& g, double rho, cudaStream_t st);
+// Gin = adjoint of one level applied to Gout, for the level whose input is Uin
+cudaError_t stout_backward(const double2* Uin, const double2* Gout, double2* Gin, double2* scratch, const Geom& g,
+                           double rho, cudaStream_t st);
+
+// ---------------------------------------------------------------- diagnostics
+cudaError_t fp64_peak_kernel_run(double* flops, double* seconds);
+
+}  // namespace lgt
