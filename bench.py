@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: molecular-dynamics force evaluations per second on a 32^3 x 64
+lattice (two-flavour Wilson fermions, even-odd pseudofermion action, beta 5.8,
+kappa 0.156, seeded links exp(i 0.5 H)), mixed-precision path vs FP64 path,
+Wilson-hop HBM bandwidth, end-to-end rate with host buffers, and the FP64 CPU
+oracle as the baseline.
+
+One step = one MD update: a force evaluation from scratch (CG on Dhat^+ Dhat from a
+zero guess to tol 1e-10, X/Y vectors, fermion and gauge force fused into the
+momentum kick) followed by the link update U <- exp(i eps P) U.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --kernel hop32|hop64 [--reps R]   # a few hop launches, for ncu
+
+Prints one JSON line (rank 0).  With torchrun each rank runs an independent
+replica (no collective in the data path; weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "force evals/s + Dslash HBM GB/s at 32^3×64, mixed vs FP64; p99 solve latency"
+UNIT = "force evals/s"
+DIMS = (32, 32, 32, 64)
+BETA, KAPPA, ALPHA, TOL, DELTA = 5.8, 0.156, 0.5, 1e-10, 0.1
+EPS = 1.0 / 20
+SEED = 4
+# FP64 CG iterations of this workload (Dhat^+Dhat, tol 1e-10, zero guess): used only to
+# scale the oracle's capped-CG sample in the reference arm (the default arm uses the
+# count it measures in the same run)
+CG_ITERS_FP64 = 146
+# algorithmic (compulsory) bytes per output site of one even-odd hop:
+# 8 links + 1 input spinor + 1 output spinor (each array touched once)
+HOP_BYTES = {"fp32": 8 * 48 + 96 + 96, "fp64": 8 * 144 + 192 + 192}
+HOP_FLOPS = 1320
+# ncu DRAM traffic (read + write) of one FP32 hop launch at 32^3 x 64, and the hash of
+# the kernel sources it was taken from (traffic is reported as null once they change)
+NCU_TRAFFIC = {"bytes": 595180544,
+               "sources_sha256": "433e5646e12b17044d29d6cde82935dae3fb2a69faac405135981dbb89a3f739"}
+HOP_SOURCES = ["paper_2602_20516_b300/csrc/lgt_dirac.cu", "paper_2602_20516_b300/csrc/lgt_spin.cuh",
+               "paper_2602_20516_b300/csrc/lgt_common.cuh"]
+
+
+def hop_sources_hash():
+    h = hashlib.sha256()
+    for f in HOP_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), "of measured"
+    return 6400.0, "of fallback"
+
+
+def config_block(args):
+    return {"workload": "32^3x64 Nf=2 Wilson even-odd MD step: mixed CG (FP32 inner, FP64 reliable "
+                        "updates) tol 1e-10 from zero guess + fermion/gauge force fused into the momentum "
+                        "kick + link update",
+            "lattice": list(DIMS), "beta": BETA, "kappa": KAPPA, "alpha": ALPHA, "tol": TOL,
+            "delta": DELTA, "seed": SEED, "eps": EPS,
+            "l2": "inputs larger than L2 (FP64 links 1.21 GB + FP32 links 0.40 GB per replica)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(cg_iters, reps=1):
+    """Time the FP64 oracle on a bounded sample of one MD step at 32^3 x 64 and
+    scale it to one force evaluation: CG capped at 2 iterations (3 operator
+    applications with its residual check; per-iteration cost = t/3), the X/Y hops,
+    gauge force, fermion force and link update."""
+    import numpy as np
+    import oracle as O
+    d = DIMS
+    U = O.random_links(d, SEED, ALPHA)
+    phi = O.gaussian_spinor(d, SEED, 0, O.FIELD_SOURCE, 1)
+    mom = O.gaussian_momenta(d, SEED, 0)
+    est = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.cg(d, U, KAPPA, phi, eo=True, tol=TOL, max_iter=2)
+        t_cg = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        X = O.hop(d, U, phi, out_mask=2)
+        Y = O.hop(d, U, X, out_mask=1)
+        O.hop(d, U, Y, out_mask=2, dagger=True)
+        O.gauge_force(d, U, BETA)
+        O.fermion_force_xy(d, U, KAPPA, X, Y)
+        O.update_links(d, U, mom, EPS)
+        t_rest = time.perf_counter() - t1
+        est.append(t_cg / 3.0 * (cg_iters + 1) + t_rest)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"oracle (C, OpenMP) on 32^3x64: CG capped at 2 iterations scaled to {cg_iters} "
+              f"iterations (+1 residual apply), plus X/Y hops, gauge force, fermion force, link update")
+    return est, cores, sample
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2602_20516_b300 import lgt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    lat = lgt.Lattice(DIMS)
+    lat.random_links(SEED + rank, ALPHA)
+    phi = lat.gaussian_spinor(SEED + rank, 0, lgt.FIELD_SOURCE, lgt.EVEN)
+    mom = lat.gaussian_momenta(SEED + rank, 0)
+    ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True)
+    stream = torch.cuda.current_stream()
+
+    def step(sp, stats):
+        s = lat.md_update(mom, EPS, lgt.UPDATE_P, ap, phi, sp)
+        lat.md_update(mom, EPS, lgt.UPDATE_U)
+        stats.append(s)
+
+    def timed(sp, K, W, kernel_timing=False, clocks=None):
+        st = []
+        for _ in range(W):
+            step(sp, st)
+        st.clear()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        lgt.launch_count(reset=True)
+        if kernel_timing:
+            lgt.kernel_timing_start(65536)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step(sp, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        launches = lgt.launch_count()
+        kt = lgt.kernel_timing_stop() if kernel_timing else None
+        clk = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        return ms, st, launches, kt, clk
+
+    K, W = args.steps, args.warmup
+    sp_mixed = lgt.solver("mixed", tol=TOL, delta=DELTA)
+    sampler = ClockSampler(local)
+    ms, st, launches, kt, clk = timed(sp_mixed, K, W, kernel_timing=True, clocks=sampler)
+    ms_max = max_over_ranks(ms)
+    value = world * K / (ms_max / 1e3)
+    iters = statistics.mean(s["iters"] for s in st)
+    rel = statistics.mean(s["reliable_updates"] for s in st)
+
+    # FP64 path, same workload
+    K64 = max(1, min(K, args.fp64_steps))
+    ms64, st64, _, kt64, _ = timed(lgt.solver("fp64", tol=TOL), K64, 1, kernel_timing=True)
+    ms64 = max_over_ranks(ms64)
+    value64 = world * K64 / (ms64 / 1e3)
+    iters64 = statistics.mean(s["iters"] for s in st64)
+
+    # dominant kernel: the FP32 hop, timed with CUDA events on its stream inside the timed region
+    ms32_sum, n32, _, _ = kt
+    hop32_ms = ms32_sum / max(n32, 1)
+    achieved = HOP_BYTES["fp32"] * lat.Vh / (hop32_ms * 1e-3) / 1e9
+    _, _, ms64_sum, n64 = kt64
+    hop64_ms = ms64_sum / max(n64, 1)
+    fp64_peak = lgt.measure_fp64_peak()
+    peak, peak_kind = measured_peaks()
+    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources_sha256"] == hop_sources_hash() else None
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Uh = lat.get_links().cpu().pin_memory()
+        phic = lat.unpack_spinor(phi, lgt.EVEN, lgt.FP64).cpu().pin_memory()
+        Fh = torch.empty((lat.V, 4, 8), dtype=torch.float64).pin_memory()
+        Ud = torch.empty_like(Uh, device="cuda")
+        phid = torch.empty_like(phic, device="cuda")
+        Ke = max(1, min(K, args.e2e_steps))
+
+        def e2e_step():
+            Ud.copy_(Uh, non_blocking=True)
+            lat.set_links(Ud)
+            phid.copy_(phic, non_blocking=True)
+            pf = lat.pack_spinor(phid, lgt.EVEN, lgt.FP64)
+            F, _ = lat.force(ap, pf, sp_mixed)
+            Fh.copy_(lat.unpack_momenta(F), non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        te = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * Ke / te, "unit": UNIT,
+               "h2d_bytes_per_step": Uh.numel() * 16 + phic.numel() * 16,
+               "d2h_bytes_per_step": Fh.numel() * 8,
+               "steps": Ke, "step": "upload canonical links + phi (pinned host), force (mixed CG), "
+                                   "download canonical force"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        est, cores, sample = oracle_sample(int(round(iters64)), reps=1)
+        cpu = {"value": 1.0 / statistics.mean(est), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+           "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64 (mixed)", "data": "synthetic: seeded links exp(i 0.5 H), Gaussian pseudofermion",
+           "config": config_block(args),
+           "cg_iters_per_step": iters, "reliable_updates_per_step": rel,
+           "fp64": {"value": value64, "ms_per_step": ms64 / K64, "steps": K64, "cg_iters_per_step": iters64,
+                    "mixed_speedup": value / value64},
+           "dslash": {"fp32_hop_us": hop32_ms * 1e3, "fp32_hop_GBs_compulsory": achieved,
+                      "fp32_hop_launches": n32, "fp64_hop_us": hop64_ms * 1e3,
+                      "fp64_hop_TFLOPs": HOP_FLOPS * lat.Vh / (hop64_ms * 1e-3) / 1e12,
+                      "fp64_peak_TFLOPs_measured": fp64_peak / 1e12,
+                      "fp64_hop_frac_of_fp64_peak": HOP_FLOPS * lat.Vh / (hop64_ms * 1e-3) / fp64_peak},
+           "roofline": {"bound": "hbm", "kernel": "hop_kernel<float> (FP32 Wilson hop, two-row links)",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_source": peak_kind,
+                        "traffic": traffic, "algorithmic_bytes_per_launch": HOP_BYTES["fp32"] * lat.Vh},
+           "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    est, cores, sample = oracle_sample(CG_ITERS_FP64, reps=W + K)
+    timed = est[W:]
+    value = len(timed) / sum(timed)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": K, "warmup": W, "ms_per_step": 1e3 * statistics.mean(timed), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (same seeds)",
+           "config": config_block(args),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- single-kernel mode (ncu)
+def run_kernel(args):
+    import torch
+    from paper_2602_20516_b300 import lgt
+    lat = lgt.Lattice(DIMS)
+    lat.random_links(SEED, ALPHA)
+    prec = lgt.FP32 if args.kernel == "hop32" else lgt.FP64
+    src = lat.pack_spinor(lat.unpack_spinor(lat.gaussian_spinor(SEED, 0, lgt.FIELD_SOURCE, lgt.ODD),
+                                            lgt.ODD, lgt.FP64), lgt.ODD, prec)
+    out = lat.spinor_field(lgt.EVEN, prec)
+    for _ in range(args.reps):
+        lat.dslash(src, lgt.OP_HOP, lgt.EVEN, False, 0.0, prec, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": args.kernel, "launches": args.reps, "lattice": list(DIMS)}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kernel", choices=["hop32", "hop64"])
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "ours" and not args.kernel:
+        args.warmup = max(3, args.warmup)   # timing rule: at least 3 untimed steps
+    if args.kernel:
+        run_kernel(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

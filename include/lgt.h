@@ -227,6 +227,12 @@ int lgt_hmc_trajectory(lgt_lattice_t lat, const lgt_action_params *ap,
 /* ------------------------------------------------------------------ diagnostics */
 /* Peak FP64 FMA throughput of this device (dependent FMA chains), in FLOP/s. */
 int lgt_measure_fp64_peak(double *flops, double *seconds);
+/* CUDA-event timing of the Wilson hop launches: start arms up to max_launches
+ * event pairs (recorded on the launching stream around each hop launch of any
+ * handle); stop waits for them and returns the summed durations (ms) and counts
+ * of the FP32 and FP64 hop launches.  Process-wide; not thread safe. */
+int lgt_kernel_timing_start(int max_launches);
+int lgt_kernel_timing_stop(double *ms_fp32, int64_t *n_fp32, double *ms_fp64, int64_t *n_fp64);
 /* Kernel launches the library enqueued on this thread since the last reset. */
 int64_t lgt_launch_count(int reset);
 

@@ -20,8 +20,25 @@ using namespace lgt;
 static thread_local std::string g_err = "";
 static thread_local int64_t g_launches = 0;
 
+// hop-kernel timing: event pairs recorded around each hop launch while enabled
+struct KernelTiming {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    size_t used = 0;
+};
+static KernelTiming g_kt;
+
 namespace lgt {
 void count_launch() { ++g_launches; }
+bool kernel_timing_slot(int kind, cudaEvent_t* a, cudaEvent_t* b) {
+    if (!g_kt.on || g_kt.used + 2 > g_kt.ev.size()) return false;
+    *a = g_kt.ev[g_kt.used];
+    *b = g_kt.ev[g_kt.used + 1];
+    g_kt.kind[g_kt.used / 2] = kind;
+    g_kt.used += 2;
+    return true;
+}
 }
 
 static int fail(int code, const char* fmt, ...) {
@@ -868,6 +885,40 @@ extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, 
 }
 
 // ---------------------------------------------------------------- diagnostics
+extern "C" int lgt_kernel_timing_start(int max_launches) {
+    if (max_launches <= 0 || max_launches > (1 << 20)) return fail(LGT_EINVAL, "max_launches %d", max_launches);
+    size_t need = 2 * (size_t)max_launches;
+    while (g_kt.ev.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        g_kt.ev.push_back(e);
+    }
+    g_kt.kind.assign(max_launches, 0);
+    g_kt.used = 0;
+    g_kt.on = true;
+    return LGT_OK;
+}
+
+extern "C" int lgt_kernel_timing_stop(double* ms_fp32, int64_t* n_fp32, double* ms_fp64, int64_t* n_fp64) {
+    g_kt.on = false;
+    double ms[2] = {0.0, 0.0};
+    int64_t n[2] = {0, 0};
+    for (size_t k = 0; k + 1 < g_kt.used; k += 2) {
+        CK(cudaEventSynchronize(g_kt.ev[k + 1]));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, g_kt.ev[k], g_kt.ev[k + 1]));
+        int kind = g_kt.kind[k / 2];
+        ms[kind] += t;
+        n[kind] += 1;
+    }
+    g_kt.used = 0;
+    if (ms_fp32) *ms_fp32 = ms[0];
+    if (n_fp32) *n_fp32 = n[0];
+    if (ms_fp64) *ms_fp64 = ms[1];
+    if (n_fp64) *n_fp64 = n[1];
+    return LGT_OK;
+}
+
 extern "C" int lgt_measure_fp64_peak(double* flops, double* seconds) {
     if (!flops) return fail(LGT_EINVAL, "null argument");
     double secs = 0;

@@ -195,8 +195,14 @@ static cudaError_t launch_epi(const HopArgs& A, int epi, cudaStream_t st) {
 }
 
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st) {
-    if (fp64) return dagger ? launch_epi<double, true>(A, epi, st) : launch_epi<double, false>(A, epi, st);
-    return dagger ? launch_epi<float, true>(A, epi, st) : launch_epi<float, false>(A, epi, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = kernel_timing_slot(fp64 ? 1 : 0, &e0, &e1);
+    if (timed) cudaEventRecord(e0, st);
+    cudaError_t e;
+    if (fp64) e = dagger ? launch_epi<double, true>(A, epi, st) : launch_epi<double, false>(A, epi, st);
+    else e = dagger ? launch_epi<float, true>(A, epi, st) : launch_epi<float, false>(A, epi, st);
+    if (timed) cudaEventRecord(e1, st);
+    return e;
 }
 
 int hop_grid(const Geom& g, int parity) {

@@ -36,6 +36,9 @@ int hop_grid(const Geom& g, int parity);
 
 // launch counting (per host thread)
 void count_launch();
+// CUDA-event timing of hop launches (kind 0 FP32, 1 FP64): returns true and an
+// event pair to record around the launch while timing is on and slots remain
+bool kernel_timing_slot(int kind, cudaEvent_t* start, cudaEvent_t* stop);
 
 // ---------------------------------------------------------------- BLAS (lgt_blas.cu)
 struct RedArgs {

@@ -113,6 +113,9 @@ SIGNATURES = [
     ("lgt_hmc_trajectory", _I, [_P, C.POINTER(ActionParams), C.POINTER(HMCParams), _U64, _U32,
                                 C.POINTER(HMCResult)]),
     ("lgt_measure_fp64_peak", _I, [C.POINTER(_D), C.POINTER(_D)]),
+    ("lgt_kernel_timing_start", _I, [_I]),
+    ("lgt_kernel_timing_stop", _I, [C.POINTER(_D), C.POINTER(C.c_int64), C.POINTER(_D),
+                                    C.POINTER(C.c_int64)]),
     ("lgt_launch_count", C.c_int64, [_I]),
 ]
 
@@ -159,6 +162,17 @@ def measure_fp64_peak():
     f, s = C.c_double(), C.c_double()
     check(lib().lgt_measure_fp64_peak(C.byref(f), C.byref(s)))
     return f.value
+
+
+def kernel_timing_start(max_launches=65536):
+    check(lib().lgt_kernel_timing_start(max_launches))
+
+
+def kernel_timing_stop():
+    """(ms_fp32, n_fp32, ms_fp64, n_fp64) of the hop launches since kernel_timing_start."""
+    a, b, c, d = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
+    check(lib().lgt_kernel_timing_stop(C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+    return a.value, b.value, c.value, d.value
 
 
 def launch_count(reset=False):
