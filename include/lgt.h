@@ -158,6 +158,22 @@ int lgt_reunitarise(lgt_lattice_t lat);
 /* <P> = sum_{x,mu<nu} Re tr U_munu / (3 * 6 V) (host result). */
 int lgt_plaquette(lgt_lattice_t lat, double *plaq);
 
+/* Mean plaquette, as lgt_plaquette, of a canonical link field (device,
+ * complex128 [V][4][3][3], extents dims[0..3], all even) without allocating any
+ * device memory and without a lattice handle.  The paper has no counterpart:
+ * this entry point is for callers that cannot allocate device memory when they
+ * need the number (inside another framework's memory pool or budget, allocator-
+ * free runtimes, hooks between someone else's launches).  The result (one double)
+ * is written to plaq_dev, a device pointer, in stream order on `stream`; the call
+ * does not synchronise.  Scratch is a fixed file-scope device array, so
+ * V > 8,388,608 sites is rejected with LGT_EINVAL.  The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * kernels overlap on the GPU race and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+int lgt_plaquette_noalloc(const double *links_canonical, const int dims[4], double *plaq_dev,
+                          void *stream);
+
 /* ------------------------------------------------------------------ layouts */
 /* canonical spinor (device, complex128 [V][4][3]) <-> device field of the given
  * parity (LGT_EVEN/ODD: only that parity's sites) and precision. */

@@ -31,6 +31,10 @@ static KernelTiming g_kt;
 
 namespace lgt {
 void count_launch() { ++g_launches; }
+int set_error(int code, const char* msg) {
+    g_err = msg;
+    return code;
+}
 bool kernel_timing_slot(int kind, cudaEvent_t* a, cudaEvent_t* b) {
     if (!g_kt.on || g_kt.used + 2 > g_kt.ev.size()) return false;
     *a = g_kt.ev[g_kt.used];

@@ -36,6 +36,8 @@ int hop_grid(const Geom& g, int parity);
 
 // launch counting (per host thread)
 void count_launch();
+// record the thread-local message returned by lgt_last_error(); returns code
+int set_error(int code, const char* msg);
 // CUDA-event timing of hop launches (kind 0 FP32, 1 FP64): returns true and an
 // event pair to record around the launch while timing is on and slots remain
 bool kernel_timing_slot(int kind, cudaEvent_t* start, cudaEvent_t* stop);

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("lgt_random_links", _I, [_P, _U64, _D]),
     ("lgt_reunitarise", _I, [_P]),
     ("lgt_plaquette", _I, [_P, C.POINTER(_D)]),
+    ("lgt_plaquette_noalloc", _I, [_P, C.POINTER(C.c_int), _P, _P]),
     ("lgt_pack_spinor", _I, [_P, _P, _P, _I, _I]),
     ("lgt_unpack_spinor", _I, [_P, _P, _P, _I, _I]),
     ("lgt_pack_momenta", _I, [_P, _P, _P]),
