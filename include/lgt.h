@@ -88,8 +88,10 @@ typedef struct {
     double kappa;     /* hopping parameter of D */
     int fermions;     /* 1: include S_f, 0: pure gauge */
     int even_odd;     /* 1: S_f = phi_e^+ (Dhat^+Dhat)^{-1} phi_e; 0: full lattice */
-    int n_stout;      /* stout levels in front of D (0 .. 4) */
+    int n_stout;      /* stout levels in front of D (0 .. 4); S_G sees thin links */
     double rho;       /* stout parameter */
+    int stout_recompute; /* 0: keep every smeared level for the adjoint;
+                            1: keep only the top level and recompute the others */
 } lgt_action_params;
 
 typedef struct {
@@ -220,6 +222,23 @@ int lgt_kinetic_energy(lgt_lattice_t lat, const double *mom, double *K);
  * Synchronous (returns after the solve). */
 int lgt_force(lgt_lattice_t lat, const lgt_action_params *ap, const double *phi,
               const lgt_solver_params *sp, double *F_out, int form, lgt_solve_stats *stats);
+
+/* Lie components F_a = Re tr(G^+ i T^a U) (the projection of Eq. 9 applied to a
+ * real-component gradient G, Eq. S2.11) on the handle's links: G in the G-form
+ * layout, F in the momentum layout (both device).  Asynchronous. */
+int lgt_grad_to_lie(lgt_lattice_t lat, const double *G_field, double *F_mom);
+
+/* ------------------------------------------------------------------ stout smearing */
+/* n_levels of stout smearing (Morningstar-Peardon, the "smear" steps of Fig. 1)
+ * of the handle's gauge field, written in canonical layout to out_canonical
+ * (device, complex128 [V][4][3][3]).  Synchronous. */
+int lgt_stout_smear(lgt_lattice_t lat, double rho, int n_levels, int recompute, double *out_canonical);
+/* Adjoint of that smearing (the reverse recursion of Eq. 3 through each level):
+ * given the real-component gradient (Eq. S2.11) w.r.t. the top level, write the
+ * gradient w.r.t. the handle's thin links (both canonical, device).  recompute = 1
+ * keeps only the top level and recomputes intermediate levels.  Synchronous. */
+int lgt_stout_backward(lgt_lattice_t lat, double rho, int n_levels, int recompute,
+                       const double *G_top_canonical, double *G_thin_canonical);
 
 /* ------------------------------------------------------------------ molecular dynamics */
 /* which = LGT_UPDATE_U: U <- exp(i eps P) U (Eq. S2.1), P from mom.

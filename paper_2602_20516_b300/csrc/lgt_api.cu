@@ -103,10 +103,15 @@ struct lgt_lattice {
     // HMC / force workspace
     double2 *mom, *Ubak, *phi, *xi, *F, *G;
     bool have_md;
-    // stout stack: smeared links of each level and the per-level gradients
-    Links smeared[5];
-    double2* stout_scratch;
+    // stout stack: stored levels 1..n (FP64), or top + one scratch field when the
+    // intermediate levels are recomputed; FP32 copy of the top level only;
+    // gradient ping-pong and the per-link G_C scratch of the adjoint
+    double2* smeared[5];
     int n_smeared_alloc;
+    double2* stout_top;
+    double2* stout_tmp;
+    float4* stout_top12;
+    double2* sgrad[3];
     // reductions
     double* partials;
     unsigned* counter;
@@ -165,13 +170,20 @@ static int ensure_md(lgt_lattice* L) {
     return LGT_OK;
 }
 
-static int ensure_stout(lgt_lattice* L, int n) {
+static int ensure_stout(lgt_lattice* L, int n, bool recompute) {
     if (n > 4) return fail(LGT_EINVAL, "n_stout = %d > 4", n);
-    if (!L->stout_scratch && n > 0) TRY(A(L, 2 * links64(L), &L->stout_scratch));
-    while (L->n_smeared_alloc < n) {
-        int k = ++L->n_smeared_alloc;
-        TRY(A(L, links64(L), &L->smeared[k].U));
-        TRY(A(L, links12(L), &L->smeared[k].U12));
+    if (n == 0) return LGT_OK;
+    if (!L->stout_top12) TRY(A(L, links12(L), &L->stout_top12));
+    if (!L->sgrad[0])
+        for (int k = 0; k < 3; ++k) TRY(A(L, links64(L), &L->sgrad[k]));
+    if (recompute) {
+        if (!L->stout_top) TRY(A(L, links64(L), &L->stout_top));
+        if (!L->stout_tmp) TRY(A(L, links64(L), &L->stout_tmp));
+    } else {
+        while (L->n_smeared_alloc < n) {
+            int k = ++L->n_smeared_alloc;
+            TRY(A(L, links64(L), &L->smeared[k]));
+        }
     }
     return LGT_OK;
 }
@@ -238,7 +250,7 @@ extern "C" int lgt_create_lattice(const int dims[4], const lgt_allocator* alloc,
         lgt_destroy_lattice(L);
         return fail(LGT_ECUDA, "lattice initialisation: %s", cudaGetErrorString(e));
     }
-    L->smeared[0] = L->thin;
+    L->smeared[0] = L->thin.U;
     *out = L;
     return LGT_OK;
 }
@@ -610,15 +622,41 @@ static int check_action(const lgt_action_params* ap) {
     if (ap->n_stout < 0 || ap->n_stout > 4) return fail(LGT_EINVAL, "n_stout = %d outside 0..4", ap->n_stout);
     return LGT_OK;
 }
-// links seen by the Dirac operator: thin, or the last stout level (forward pass stored)
+// Smear the thin links through levels 1..n.  Stored mode keeps every level in
+// smeared[k]; recompute mode keeps only the top level (stout_top), alternating
+// with stout_tmp so that level n lands in stout_top.
+static int smear_to(lgt_lattice* L, int n, double rho, bool recompute, double2** level_n) {
+    const double2* src = L->thin.U;
+    for (int k = 1; k <= n; ++k) {
+        double2* dst = recompute ? (((n - k) % 2 == 0) ? L->stout_top : L->stout_tmp) : L->smeared[k];
+        CK(stout_forward(src, dst, L->g, rho, L->st));
+        src = dst;
+    }
+    *level_n = (double2*)src;
+    return LGT_OK;
+}
+// U_{k} for the adjoint of level k+1 in recompute mode: recomputed into stout_tmp
+// (stout_top is free once the top-level gradient exists)
+static int recompute_level(lgt_lattice* L, int k, double rho, const double2** out) {
+    if (k == 0) { *out = L->thin.U; return LGT_OK; }
+    const double2* src = L->thin.U;
+    for (int j = 1; j <= k; ++j) {
+        double2* dst = ((k - j) % 2 == 0) ? L->stout_tmp : L->stout_top;
+        CK(stout_forward(src, dst, L->g, rho, L->st));
+        src = dst;
+    }
+    *out = src;
+    return LGT_OK;
+}
+// links seen by the Dirac operator: thin, or the top stout level (+ its FP32 copy)
 static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out) {
     if (ap->n_stout == 0) { *out = L->thin; return LGT_OK; }
-    TRY(ensure_stout(L, ap->n_stout));
-    for (int k = 1; k <= ap->n_stout; ++k) {
-        CK(stout_forward(L->smeared[k - 1].U, L->smeared[k].U, L->g, ap->rho, L->st));
-        CK(gauge_make12(L->smeared[k].U12, L->smeared[k].U, L->g, L->st));
-    }
-    *out = L->smeared[ap->n_stout];
+    const bool rc = ap->stout_recompute != 0;
+    TRY(ensure_stout(L, ap->n_stout, rc));
+    double2* top;
+    TRY(smear_to(L, ap->n_stout, ap->rho, rc, &top));
+    CK(gauge_make12(L->stout_top12, top, L->g, L->st));
+    *out = Links{top, L->stout_top12};
     return LGT_OK;
 }
 
@@ -710,14 +748,31 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
     return LGT_OK;
 }
 
-// Smeared fermion action: G_fermion w.r.t. the last level, taken back level by
+// Adjoint of the smearing levels n..1: sgrad[0] holds the gradient w.r.t. the top
+// level on entry; the gradient w.r.t. the thin links is written to G.
+static int stout_chain(lgt_lattice* L, const lgt_action_params* ap, double2* G) {
+    double2* ga = L->sgrad[0];
+    double2* gb = L->sgrad[1];
+    const bool rc = ap->stout_recompute != 0;
+    for (int k = ap->n_stout; k >= 1; --k) {
+        const double2* Uin;
+        if (rc) TRY(recompute_level(L, k - 1, ap->rho, &Uin));
+        else Uin = L->smeared[k - 1];
+        double2* dst = (k == 1) ? G : gb;
+        CK(stout_backward(Uin, ga, dst, L->sgrad[2], L->g, ap->rho, L->st));
+        std::swap(ga, gb);
+    }
+    return LGT_OK;
+}
+
+// Smeared fermion action: G_fermion w.r.t. the top level, taken back level by
 // level; the gauge action sees the thin links.  Result G in G layout (thin links).
 static int force_grad_stout(lgt_lattice* L, const lgt_action_params* ap, const double2* phi,
                             const lgt_solver_params* sp, double2* G, lgt_solve_stats* stats) {
     Links top;
     TRY(fermion_links(L, ap, &top));
-    double2* ga = L->stout_scratch;                       // gradient ping-pong
-    double2* gb = L->stout_scratch + (size_t)8 * 9 * L->g.Vh;
+    double2* ga = L->sgrad[0];
+    double2* gb = L->sgrad[1];
     lgt_action_params fa = *ap;
     fa.beta = 0.0;
     if (ap->fermions) {
@@ -725,13 +780,48 @@ static int force_grad_stout(lgt_lattice* L, const lgt_action_params* ap, const d
     } else {
         CK(cudaMemsetAsync(ga, 0, links64(L), L->st));
     }
-    for (int k = ap->n_stout; k >= 1; --k) {
-        double2* dst = (k == 1) ? G : gb;
-        CK(stout_backward(L->smeared[k - 1].U, ga, dst, L->t /*scratch*/, L->g, ap->rho, L->st));
-        std::swap(ga, gb);
-        if (k == 1) break;
-    }
+    TRY(stout_chain(L, ap, G));
     if (ap->beta != 0.0) CK(gauge_force(L->thin.U, L->g, ap->beta, 1.0, 1, 1, G, L->st));
+    return LGT_OK;
+}
+
+// Lie components F_a = Re tr(G^+ i T^a U) of a G-form gradient on the handle's links
+extern "C" int lgt_grad_to_lie(lgt_lattice_t L, const double* G_field, double* F_mom) {
+    if (!L || !G_field || !F_mom) return fail(LGT_EINVAL, "null argument");
+    CK(grad_to_lie((double2*)F_mom, (const double2*)G_field, L->thin.U, L->g, L->st));
+    return LGT_OK;
+}
+
+// smeared links of the handle's gauge field, in canonical layout
+extern "C" int lgt_stout_smear(lgt_lattice_t L, double rho, int n_levels, int recompute, double* out_canonical) {
+    if (!L || !out_canonical) return fail(LGT_EINVAL, "null argument");
+    lgt_action_params ap = {0.0, 0.0, 0, 0, n_levels, rho, recompute};
+    TRY(check_action(&ap));
+    Links top;
+    TRY(fermion_links(L, &ap, &top));
+    CK(gauge_unpack_links(out_canonical, top.U, L->g, L->st));
+    CK(cudaStreamSynchronize(L->st));
+    return LGT_OK;
+}
+
+// adjoint of the n-level smearing: gradient w.r.t. the top level -> thin links
+extern "C" int lgt_stout_backward(lgt_lattice_t L, double rho, int n_levels, int recompute,
+                                  const double* G_top_canonical, double* G_thin_canonical) {
+    if (!L || !G_top_canonical || !G_thin_canonical) return fail(LGT_EINVAL, "null argument");
+    lgt_action_params ap = {0.0, 0.0, 0, 0, n_levels, rho, recompute};
+    TRY(check_action(&ap));
+    TRY(ensure_md(L));
+    if (n_levels == 0) {
+        CK(cudaMemcpyAsync(G_thin_canonical, G_top_canonical, links64(L), cudaMemcpyDeviceToDevice, L->st));
+        CK(cudaStreamSynchronize(L->st));
+        return LGT_OK;
+    }
+    Links top;
+    TRY(fermion_links(L, &ap, &top));   // forward levels (stored mode needs them all)
+    CK(gauge_pack_field(L->sgrad[0], (const double2*)G_top_canonical, L->g, L->st));
+    TRY(stout_chain(L, &ap, L->G));
+    CK(gauge_unpack_field(G_thin_canonical, L->G, L->g, L->st));
+    CK(cudaStreamSynchronize(L->st));
     return LGT_OK;
 }
 

@@ -13,32 +13,6 @@ namespace lgt {
 
 static inline int grid_for(long n) { return (int)((n + NT - 1) / NT); }
 
-// thread -> (mu, parity, i) for 4 V links
-__device__ __forceinline__ bool link_index(const Geom& g, int& mu, int& p, int& i) {
-    const long t = (long)blockIdx.x * NT + threadIdx.x;
-    if (t >= 8L * g.Vh) return false;
-    mu = (int)(t / (2 * g.Vh));
-    int rem = (int)(t - (long)mu * 2 * g.Vh);
-    p = rem >= g.Vh;
-    i = rem - p * g.Vh;
-    return true;
-}
-
-// coordinates and lexicographic index of an arbitrary site
-__device__ __forceinline__ int lex_of(const Geom& g, const int x[4]) {
-    return x[0] + g.stride[1] * x[1] + g.stride[2] * x[2] + g.stride[3] * x[3];
-}
-__device__ __forceinline__ dmat link_at(const double2* U, const Geom& g, const int x[4], int mu) {
-    int lex = lex_of(g, x);
-    int par = (x[0] + x[1] + x[2] + x[3]) & 1;
-    return load_link(U, g.Vh, par, mu, lex >> 1);
-}
-__device__ __forceinline__ void shift(const Geom& g, int x[4], int mu, int dir) {
-    x[mu] += dir;
-    if (x[mu] == g.L[mu]) x[mu] = 0;
-    if (x[mu] < 0) x[mu] = g.L[mu] - 1;
-}
-
 // ---------------------------------------------------------------- layouts
 template <bool WITH12>
 __global__ void __launch_bounds__(NT) pack_links_kernel(double2* U, float4* U12, const double2* canon, Geom g) {

@@ -5,6 +5,33 @@
 
 namespace lgt {
 
+// thread -> (mu, parity, i) for 4 V links
+__device__ __forceinline__ bool link_index(const Geom& g, int& mu, int& p, int& i) {
+    const long t = (long)blockIdx.x * NT + threadIdx.x;
+    if (t >= 8L * g.Vh) return false;
+    mu = (int)(t / (2 * g.Vh));
+    int rem = (int)(t - (long)mu * 2 * g.Vh);
+    p = rem >= g.Vh;
+    i = rem - p * g.Vh;
+    return true;
+}
+
+// coordinates and lexicographic index of an arbitrary site
+__device__ __forceinline__ int lex_of(const Geom& g, const int x[4]) {
+    return x[0] + g.stride[1] * x[1] + g.stride[2] * x[2] + g.stride[3] * x[3];
+}
+__device__ __forceinline__ dmat link_at(const double2* U, const Geom& g, const int x[4], int mu) {
+    int lex = lex_of(g, x);
+    int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    return load_link(U, g.Vh, par, mu, lex >> 1);
+}
+__device__ __forceinline__ void shift(const Geom& g, int x[4], int mu, int dir) {
+    x[mu] += dir;
+    if (x[mu] == g.L[mu]) x[mu] = 0;
+    if (x[mu] < 0) x[mu] = g.L[mu] - 1;
+}
+
+
 // ---------------------------------------------------------------- exp(iQ)
 // exp(iQ) for Hermitian traceless Q.  With c0 = det Q, c1 = tr(Q^2)/2, the
 // Cayley-Hamilton coefficients f_j give exp(iQ) = f0 + f1 Q + f2 Q^2; c0 < 0 is

@@ -48,7 +48,8 @@ class SolveStats(C.Structure):
 
 class ActionParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("fermions", C.c_int),
-                ("even_odd", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double)]
+                ("even_odd", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double),
+                ("stout_recompute", C.c_int)]
 
 
 class HMCParams(C.Structure):
@@ -109,6 +110,9 @@ SIGNATURES = [
                        C.POINTER(SolveStats)]),
     ("lgt_md_update", _I, [_P, _P, _D, _I, C.POINTER(ActionParams), _P, C.POINTER(SolverParams),
                            C.POINTER(SolveStats)]),
+    ("lgt_grad_to_lie", _I, [_P, _P, _P]),
+    ("lgt_stout_smear", _I, [_P, _D, _I, _I, _P]),
+    ("lgt_stout_backward", _I, [_P, _D, _I, _I, _P, _P]),
     ("lgt_gaussian_momenta", _I, [_P, _P, _U64, _U32]),
     ("lgt_gaussian_spinor", _I, [_P, _P, _U64, _U32, _U32, _I]),
     ("lgt_hmc_trajectory", _I, [_P, C.POINTER(ActionParams), C.POINTER(HMCParams), _U64, _U32,
@@ -145,13 +149,14 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def solver(precision="fp64", tol=1e-10, max_iter=10000, delta=0.1, check_every=16):
+def solver(precision="fp64", tol=1e-10, max_iter=10000, delta=1e-3, check_every=16):
     prec = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else precision
     return SolverParams(prec, tol, max_iter, delta, check_every)
 
 
-def action_params(beta=0.0, kappa=0.0, fermions=True, even_odd=False, n_stout=0, rho=0.0):
-    return ActionParams(beta, kappa, int(fermions), int(even_odd), n_stout, rho)
+def action_params(beta=0.0, kappa=0.0, fermions=True, even_odd=False, n_stout=0, rho=0.0,
+                  stout_recompute=False):
+    return ActionParams(beta, kappa, int(fermions), int(even_odd), n_stout, rho, int(stout_recompute))
 
 
 def hmc_params(integrator="leapfrog", n_steps=10, tau=1.0, md_solver=None, action_solver=None):
@@ -368,6 +373,17 @@ class Lattice:
         check(lib().lgt_md_update(self.h, _ptr(mom), eps, which, C.byref(ap),
                                   _ptr(phi) if phi is not None else None, C.byref(sp), C.byref(st)))
         return st.as_dict()
+
+    def stout_smear(self, rho, n_levels, recompute=False):
+        out = torch.zeros((self.V, 4, 3, 3), dtype=torch.complex128, device=self.device)
+        check(lib().lgt_stout_smear(self.h, rho, n_levels, int(recompute), _ptr(out)))
+        return out
+
+    def stout_backward(self, rho, n_levels, G_top, recompute=False):
+        G_top = self._dev(G_top, torch.complex128)
+        out = torch.zeros((self.V, 4, 3, 3), dtype=torch.complex128, device=self.device)
+        check(lib().lgt_stout_backward(self.h, rho, n_levels, int(recompute), _ptr(G_top), _ptr(out)))
+        return out
 
     def gaussian_momenta(self, seed, traj=0, out=None):
         m = self.momentum_field() if out is None else out
