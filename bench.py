@@ -31,7 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "force evals/s + Dslash HBM GB/s at 32^3×64, mixed vs FP64; p99 solve latency"
 UNIT = "force evals/s"
 DIMS = (32, 32, 32, 64)
-BETA, KAPPA, ALPHA, TOL, DELTA = 5.8, 0.156, 0.5, 1e-10, 0.1
+# DELTA: reliable-update threshold of the mixed CG (|r| < DELTA max|r| triggers an FP64
+# residual replacement); on this workload the iteration count is the same from 0.1 to
+# 1e-4 while the FP64 updates drop from 10 to 3 per solve
+BETA, KAPPA, ALPHA, TOL, DELTA = 5.8, 0.156, 0.5, 1e-10, 1e-4
 EPS = 1.0 / 20
 SEED = 4
 # FP64 CG iterations of this workload (Dhat^+Dhat, tol 1e-10, zero guess): used only to
@@ -41,7 +44,14 @@ CG_ITERS_FP64 = 146
 # algorithmic (compulsory) bytes per output site of one even-odd hop:
 # 8 links + 1 input spinor + 1 output spinor (each array touched once)
 HOP_BYTES = {"fp32": 8 * 48 + 96 + 96, "fp64": 8 * 144 + 192 + 192}
+# per epilogue: + y read (xpay); the fused CG update reads y, x, r, p and writes x, r
+# instead of writing the output
+HOP_BYTES_EPI = {prec: {"hop": b, "xpay": b + s, "xpay_norm": b + s, "cg_update": b - s + s + 3 * s + 2 * s,
+                        "residual": b + 2 * s}
+                 for prec, b, s in (("fp32", HOP_BYTES["fp32"], 96), ("fp64", HOP_BYTES["fp64"], 192))}
 HOP_FLOPS = 1320
+# launches shorter than this did no work (a full hop at 32^3 x 64 takes >= 70 us)
+HOP_MIN_MS = 0.010
 # ncu DRAM traffic (read + write) of one FP32 hop launch at 32^3 x 64, and the hash of
 # the kernel sources it was taken from (traffic is reported as null once they change)
 NCU_TRAFFIC = {"bytes": 595180544,
@@ -202,7 +212,8 @@ def run_ours(args):
         barrier()
         torch.cuda.synchronize()
         launches = lgt.launch_count()
-        kt = lgt.kernel_timing_stop() if kernel_timing else None
+        # hops enqueued after a solve stopped return at entry (a few us): excluded
+        kt = lgt.kernel_timing_stop(HOP_MIN_MS) if kernel_timing else None
         clk = clocks.stop() if clocks else None
         ms = e0.elapsed_time(e1)
         return ms, st, launches, kt, clk
@@ -223,12 +234,26 @@ def run_ours(args):
     value64 = world * K64 / (ms64 / 1e3)
     iters64 = statistics.mean(s["iters"] for s in st64)
 
-    # dominant kernel: the FP32 hop, timed with CUDA events on its stream inside the timed region
-    ms32_sum, n32, _, _ = kt
+    # error of the mixed force against the FP64 path on the same field
+    Fm, _ = lat.force(ap, phi, sp_mixed)
+    Fd, _ = lat.force(ap, phi, lgt.solver("fp64", tol=TOL))
+    force_err = (torch.linalg.norm(Fm - Fd) / torch.linalg.norm(Fd)).item()
+    del Fm, Fd
+
+    # dominant kernel: the FP32 hop, timed with CUDA events on its stream inside the
+    # timed region; each epilogue variant counts its own algorithmic bytes
+    kinds, n32_short = kt
+    bytes32 = sum(HOP_BYTES_EPI["fp32"][e] * lat.Vh * n for (p, e), (ms_, n) in kinds.items() if p == "fp32")
+    ms32_sum = sum(ms_ for (p, e), (ms_, n) in kinds.items() if p == "fp32")
+    n32 = sum(n for (p, e), (ms_, n) in kinds.items() if p == "fp32")
     hop32_ms = ms32_sum / max(n32, 1)
-    achieved = HOP_BYTES["fp32"] * lat.Vh / (hop32_ms * 1e-3) / 1e9
-    _, _, ms64_sum, n64 = kt64
-    hop64_ms = ms64_sum / max(n64, 1)
+    achieved = bytes32 / (ms32_sum * 1e-3) / 1e9
+    per_variant = {e: {"launches": n, "avg_us": 1e3 * ms_ / n,
+                       "GBs": HOP_BYTES_EPI["fp32"][e] * lat.Vh / (ms_ / n * 1e-3) / 1e9}
+                   for (p, e), (ms_, n) in kinds.items() if p == "fp32"}
+    kinds64, _ = kt64
+    plain64 = kinds64.get(("fp64", "hop"), (0.0, 0))
+    hop64_ms = plain64[0] / max(plain64[1], 1)
     fp64_peak = lgt.measure_fp64_peak()
     peak, peak_kind = measured_peaks()
     traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources_sha256"] == hop_sources_hash() else None
@@ -267,6 +292,12 @@ def run_ours(args):
                "steps": Ke, "step": "upload canonical links + phi (pinned host), force (mixed CG), "
                                    "download canonical force"}
 
+    serving = None
+    if args.serve_requests > 0:
+        free, total = torch.cuda.mem_get_info()
+        serving = {"full": run_serving(args.serve_requests, int(0.8 * free)),
+                   "tight_8GB": run_serving(args.serve_requests, 8 << 30) if args.serve_tight else None}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         est, cores, sample = oracle_sample(int(round(iters64)), reps=1)
@@ -279,21 +310,109 @@ def run_ours(args):
            "config": config_block(args),
            "cg_iters_per_step": iters, "reliable_updates_per_step": rel,
            "fp64": {"value": value64, "ms_per_step": ms64 / K64, "steps": K64, "cg_iters_per_step": iters64,
-                    "mixed_speedup": value / value64},
-           "dslash": {"fp32_hop_us": hop32_ms * 1e3, "fp32_hop_GBs_compulsory": achieved,
-                      "fp32_hop_launches": n32, "fp64_hop_us": hop64_ms * 1e3,
+                    "mixed_speedup": value / value64,
+                    "mixed_force_rel_err_vs_fp64_path": force_err},
+           "dslash": {"fp32_hop_avg_us": hop32_ms * 1e3, "fp32_hop_GBs_algorithmic": achieved,
+                      "fp32_variants": per_variant,
+                      "fp32_hop_launches": n32, "skipped_hop_launches": n32_short,
+                      "fp64_plain_hop_us": hop64_ms * 1e3,
                       "fp64_hop_TFLOPs": HOP_FLOPS * lat.Vh / (hop64_ms * 1e-3) / 1e12,
                       "fp64_peak_TFLOPs_measured": fp64_peak / 1e12,
                       "fp64_hop_frac_of_fp64_peak": HOP_FLOPS * lat.Vh / (hop64_ms * 1e-3) / fp64_peak},
            "roofline": {"bound": "hbm", "kernel": "hop_kernel<float> (FP32 Wilson hop, two-row links)",
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_source": peak_kind,
-                        "traffic": traffic, "algorithmic_bytes_per_launch": HOP_BYTES["fp32"] * lat.Vh},
+                        "traffic": traffic, "traffic_kernel": "plain FP32 hop (ncu capture)",
+                        "algorithmic_bytes_per_launch": bytes32 / max(n32, 1),
+                        "algorithmic_bytes_plain_hop": HOP_BYTES["fp32"] * lat.Vh},
+           "serving": serving,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- serving (p50/p99 latency)
+SERVE_VOLUMES = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 48)]
+
+
+def run_serving(n_per_rate, budget_bytes, seed=10):
+    """Resident pool of 2 gauge fields per volume (alpha ~ U[0.3, 0.6]); requests:
+    70% Dirac solves, 30% force evaluations, kappa ~ U[0.14, 0.157], FP64 / mixed
+    50/50, tol 1e-10.  Saturated throughput, then open-loop Poisson arrivals at
+    0.5, 0.9 and 1.2 x that rate; latency = completion - scheduled arrival."""
+    import numpy as np
+    from paper_2602_20516_b300 import serve
+    rng = np.random.default_rng(seed)
+    srv = serve.Server(budget_bytes, max_active=64, batch_iters=8, delta=DELTA)
+    gids = []
+    for k, d in enumerate(SERVE_VOLUMES):
+        for j in range(2):
+            gids.append(srv.add_gauge(d, 1000 + 10 * k + j, float(rng.uniform(0.3, 0.6))))
+    warm = max(10, n_per_rate // 10)
+    serve.saturated(srv, serve.workload(gids, warm, seed=seed))          # warm-up
+    thr, done = serve.saturated(srv, serve.workload(gids, n_per_rate, seed=seed + 1))
+    out = {"saturated_requests_per_s": thr, "budget_bytes": budget_bytes,
+           "requests_per_rate": n_per_rate, "warmup_per_rate": warm, "rates": {}}
+    for j, f in enumerate((0.5, 0.9, 1.2)):
+        reqs = serve.workload(gids, n_per_rate + warm, seed=seed + 2 + j)
+        d = serve.poisson(srv, reqs, f * thr, seed=seed + 20 + j, warmup=warm)
+        st = serve.latency_stats(d)
+        solves = [c for c in d if c["status"] == 0]
+        st["offered_per_s"] = f * thr
+        st["completed"] = len(solves)
+        out["rates"][f"{f}x"] = st
+    srv.close()
+    return out
+
+
+# ---------------------------------------------------------------- HMC on the 32^3 x 64 lattice
+def run_hmc(args):
+    """Full Nf=2 HMC at 32^3 x 64 (beta 5.8, kappa 0.156, even-odd S_f, Omelyan 2MN,
+    20 steps, tau = 1) from the seeded alpha = 0.5 start, mixed-precision solver
+    (tol 1e-10 in MD and action).  The first --hmc-fp64 trajectories are replayed on
+    the FP64 path from the same starting field and seeds: Delta H is compared
+    trajectory by trajectory (free-running chains diverge by MD chaos)."""
+    import torch
+    from paper_2602_20516_b300 import lgt
+    torch.cuda.set_device(0)
+    ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True)
+    mixed = lgt.solver("mixed", tol=TOL, delta=DELTA)
+    fp64 = lgt.solver("fp64", tol=TOL)
+    hp_m = lgt.hmc_params("omelyan", 20, 1.0, mixed, mixed)
+    hp_d = lgt.hmc_params("omelyan", 20, 1.0, fp64, fp64)
+    lat = lgt.Lattice(DIMS)
+    lat.random_links(SEED, ALPHA)
+    ref = lgt.Lattice(DIMS) if args.hmc_fp64 > 0 else None
+    trajs = []
+    for k in range(args.hmc):
+        U0 = lat.get_links() if k < args.hmc_fp64 else None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = lat.hmc_trajectory(ap, hp_m, SEED, k)
+        torch.cuda.synchronize()
+        rec = {"traj": k, "dH": r["dH"], "accepted": r["accepted"], "plaquette": r["plaquette"],
+               "seconds": time.perf_counter() - t0, "force_evals": r["force_evals"],
+               "cg_iters": r["total"]["iters"], "reliable_updates": r["total"]["reliable_updates"]}
+        if U0 is not None:
+            ref.set_links(U0)
+            t1 = time.perf_counter()
+            rd = ref.hmc_trajectory(ap, hp_d, SEED, k)
+            rec.update({"dH_fp64": rd["dH"], "accepted_fp64": rd["accepted"],
+                        "dH_abs_diff": abs(rd["dH"] - r["dH"]), "fp64_seconds": time.perf_counter() - t1})
+        trajs.append(rec)
+        print(json.dumps({"progress": rec}), file=sys.stderr, flush=True)
+    acc = sum(t["accepted"] for t in trajs) / max(len(trajs), 1)
+    mixed_s = statistics.mean(t["seconds"] for t in trajs)
+    out = {"metric": "HMC trajectories at 32^3x64 (Omelyan 2MN, 20 steps, tau 1), mixed vs FP64",
+           "trajectories": len(trajs), "acceptance": acc, "seconds_per_trajectory_mixed": mixed_s,
+           "seconds_per_trajectory_fp64": statistics.mean(t["fp64_seconds"] for t in trajs if "fp64_seconds" in t)
+           if args.hmc_fp64 else None,
+           "config": {"lattice": list(DIMS), "beta": BETA, "kappa": KAPPA, "alpha_start": ALPHA, "seed": SEED,
+                      "tol": TOL, "delta": DELTA, "integrator": "omelyan2mn", "n_steps": 20, "tau": 1.0},
+           "per_trajectory": trajs}
+    print(json.dumps(out), flush=True)
 
 
 # ---------------------------------------------------------------- reference arm (the oracle)
@@ -340,6 +459,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests per arrival rate in the serving measurement (0 skips it)")
+    ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")
+    ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
+    ap.add_argument("--hmc-fp64", type=int, default=2, help="trajectories replayed on the FP64 path")
     ap.add_argument("--kernel", choices=["hop32", "hop64"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
@@ -347,6 +471,8 @@ def main():
         args.warmup = max(3, args.warmup)   # timing rule: at least 3 untimed steps
     if args.kernel:
         run_kernel(args)
+    elif args.hmc > 0:
+        run_hmc(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

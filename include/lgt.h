@@ -259,15 +259,74 @@ int lgt_hmc_trajectory(lgt_lattice_t lat, const lgt_action_params *ap,
                        const lgt_hmc_params *hp, uint64_t seed, uint32_t traj,
                        lgt_hmc_result *res);
 
+/* ------------------------------------------------------------------ serving */
+/* A request server over a pool of resident gauge fields of different volumes.
+ * Requests (Dirac solves and force evaluations) are queued by lgt_server_submit
+ * and advanced by lgt_server_step: each step admits queued requests in arrival
+ * order while active slots and the HBM budget allow, runs `batch_iters` CG
+ * iterations of every running request with batched launches (one launch per CG
+ * kernel step covers all running requests of a precision, whatever their
+ * volume), forms the FP64 true residual of requests whose stop condition fired
+ * (mixed requests: a reliable update), and finishes converged requests.  A
+ * request's arithmetic does not depend on the other requests: its result is the
+ * same alone and in any mix.  Timestamps are host steady-clock seconds
+ * (lgt_clock).  Memory of requests, gauge fields and descriptors is allocated
+ * through `alloc` (NULL: cudaMalloc) and counted against hbm_budget_bytes. */
+typedef struct lgt_server *lgt_server_t;
+enum { LGT_REQ_SOLVE = 0,   /* x = D^{-1} b, b Gaussian from source_seed, by even-odd CGNE:
+                               Dhat^+Dhat x_e = Dhat^+(b_e + kappa H_eo b_o), x_o = b_o + kappa H_oe x_e */
+       LGT_REQ_FORCE = 1 }; /* F = dS_G + dS_f (even-odd S_f, phi_e Gaussian from source_seed), Lie form */
+typedef struct {
+    int gauge_id;        /* from lgt_server_add_gauge */
+    int kind;            /* LGT_REQ_SOLVE or LGT_REQ_FORCE */
+    int precision;       /* LGT_FP64 or LGT_MIXED */
+    double kappa, beta;  /* beta only for force requests (0 drops S_G) */
+    double tol;          /* true relative residual of the normal equations */
+    int max_iter;
+    uint64_t source_seed;
+    int keep_result;     /* 1: keep the result on the device until lgt_server_result */
+} lgt_request;
+typedef struct {
+    uint64_t id;
+    int status;          /* LGT_OK, LGT_ENOCONV, LGT_ENAN, LGT_ENOMEM (cannot fit the budget) */
+    int iters, reliable_updates;
+    double true_rel_residual;
+    double t_submit, t_admit, t_done;
+} lgt_completion;
+
+/* delta: reliable-update threshold of mixed requests (<= 0: 1e-3). */
+int lgt_server_create(const lgt_allocator *alloc, size_t hbm_budget_bytes, int max_active, int batch_iters,
+                      double delta, void *stream, lgt_server_t *out);
+int lgt_server_destroy(lgt_server_t srv);
+/* Add a resident gauge field exp(i alpha H) (Philox seed, as lgt_random_links). */
+int lgt_server_add_gauge(lgt_server_t srv, const int dims[4], uint64_t seed, double alpha, int *gauge_id);
+/* Canonical copy (device, complex128 [V][4][3][3]) of a resident gauge field. */
+int lgt_server_get_links(lgt_server_t srv, int gauge_id, double *links_canonical);
+/* Queue a request (non-blocking); returns its id. */
+int lgt_server_submit(lgt_server_t srv, const lgt_request *req, uint64_t *id);
+/* One scheduling step (see above); synchronises the server's stream. */
+int lgt_server_step(lgt_server_t srv, int *n_active, int *n_queued);
+/* Completions since the last poll (at most max); *n gets the count. */
+int lgt_server_poll(lgt_server_t srv, lgt_completion *out, int max, int *n);
+/* Copy a kept result to out_dev (solve: FP64 full spinor field [2][12][Vh];
+ * force: momentum layout) and release it; out_dev NULL only releases it. */
+int lgt_server_result(lgt_server_t srv, uint64_t id, double *out_dev, size_t bytes);
+int lgt_server_info(lgt_server_t srv, size_t *used_bytes, size_t *budget_bytes, int *n_active, int *n_queued);
+/* Host steady clock in seconds (the clock of the completion timestamps). */
+double lgt_clock(void);
+
 /* ------------------------------------------------------------------ diagnostics */
 /* Peak FP64 FMA throughput of this device (dependent FMA chains), in FLOP/s. */
 int lgt_measure_fp64_peak(double *flops, double *seconds);
 /* CUDA-event timing of the Wilson hop launches: start arms up to max_launches
  * event pairs (recorded on the launching stream around each hop launch of any
- * handle); stop waits for them and returns the summed durations (ms) and counts
- * of the FP32 and FP64 hop launches.  Process-wide; not thread safe. */
+ * handle); stop waits for them and fills ms[10] / n[10] with the summed
+ * durations (ms) and counts per kind = 5 * fp64 + epilogue (0 hop, 1 xpay,
+ * 2 xpay + norm, 3 fused CG update, 4 true residual).  Launches shorter than
+ * min_ms are only counted (n_short): inside a CG batch, hops enqueued after the
+ * solver stopped return at entry and do no work.  Process-wide; not thread safe. */
 int lgt_kernel_timing_start(int max_launches);
-int lgt_kernel_timing_stop(double *ms_fp32, int64_t *n_fp32, double *ms_fp64, int64_t *n_fp64);
+int lgt_kernel_timing_stop(double min_ms, double *ms, int64_t *n, int64_t *n_short);
 /* Kernel launches the library enqueued on this thread since the last reset. */
 int64_t lgt_launch_count(int reset);
 

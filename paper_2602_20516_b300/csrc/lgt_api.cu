@@ -45,6 +45,16 @@ bool kernel_timing_slot(int kind, cudaEvent_t* a, cudaEvent_t* b) {
 }
 }
 
+// hop launch with optional CUDA-event timing; kind = 5 * fp64 + epilogue
+static cudaError_t timed_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = kernel_timing_slot((fp64 ? 5 : 0) + epi, &e0, &e1);
+    if (timed) cudaEventRecord(e0, st);
+    cudaError_t e = launch_hop(A, fp64, dagger, epi, st);
+    if (timed) cudaEventRecord(e1, st);
+    return e;
+}
+
 static int fail(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -98,7 +108,7 @@ struct lgt_lattice {
     Links thin;
     // solver workspace (full fields; even-odd solves use the even half)
     double2 *r, *p, *u, *t, *X, *Y, *b;
-    float4 *r32, *p32, *x32, *u32, *t32;
+    float4 *r32, *p32, *x32, *u32, *t32, *X32, *Y32;
     bool have_solver;
     // HMC / force workspace
     double2 *mom, *Ubak, *phi, *xi, *F, *G;
@@ -114,6 +124,7 @@ struct lgt_lattice {
     double2* sgrad[3];
     // reductions
     double* partials;
+    int n_partials;
     unsigned* counter;
     Scalars* s;
     Scalars* hs;   // pinned host mirror
@@ -154,6 +165,7 @@ static int ensure_solver(lgt_lattice* L) {
     TRY(A(L, s64, &L->X)); TRY(A(L, s64, &L->Y)); TRY(A(L, s64, &L->b));
     TRY(A(L, s32, &L->r32)); TRY(A(L, s32, &L->p32)); TRY(A(L, s32, &L->x32)); TRY(A(L, s32, &L->u32));
     TRY(A(L, s32, &L->t32));
+    TRY(A(L, s32, &L->X32)); TRY(A(L, s32, &L->Y32));
     L->have_solver = true;
     return LGT_OK;
 }
@@ -188,7 +200,7 @@ static int ensure_stout(lgt_lattice* L, int n, bool recompute) {
     return LGT_OK;
 }
 
-static RedArgs red(lgt_lattice* L) { return RedArgs{L->s, L->partials, L->counter}; }
+static RedArgs red(lgt_lattice* L) { return RedArgs{L->s, L->partials, L->counter, L->n_partials}; }
 
 static int sync_scalars(lgt_lattice* L) {
     CK(cudaMemcpyAsync(L->hs, L->s, sizeof(Scalars), cudaMemcpyDeviceToHost, L->st));
@@ -229,10 +241,12 @@ extern "C" int lgt_create_lattice(const int dims[4], const lgt_allocator* alloc,
     L->g.stride[3] = dims[0] * dims[1] * dims[2];
     L->custom_alloc = alloc != nullptr;
     if (alloc) L->alloc = *alloc;
+    // one partial sum per block of the largest reducing grid: one thread per link (4V)
+    L->n_partials = (int)((8L * L->g.Vh + NT - 1) / NT) + 64;
     L->st = (cudaStream_t)stream;
     int rc;
     if ((rc = A(L, links64(L), &L->thin.U)) || (rc = A(L, links12(L), &L->thin.U12)) ||
-        (rc = A(L, sizeof(double) * (size_t)(2 * L->g.Vh / NT + 4096), &L->partials)) ||
+        (rc = A(L, sizeof(double) * (size_t)L->n_partials, &L->partials)) ||
         (rc = A(L, 64, &L->counter)) || (rc = A(L, sizeof(Scalars), &L->s))) {
         lgt_destroy_lattice(L);
         return rc;
@@ -377,6 +391,7 @@ static HopArgs hop_base(lgt_lattice* L, const Links& lk, bool fp64) {
     a.g = L->g;
     a.s = L->s;
     a.partials = L->partials;
+    a.red_capacity = L->n_partials;
     a.counter = L->counter;
     a.a = 1.0;
     return a;
@@ -399,7 +414,7 @@ static int hop1(lgt_lattice* L, const Links& lk, bool fp64, bool dag, int q, con
     A.out[q] = out_half;
     A.y[q] = y_half;
     A.a = a;
-    CK(launch_hop(A, fp64, dag, epi, L->st));
+    CK(timed_hop(A, fp64, dag, epi, L->st));
     return LGT_OK;
 }
 // full-lattice D or D^+: out = in - kappa H in
@@ -412,7 +427,7 @@ static int dfull(lgt_lattice* L, const Links& lk, bool fp64, bool dag, const voi
         A.y[q] = half(in, L, fp64, q);
     }
     A.a = -kappa;
-    CK(launch_hop(A, fp64, dag, EPI_XPAY, L->st));
+    CK(timed_hop(A, fp64, dag, EPI_XPAY, L->st));
     return LGT_OK;
 }
 // Dhat^(+) on even half fields: out = in - kappa^2 H_eo H_oe in, tmp an odd half field
@@ -459,20 +474,20 @@ static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, dou
         HopArgs A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 1; A.in[0] = p; A.out[1] = t;
-        CK(launch_hop(A, fp64, false, EPI_HOP, L->st));
+        CK(timed_hop(A, fp64, false, EPI_HOP, L->st));
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 0; A.in[1] = t; A.out[0] = u; A.y[0] = p; A.a = -kappa * kappa; A.red_op = RED_PAP;
-        CK(launch_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
+        CK(timed_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 1; A.in[0] = u; A.out[1] = t;
-        CK(launch_hop(A, fp64, true, EPI_HOP, L->st));
+        CK(timed_hop(A, fp64, true, EPI_HOP, L->st));
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 0; A.in[1] = t; A.y[0] = u; A.a = -kappa * kappa; A.red_op = RED_RR;
         A.x[0] = x; A.r[0] = r; A.pv[0] = p;
-        CK(launch_hop(A, fp64, true, EPI_CG, L->st));
+        CK(timed_hop(A, fp64, true, EPI_CG, L->st));
         CK(blas_cg_p_update(p, r, L->g.Vh, L->g.Vh, fp64, red(L), L->st));
     } else {
         HopArgs A = hop_base(L, lk, fp64);
@@ -482,7 +497,7 @@ static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, dou
             A.in[q] = half(p, L, fp64, q); A.out[q] = half(u, L, fp64, q); A.y[q] = half(p, L, fp64, q);
         }
         A.a = -kappa; A.red_op = RED_PAP;
-        CK(launch_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
+        CK(timed_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 2;
@@ -491,7 +506,7 @@ static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, dou
             A.x[q] = half(x, L, fp64, q); A.r[q] = half(r, L, fp64, q); A.pv[q] = half(p, L, fp64, q);
         }
         A.a = -kappa; A.red_op = RED_RR;
-        CK(launch_hop(A, fp64, true, EPI_CG, L->st));
+        CK(timed_hop(A, fp64, true, EPI_CG, L->st));
         CK(blas_cg_p_update(p, r, 2 * L->g.Vh, L->g.Vh, fp64, red(L), L->st));
     }
     return LGT_OK;
@@ -507,7 +522,7 @@ static int true_residual(lgt_lattice* L, const Links& lk, bool eo, double kappa,
         HopArgs A = hop_base(L, lk, true);
         A.parity = 0; A.in[1] = L->t; A.y[0] = L->u; A.a = -kappa * kappa; A.out[0] = res; A.pv[0] = b;
         A.red_op = RED_STORE; A.red_slot = 0;
-        CK(launch_hop(A, true, true, EPI_RESID, L->st));
+        CK(timed_hop(A, true, true, EPI_RESID, L->st));
     } else {
         TRY(dfull(L, lk, true, false, x, L->u, kappa));
         HopArgs A = hop_base(L, lk, true);
@@ -517,7 +532,7 @@ static int true_residual(lgt_lattice* L, const Links& lk, bool eo, double kappa,
             A.out[q] = half(res, L, true, q); A.pv[q] = half(b, L, true, q);
         }
         A.a = -kappa; A.red_op = RED_STORE; A.red_slot = 0;
-        CK(launch_hop(A, true, true, EPI_RESID, L->st));
+        CK(timed_hop(A, true, true, EPI_RESID, L->st));
     }
     return LGT_OK;
 }
@@ -708,11 +723,26 @@ extern "C" int lgt_kinetic_energy(lgt_lattice_t L, const double* mom, double* K)
 }
 
 // ---------------------------------------------------------------- forces
-// Solve and build X, Y of the fermion force on links lk.
+// Solve and build X, Y of the fermion force on links lk (FP64 X, Y; with fp32 the
+// vectors are built in FP32 from the FP64 solution: X32, Y32).
 static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_params* ap, const double2* phi,
-                         const lgt_solver_params* sp, lgt_solve_stats* stats) {
+                         const lgt_solver_params* sp, lgt_solve_stats* stats, bool fp32) {
     const bool eo = ap->even_odd != 0;
     TRY(cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats));
+    if (fp32) {
+        if (eo) {
+            float4* Xo = (float4*)half(L->X32, L, false, 1);
+            float4* Yo = (float4*)half(L->Y32, L, false, 1);
+            CK(blas_d2f(L->X32, L->X, L->g.Vh, L->g.Vh, L->st));
+            TRY(hop1(L, lk, false, false, 1, L->X32, Xo, ap->kappa));
+            TRY(hop1(L, lk, false, false, 0, Xo, L->Y32, -ap->kappa, EPI_XPAY, L->X32));
+            TRY(hop1(L, lk, false, true, 1, L->Y32, Yo, ap->kappa));
+        } else {
+            CK(blas_d2f(L->X32, L->X, 2 * L->g.Vh, L->g.Vh, L->st));
+            TRY(dfull(L, lk, false, false, L->X32, L->Y32, ap->kappa));
+        }
+        return LGT_OK;
+    }
     if (eo) {
         double2* Xo = (double2*)half(L->X, L, true, 1);
         double2* Yo = (double2*)half(L->Y, L, true, 1);
@@ -727,21 +757,25 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
 }
 
 // out = keep*out + coef * (dS_G + dS_f) in Lie (form 0) or G (form 1) layout, on the
-// links the actions see (no smearing here).
+// links the actions see (no smearing here).  With the mixed solver the Lie form is
+// computed in FP32 arithmetic (X, Y, staples, outer products) and accumulated in FP64.
 static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk, const lgt_action_params* ap,
                     const double2* phi, const lgt_solver_params* sp, double coef, int keep, int form, double2* out,
                     lgt_solve_stats* stats) {
+    const bool fp32 = form == 0 && sp && sp->precision == LGT_MIXED;
     if (ap->fermions) {
         if (!phi) return fail(LGT_EINVAL, "null phi");
         TRY(ensure_solver(L));
-        TRY(force_vectors(L, ferm_lk, ap, phi, sp, stats));
+        TRY(force_vectors(L, ferm_lk, ap, phi, sp, stats, fp32));
     }
     if (ap->beta != 0.0) {
-        CK(gauge_force(gauge_lk.U, L->g, ap->beta, coef, keep, form, out, L->st));
+        if (fp32) CK(gauge_force_fp32(gauge_lk.U12, L->g, ap->beta, coef, keep, out, L->st));
+        else CK(gauge_force(gauge_lk.U, L->g, ap->beta, coef, keep, form, out, L->st));
         keep = 1;
     }
     if (ap->fermions) {
-        CK(fermion_force(ferm_lk.U, L->X, L->Y, L->g, ap->kappa, coef, keep, form, out, L->st));
+        if (fp32) CK(fermion_force_fp32(ferm_lk.U12, L->X32, L->Y32, L->g, ap->kappa, coef, keep, out, L->st));
+        else CK(fermion_force(ferm_lk.U, L->X, L->Y, L->g, ap->kappa, coef, keep, form, out, L->st));
         keep = 1;
     }
     if (!keep) CK(cudaMemsetAsync(out, 0, form == 0 ? mom_bytes(L) : links64(L), L->st));
@@ -772,7 +806,6 @@ static int force_grad_stout(lgt_lattice* L, const lgt_action_params* ap, const d
     Links top;
     TRY(fermion_links(L, ap, &top));
     double2* ga = L->sgrad[0];
-    double2* gb = L->sgrad[1];
     lgt_action_params fa = *ap;
     fa.beta = 0.0;
     if (ap->fermions) {
@@ -993,23 +1026,28 @@ extern "C" int lgt_kernel_timing_start(int max_launches) {
     return LGT_OK;
 }
 
-extern "C" int lgt_kernel_timing_stop(double* ms_fp32, int64_t* n_fp32, double* ms_fp64, int64_t* n_fp64) {
+extern "C" int lgt_kernel_timing_stop(double min_ms, double* ms, int64_t* n, int64_t* n_short) {
     g_kt.on = false;
-    double ms[2] = {0.0, 0.0};
-    int64_t n[2] = {0, 0};
+    double acc[10] = {0};
+    int64_t cnt[10] = {0}, nshort = 0;
     for (size_t k = 0; k + 1 < g_kt.used; k += 2) {
         CK(cudaEventSynchronize(g_kt.ev[k + 1]));
         float t = 0.f;
         CK(cudaEventElapsedTime(&t, g_kt.ev[k], g_kt.ev[k + 1]));
+        if (t < min_ms) {   // returned at entry: its solver had already stopped
+            ++nshort;
+            continue;
+        }
         int kind = g_kt.kind[k / 2];
-        ms[kind] += t;
-        n[kind] += 1;
+        acc[kind] += t;
+        cnt[kind] += 1;
     }
     g_kt.used = 0;
-    if (ms_fp32) *ms_fp32 = ms[0];
-    if (n_fp32) *n_fp32 = n[0];
-    if (ms_fp64) *ms_fp64 = ms[1];
-    if (n_fp64) *n_fp64 = n[1];
+    for (int k = 0; k < 10; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (n) n[k] = cnt[k];
+    }
+    if (n_short) *n_short = nshort;
     return LGT_OK;
 }
 

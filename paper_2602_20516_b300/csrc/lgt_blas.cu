@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(NT) norm2_kernel(const void* a, int n, int Vh,
 }
 
 cudaError_t blas_norm2(const void* a, int n, int Vh, bool fp64, const RedArgs& R, int slot, cudaStream_t st) {
+    if (grid_for(n) > R.capacity) return cudaErrorInvalidValue;   // partials too small
     if (fp64) norm2_kernel<true><<<grid_for(n), NT, 0, st>>>(a, n, Vh, R, slot);
     else norm2_kernel<false><<<grid_for(n), NT, 0, st>>>(a, n, Vh, R, slot);
     count_launch();
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(NT) redot_kernel(const double2* a, const doubl
 
 cudaError_t blas_redot(const double2* a, const double2* b, int n, int Vh, const RedArgs& R, int slot,
                        cudaStream_t st) {
+    if (grid_for(n) > R.capacity) return cudaErrorInvalidValue;
     redot_kernel<<<grid_for(n), NT, 0, st>>>(a, b, n, Vh, R, slot);
     count_launch();
     return cudaGetLastError();
@@ -78,9 +80,9 @@ __device__ __forceinline__ void xpby(float4& p, float4 r, double bd) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) p_update_kernel(T* p, const T* r, long ne, RedArgs R) {
+__device__ __forceinline__ void p_update_body(T* p, const T* r, long ne, const RedArgs& R, int blk, int nblk) {
     if (R.s->done >= 2) return;
-    const long e = (long)blockIdx.x * NT + threadIdx.x;
+    const long e = (long)blk * NT + threadIdx.x;
     if (e < ne) {
         T pv = p[e];
         xpby(pv, __ldg(r + e), R.s->beta);
@@ -91,13 +93,39 @@ __global__ void __launch_bounds__(NT) p_update_kernel(T* p, const T* r, long ne,
     if (threadIdx.x == 0) {
         __threadfence();
         unsigned prev = atomicAdd(R.counter, 1u);
-        last = (prev == gridDim.x - 1);
+        last = (prev == (unsigned)nblk - 1);
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
         *R.counter = 0u;
         if (R.s->done == 1) R.s->done = 2;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) p_update_kernel(T* p, const T* r, long ne, RedArgs R) {
+    p_update_body<T>(p, r, ne, R, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) p_update_batch_kernel(const BatchAxpy* __restrict__ d, int n) {
+    int lo = 0, hi = n - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].first <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchAxpy& e = d[lo];
+    p_update_body<T>((T*)e.p, (const T*)e.r, e.ne, e.red, b - e.first, e.nblk);
+}
+
+cudaError_t launch_p_update_batch(const BatchAxpy* d, int n, int total_blocks, bool fp64, cudaStream_t st) {
+    if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+    if (fp64) p_update_batch_kernel<double2><<<total_blocks, NT, 0, st>>>(d, n);
+    else p_update_batch_kernel<float4><<<total_blocks, NT, 0, st>>>(d, n);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t blas_cg_p_update(void* p, const void* r, int n, int Vh, bool fp64, const RedArgs& R,

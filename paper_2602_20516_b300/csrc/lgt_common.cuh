@@ -118,8 +118,9 @@ template <typename R> __device__ __forceinline__ R retrace(const mat3<R>& a) {
 }
 
 // Lie components of M: c_a = Im tr(lambda^a M) = 2 Im tr(T^a M), a = 0..7.
-__device__ __forceinline__ void lie_im_tr(const dmat& M, double c[8]) {
-    const double is3 = 0.57735026918962576451;  // 1/sqrt(3)
+template <typename R>
+__device__ __forceinline__ void lie_im_tr(const mat3<R>& M, R c[8]) {
+    const R is3 = (R)0.57735026918962576451;  // 1/sqrt(3)
     c[0] = M.e[0][1].i + M.e[1][0].i;
     c[1] = M.e[0][1].r - M.e[1][0].r;
     c[2] = M.e[0][0].i - M.e[1][1].i;
@@ -127,7 +128,7 @@ __device__ __forceinline__ void lie_im_tr(const dmat& M, double c[8]) {
     c[4] = M.e[0][2].r - M.e[2][0].r;
     c[5] = M.e[1][2].i + M.e[2][1].i;
     c[6] = M.e[1][2].r - M.e[2][1].r;
-    c[7] = (M.e[0][0].i + M.e[1][1].i - 2.0 * M.e[2][2].i) * is3;
+    c[7] = (M.e[0][0].i + M.e[1][1].i - (R)2 * M.e[2][2].i) * is3;
 }
 // P = sum_a p_a T^a (Hermitian traceless)
 __device__ __forceinline__ dmat herm_from_lie(const double p[8]) {
@@ -341,27 +342,32 @@ __device__ __forceinline__ void apply_reduce_op(Scalars* s, int op, int slot, do
     }
 }
 
-// Deterministic grid reduction: each block stores its partial, the last block to
+// Deterministic grid reduction over the nblk blocks of one problem (blk = this
+// block's index among them): each block stores its partial, the last block to
 // finish sums all partials in index order and applies `op` to the scalars.
 __device__ __forceinline__ void grid_reduce(double block_partial, double* partials, unsigned* counter,
-                                            Scalars* s, int op, int slot) {
+                                            Scalars* s, int op, int slot, int blk, int nblk) {
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = block_partial;
+        partials[blk] = block_partial;
         __threadfence();
         unsigned prev = atomicAdd(counter, 1u);
-        last = (prev == gridDim.x - 1);
+        last = (prev == (unsigned)nblk - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     double acc = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += NT) acc += __ldcg(partials + k);
+    for (int k = threadIdx.x; k < nblk; k += NT) acc += __ldcg(partials + k);
     acc = block_sum(acc);
     if (threadIdx.x == 0) {
         *counter = 0u;
         apply_reduce_op(s, op, slot, acc);
     }
+}
+__device__ __forceinline__ void grid_reduce(double block_partial, double* partials, unsigned* counter,
+                                            Scalars* s, int op, int slot) {
+    grid_reduce(block_partial, partials, counter, s, op, slot, blockIdx.x, gridDim.x);
 }
 
 }  // namespace lgt

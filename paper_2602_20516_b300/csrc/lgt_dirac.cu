@@ -82,22 +82,25 @@ __device__ __forceinline__ void hop_dir(const HopArgs& A, int p, int lex, const 
     }
 }
 
+// squared norm of one site's spinor in the field's own precision (the cross-site
+// accumulation is FP64); FP64 arithmetic here would cost 24 FP64 FMAs per site,
+// far more than the FP32 hop's own arithmetic on this part
 template <typename R> __device__ __forceinline__ double sq(const cx<R> (&v)[4][3]) {
-    double acc = 0.0;
+    R acc = 0;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc += (double)v[a][c].r * (double)v[a][c].r + (double)v[a][c].i * (double)v[a][c].i;
-    return acc;
+        for (int c = 0; c < 3; ++c) acc = fma(v[a][c].r, v[a][c].r, fma(v[a][c].i, v[a][c].i, acc));
+    return (double)acc;
 }
 
 template <typename R, bool DAG, int EPI>
-__global__ void __launch_bounds__(NT) hop_kernel(HopArgs A) {
+__device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk) {
     using P = Prec<R>;
     using T = typename P::T;
     if (A.skip && A.s->done >= 1) return;
     const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
-    const int t = blockIdx.x * NT + threadIdx.x;
+    const int t = blk * NT + threadIdx.x;
     const bool valid = t < n;
     double red = 0.0;
     if (valid) {
@@ -174,14 +177,71 @@ __global__ void __launch_bounds__(NT) hop_kernel(HopArgs A) {
     }
     if (EPI == EPI_XPAY_NORM || EPI == EPI_CG || EPI == EPI_RESID) {
         double b = block_sum(red);
-        grid_reduce(b, A.partials, A.counter, A.s, A.red_op, A.red_slot);
+        grid_reduce(b, A.partials, A.counter, A.s, A.red_op, A.red_slot, blk, nblk);
     }
+}
+
+// Resident blocks per SM requested from the register allocator for the FP32 hop
+// (the FP64 hop keeps its registers: it is FP64-ALU bound, not latency bound).
+#ifndef LGT_HOP32_MIN_BLOCKS
+#define LGT_HOP32_MIN_BLOCKS 4
+#endif
+#ifndef LGT_HOP32_EPI_MIN_BLOCKS
+#define LGT_HOP32_EPI_MIN_BLOCKS 6
+#endif
+template <typename R, int EPI> constexpr int hop_min_blocks() {
+    return sizeof(R) == 4 ? (EPI == EPI_HOP ? LGT_HOP32_MIN_BLOCKS : LGT_HOP32_EPI_MIN_BLOCKS) : 1;
+}
+
+template <typename R, bool DAG, int EPI>
+__global__ void __launch_bounds__(NT, (hop_min_blocks<R, EPI>())) hop_kernel(HopArgs A) {
+    hop_body<R, DAG, EPI>(A, blockIdx.x, gridDim.x);
+}
+
+// Many independent problems (lattices of any size) in one launch: block b runs
+// block b - first of the descriptor whose range [first, first + nblk) holds b.
+template <typename R, bool DAG, int EPI>
+__global__ void __launch_bounds__(NT) hop_batch_kernel(const BatchHop* __restrict__ d, int n) {
+    int lo = 0, hi = n - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].first <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchHop& e = d[lo];
+    hop_body<R, DAG, EPI>(e.a, b - e.first, e.nblk);
+}
+
+template <typename R, bool DAG>
+static cudaError_t launch_batch_epi(const BatchHop* d, int n, int total_blocks, int epi, cudaStream_t st) {
+    switch (epi) {
+    case EPI_HOP: hop_batch_kernel<R, DAG, EPI_HOP><<<total_blocks, NT, 0, st>>>(d, n); break;
+    case EPI_XPAY: hop_batch_kernel<R, DAG, EPI_XPAY><<<total_blocks, NT, 0, st>>>(d, n); break;
+    case EPI_XPAY_NORM: hop_batch_kernel<R, DAG, EPI_XPAY_NORM><<<total_blocks, NT, 0, st>>>(d, n); break;
+    case EPI_CG: hop_batch_kernel<R, DAG, EPI_CG><<<total_blocks, NT, 0, st>>>(d, n); break;
+    case EPI_RESID: hop_batch_kernel<R, DAG, EPI_RESID><<<total_blocks, NT, 0, st>>>(d, n); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hop_batch(const BatchHop* d, int n, int total_blocks, bool fp64, bool dagger, int epi,
+                             cudaStream_t st) {
+    if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+    if (fp64) return dagger ? launch_batch_epi<double, true>(d, n, total_blocks, epi, st)
+                            : launch_batch_epi<double, false>(d, n, total_blocks, epi, st);
+    return dagger ? launch_batch_epi<float, true>(d, n, total_blocks, epi, st)
+                  : launch_batch_epi<float, false>(d, n, total_blocks, epi, st);
 }
 
 template <typename R, bool DAG>
 static cudaError_t launch_epi(const HopArgs& A, int epi, cudaStream_t st) {
     const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
     const int grid = (n + NT - 1) / NT;
+    const bool reduces = epi == EPI_XPAY_NORM || epi == EPI_CG || epi == EPI_RESID;
+    if (reduces && (!A.partials || grid > A.red_capacity)) return cudaErrorInvalidValue;
     switch (epi) {
     case EPI_HOP: hop_kernel<R, DAG, EPI_HOP><<<grid, NT, 0, st>>>(A); break;
     case EPI_XPAY: hop_kernel<R, DAG, EPI_XPAY><<<grid, NT, 0, st>>>(A); break;
@@ -195,14 +255,8 @@ static cudaError_t launch_epi(const HopArgs& A, int epi, cudaStream_t st) {
 }
 
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const bool timed = kernel_timing_slot(fp64 ? 1 : 0, &e0, &e1);
-    if (timed) cudaEventRecord(e0, st);
-    cudaError_t e;
-    if (fp64) e = dagger ? launch_epi<double, true>(A, epi, st) : launch_epi<double, false>(A, epi, st);
-    else e = dagger ? launch_epi<float, true>(A, epi, st) : launch_epi<float, false>(A, epi, st);
-    if (timed) cudaEventRecord(e1, st);
-    return e;
+    if (fp64) return dagger ? launch_epi<double, true>(A, epi, st) : launch_epi<double, false>(A, epi, st);
+    return dagger ? launch_epi<float, true>(A, epi, st) : launch_epi<float, false>(A, epi, st);
 }
 
 int hop_grid(const Geom& g, int parity) {

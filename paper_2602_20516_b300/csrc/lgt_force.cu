@@ -9,6 +9,8 @@
 // Lie form:  W = U P1 - P2 U^+,  F_a = -2 kappa Im tr(T^a W)  (= i kappa P[W], Eq. 9);
 // G form:    G = dS/dReU + i dS/dImU = 2 kappa (P1^+ + P2)      (Eq. S2.11).
 // One thread per link; X(x), Y(x) are re-read per direction through L1/L2.
+// The FP64 kernel serves the FP64 path and the G form; the mixed-precision MD path
+// uses FP32 arithmetic (FP32 X, Y and two-row links) accumulated into FP64 momenta.
 #include "lgt_internal.h"
 #include "lgt_spin.cuh"
 
@@ -16,28 +18,41 @@ namespace lgt {
 
 static inline int grid_for(long n) { return (int)((n + NT - 1) / NT); }
 
-template <int MU>
-__device__ __forceinline__ void outer_terms(const SpinorD& Xx, const SpinorD& Yx, const SpinorD& Xy,
-                                            const SpinorD& Yy, double b, dmat& P1, dmat& P2) {
-    dcx h[2][3], k[2][3];
-    project<MU, -1>(Xy.c, h);
-    project<MU, -1>(Yx.c, k);
+template <int MU, typename R>
+__device__ __forceinline__ void outer_terms(const cx<R> (&Xx)[4][3], const cx<R> (&Yx)[4][3],
+                                            const cx<R> (&Xy)[4][3], const cx<R> (&Yy)[4][3], R b, mat3<R>& P1,
+                                            mat3<R>& P2) {
+    cx<R> h[2][3], k[2][3];
+    project<MU, -1>(Xy, h);
+    project<MU, -1>(Yx, k);
     for (int a = 0; a < 3; ++a)
         for (int c = 0; c < 3; ++c) {
-            dcx s = {0, 0};
+            cx<R> s = {0, 0};
             s = cmad_cb(s, h[0][a], k[0][c]);
             s = cmad_cb(s, h[1][a], k[1][c]);
             P1.e[a][c] = b * s;
         }
-    project<MU, +1>(Xx.c, h);
-    project<MU, +1>(Yy.c, k);
+    project<MU, +1>(Xx, h);
+    project<MU, +1>(Yy, k);
     for (int a = 0; a < 3; ++a)
         for (int c = 0; c < 3; ++c) {
-            dcx s = {0, 0};
+            cx<R> s = {0, 0};
             s = cmad_cb(s, h[0][a], k[0][c]);
             s = cmad_cb(s, h[1][a], k[1][c]);
             P2.e[a][c] = b * s;
         }
+}
+
+template <typename R>
+__device__ __forceinline__ void outer_dispatch(int mu, const cx<R> (&Xx)[4][3], const cx<R> (&Yx)[4][3],
+                                               const cx<R> (&Xy)[4][3], const cx<R> (&Yy)[4][3], R b,
+                                               mat3<R>& P1, mat3<R>& P2) {
+    switch (mu) {
+    case 0: outer_terms<0, R>(Xx, Yx, Xy, Yy, b, P1, P2); break;
+    case 1: outer_terms<1, R>(Xx, Yx, Xy, Yy, b, P1, P2); break;
+    case 2: outer_terms<2, R>(Xx, Yx, Xy, Yy, b, P1, P2); break;
+    default: outer_terms<3, R>(Xx, Yx, Xy, Yy, b, P1, P2); break;
+    }
 }
 
 template <int FORM>
@@ -57,12 +72,7 @@ __global__ void __launch_bounds__(NT) fermion_force_kernel(const double2* U, con
     SpinorD Xx = load_spinor(X + p * hf, g.Vh, i), Yx = load_spinor(Y + p * hf, g.Vh, i);
     SpinorD Xy = load_spinor(X + (1 - p) * hf, g.Vh, j), Yy = load_spinor(Y + (1 - p) * hf, g.Vh, j);
     dmat P1, P2;
-    switch (mu) {
-    case 0: outer_terms<0>(Xx, Yx, Xy, Yy, b, P1, P2); break;
-    case 1: outer_terms<1>(Xx, Yx, Xy, Yy, b, P1, P2); break;
-    case 2: outer_terms<2>(Xx, Yx, Xy, Yy, b, P1, P2); break;
-    default: outer_terms<3>(Xx, Yx, Xy, Yy, b, P1, P2); break;
-    }
+    outer_dispatch<double>(mu, Xx.c, Yx.c, Xy.c, Yy.c, b, P1, P2);
     if (FORM == 0) {
         dmat Um = load_link(U, g.Vh, p, mu, i);
         dmat W = mul(Um, P1);
@@ -88,10 +98,49 @@ __global__ void __launch_bounds__(NT) fermion_force_kernel(const double2* U, con
     }
 }
 
+// FP32 arithmetic (X, Y: float4 [2][6][Vh]; links: two-row FP32), FP64 accumulation
+__global__ void __launch_bounds__(NT) fermion_force_fp32_kernel(const float4* U12, const float4* X, const float4* Y,
+                                                                Geom g, double kappa, double coef, int keep,
+                                                                double2* out) {
+    const long t = (long)blockIdx.x * NT + threadIdx.x;
+    if (t >= 8L * g.Vh) return;
+    const int mu = (int)(t / (2 * g.Vh));
+    const int rem = (int)(t - (long)mu * 2 * g.Vh);
+    const int p = rem >= g.Vh, i = rem - p * g.Vh;
+    int x[4];
+    const int lex = eo_coords(g, p, i, x);
+    const int j = nb_lex(g, lex, x, mu, +1) >> 1;
+    const float b = (mu == 3 && x[3] == g.L[3] - 1) ? -1.f : 1.f;
+    const size_t hf = (size_t)6 * g.Vh;
+    SpinorF Xx = load_spinor(X + p * hf, g.Vh, i), Yx = load_spinor(Y + p * hf, g.Vh, i);
+    SpinorF Xy = load_spinor(X + (1 - p) * hf, g.Vh, j), Yy = load_spinor(Y + (1 - p) * hf, g.Vh, j);
+    mat3<float> P1, P2;
+    outer_dispatch<float>(mu, Xx.c, Yx.c, Xy.c, Yy.c, b, P1, P2);
+    mat3<float> Um = load_link12(U12, g.Vh, p, mu, i);
+    mat3<float> W = mul(Um, P1);
+    mat3<float> B = mul_nd(P2, Um);
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) W.e[a][c] = W.e[a][c] - B.e[a][c];
+    float cl[8];
+    lie_im_tr(W, cl);
+    double f[8];
+    if (keep) load_mom(out, g.Vh, p, mu, i, f);
+    const double s = -coef * kappa;
+    for (int a = 0; a < 8; ++a) f[a] = (keep ? f[a] : 0.0) + s * (double)cl[a];
+    store_mom(out, g.Vh, p, mu, i, f);
+}
+
 cudaError_t fermion_force(const double2* U, const double2* X, const double2* Y, const Geom& g, double kappa,
                           double coef, int keep, int form, double2* out, cudaStream_t st) {
     if (form == 0) fermion_force_kernel<0><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, X, Y, g, kappa, coef, keep, out);
     else fermion_force_kernel<1><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, X, Y, g, kappa, coef, keep, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t fermion_force_fp32(const float4* U12, const float4* X, const float4* Y, const Geom& g, double kappa,
+                               double coef, int keep, double2* out, cudaStream_t st) {
+    fermion_force_fp32_kernel<<<grid_for(8L * g.Vh), NT, 0, st>>>(U12, X, Y, g, kappa, coef, keep, out);
     count_launch();
     return cudaGetLastError();
 }

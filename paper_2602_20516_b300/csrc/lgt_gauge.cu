@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(NT) plaquette_kernel(const double2* U, Geom g,
     grid_reduce(bs, R.partials, R.counter, R.s, RED_STORE, slot);
 }
 cudaError_t gauge_plaquette(const double2* U, const Geom& g, const RedArgs& R, int slot, cudaStream_t st) {
+    if (grid_for(2L * g.Vh) > R.capacity) return cudaErrorInvalidValue;   // partials too small
     plaquette_kernel<<<grid_for(2L * g.Vh), NT, 0, st>>>(U, g, R, slot);
     count_launch();
     return cudaGetLastError();
@@ -148,8 +149,23 @@ cudaError_t gauge_plaquette(const double2* U, const Geom& g, const RedArgs& R, i
 // ---------------------------------------------------------------- staple force
 // V_mu(x) = sum_nu [U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu)]
 // d_a S_G = (beta/3) Im tr(T^a U V) = (beta/6) Im tr(lambda^a U V);  G = -(beta/3) V^+
-__device__ __forceinline__ dmat staple_sum(const double2* U, const Geom& g, const int x[4], int mu) {
-    dmat V = zero3<double>();
+// link loads by precision: FP64 18-real links or FP32 two-row links
+template <typename R> struct GLink;
+template <> struct GLink<double> {
+    static __device__ __forceinline__ dmat at(const void* U, const Geom& g, const int x[4], int mu) {
+        return link_at((const double2*)U, g, x, mu);
+    }
+};
+template <> struct GLink<float> {
+    static __device__ __forceinline__ mat3<float> at(const void* U, const Geom& g, const int x[4], int mu) {
+        int lex = lex_of(g, x);
+        return load_link12((const float4*)U, g.Vh, (x[0] + x[1] + x[2] + x[3]) & 1, mu, lex >> 1);
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ mat3<R> staple_sum(const void* U, const Geom& g, const int x[4], int mu) {
+    mat3<R> V = zero3<R>();
     int xp[4] = {x[0], x[1], x[2], x[3]};
     shift(g, xp, mu, +1);
     for (int nu = 0; nu < 4; ++nu) {
@@ -160,13 +176,33 @@ __device__ __forceinline__ dmat staple_sum(const double2* U, const Geom& g, cons
         shift(g, xmn, nu, -1);
         int xpmn[4] = {xp[0], xp[1], xp[2], xp[3]};
         shift(g, xpmn, nu, -1);
-        dmat Unx = link_at(U, g, x, nu);
-        dmat a = mul_nd(link_at(U, g, xp, nu), link_at(U, g, xpn, mu));
+        mat3<R> Unx = GLink<R>::at(U, g, x, nu);
+        mat3<R> a = mul_nd(GLink<R>::at(U, g, xp, nu), GLink<R>::at(U, g, xpn, mu));
         add_to(V, mul_nd(a, Unx));
-        dmat b = mul_dn(link_at(U, g, xpmn, nu), dag(link_at(U, g, xmn, mu)));
-        add_to(V, mul(b, link_at(U, g, xmn, nu)));
+        mat3<R> b = mul_dn(GLink<R>::at(U, g, xpmn, nu), dag(GLink<R>::at(U, g, xmn, mu)));
+        add_to(V, mul(b, GLink<R>::at(U, g, xmn, nu)));
     }
     return V;
+}
+
+// Lie form: out = keep*out + coef*(beta/6) Im tr(lambda^a U V), accumulated in FP64
+// whatever the arithmetic precision R of the staples.
+template <typename R>
+__global__ void __launch_bounds__(NT) gauge_force_lie_kernel(const void* U, Geom g, double beta, double coef,
+                                                             int keep, double2* out) {
+    int mu, p, i;
+    if (!link_index(g, mu, p, i)) return;
+    int x[4];
+    eo_coords(g, p, i, x);
+    mat3<R> V = staple_sum<R>(U, g, x, mu);
+    mat3<R> M = mul(GLink<R>::at(U, g, x, mu), V);
+    R c[8];
+    lie_im_tr(M, c);
+    double f[8];
+    if (keep) load_mom(out, g.Vh, p, mu, i, f);
+    const double s = coef * beta / 6.0;
+    for (int a = 0; a < 8; ++a) f[a] = (keep ? f[a] : 0.0) + s * (double)c[a];
+    store_mom(out, g.Vh, p, mu, i, f);
 }
 
 template <int FORM>
@@ -176,7 +212,7 @@ __global__ void __launch_bounds__(NT) gauge_force_kernel(const double2* U, Geom 
     if (!link_index(g, mu, p, i)) return;
     int x[4];
     eo_coords(g, p, i, x);
-    dmat V = staple_sum(U, g, x, mu);
+    dmat V = staple_sum<double>(U, g, x, mu);
     if (FORM == 0) {
         dmat M = mul(load_link(U, g.Vh, p, mu, i), V);
         double c[8];
@@ -202,6 +238,12 @@ cudaError_t gauge_force(const double2* U, const Geom& g, double beta, double coe
                         double2* out, cudaStream_t st) {
     if (form == 0) gauge_force_kernel<0><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, g, beta, coef, keep, out);
     else gauge_force_kernel<1><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, g, beta, coef, keep, out);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t gauge_force_fp32(const float4* U12, const Geom& g, double beta, double coef, int keep, double2* out,
+                             cudaStream_t st) {
+    gauge_force_lie_kernel<float><<<grid_for(8L * g.Vh), NT, 0, st>>>(U12, g, beta, coef, keep, out);
     count_launch();
     return cudaGetLastError();
 }
@@ -255,6 +297,7 @@ __global__ void __launch_bounds__(NT) kinetic_kernel(const double2* mom, Geom g,
     grid_reduce(bs, R.partials, R.counter, R.s, RED_STORE, slot);
 }
 cudaError_t gauge_kinetic(const double2* mom, const Geom& g, const RedArgs& R, int slot, cudaStream_t st) {
+    if (grid_for(8L * g.Vh) > R.capacity) return cudaErrorInvalidValue;   // one partial per block of links
     kinetic_kernel<<<grid_for(8L * g.Vh), NT, 0, st>>>(mom, g, R, slot);
     count_launch();
     return cudaGetLastError();

@@ -29,10 +29,20 @@ struct HopArgs {
     unsigned* counter;
     int red_op, red_slot;
     int skip;             // 1: return at once when the solver scalars say done
+    int red_capacity;     // entries of partials (reducing epilogues need one per block)
 };
 
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st);
 int hop_grid(const Geom& g, int parity);
+
+// One entry of a batched launch: the hop arguments of one problem and its block
+// range [first, first + nblk) in the combined grid (entries sorted by first).
+struct BatchHop {
+    HopArgs a;
+    int first, nblk;
+};
+cudaError_t launch_hop_batch(const BatchHop* d_desc, int n, int total_blocks, bool fp64, bool dagger, int epi,
+                             cudaStream_t st);
 
 // launch counting (per host thread)
 void count_launch();
@@ -47,6 +57,7 @@ struct RedArgs {
     Scalars* s;
     double* partials;
     unsigned* counter;
+    int capacity;   // entries of partials: a reducing launch with more blocks is refused
 };
 // all operate on n "rows" = sites; FP64 rows are 12 double2, FP32 rows 6 float4
 cudaError_t blas_zero(void* f, size_t bytes, cudaStream_t st);
@@ -56,6 +67,15 @@ cudaError_t blas_norm2(const void* a, int n, int Vh, bool fp64, const RedArgs& R
 cudaError_t blas_redot(const double2* a, const double2* b, int n, int Vh, const RedArgs& R, int slot, cudaStream_t st);
 // p = r + beta p  (beta from scalars), skipped once done >= 2; marks done 1 -> 2
 cudaError_t blas_cg_p_update(void* p, const void* r, int n, int Vh, bool fp64, const RedArgs& R, cudaStream_t st);
+// the same for many problems in one launch (each with its own scalars and counter)
+struct BatchAxpy {
+    void* p;
+    const void* r;
+    long ne;         // elements (double2 for FP64, float4 for FP32)
+    RedArgs red;
+    int first, nblk;
+};
+cudaError_t launch_p_update_batch(const BatchAxpy* d_desc, int n, int total_blocks, bool fp64, cudaStream_t st);
 // y = x (FP64 -> FP32 rounding) / y64 += x32 / y = x
 cudaError_t blas_d2f(float4* y, const double2* x, int n, int Vh, cudaStream_t st);
 cudaError_t blas_add_f2d(double2* y, const float4* x, int n, int Vh, cudaStream_t st);
@@ -79,6 +99,10 @@ cudaError_t gauge_plaquette(const double2* U, const Geom& g, const RedArgs& R, i
 // mom (or F) update from the gauge force: F_G -> out = keep*out + coef*F (Lie or G form)
 cudaError_t gauge_force(const double2* U, const Geom& g, double beta, double coef, int keep, int form,
                         double2* out, cudaStream_t st);
+// Lie-form gauge force with FP32 staple arithmetic on the two-row links,
+// accumulated into FP64 (the mixed-precision MD path)
+cudaError_t gauge_force_fp32(const float4* U12, const Geom& g, double beta, double coef, int keep, double2* out,
+                             cudaStream_t st);
 // U <- exp(i eps P) U, refresh FP32 copy
 cudaError_t gauge_update_links(double2* U, float4* U12, const double2* mom, double eps, const Geom& g,
                                cudaStream_t st);
@@ -99,6 +123,9 @@ cudaError_t grad_to_lie(double2* F, const double2* G, const double2* U, const Ge
 // layout);  form 1: out = keep*out + coef*G (G-form layout).
 cudaError_t fermion_force(const double2* U, const double2* X, const double2* Y, const Geom& g, double kappa,
                           double coef, int keep, int form, double2* out, cudaStream_t st);
+// Lie form with FP32 arithmetic: X, Y float4 [2][6][Vh], two-row FP32 links; FP64 output
+cudaError_t fermion_force_fp32(const float4* U12, const float4* X, const float4* Y, const Geom& g, double kappa,
+                               double coef, int keep, double2* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- stout (lgt_stout.cu)
 cudaError_t stout_forward(const double2* Uin, double2* Uout, const Geom& g, double rho, cudaStream_t st);

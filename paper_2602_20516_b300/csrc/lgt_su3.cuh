@@ -54,24 +54,30 @@ __device__ __forceinline__ dmat expiQ(const dmat& Q) {
         }
         return R;
     }
-    dmat Q3 = mul(Q, Q2);
-    double c0 = retrace(Q3) / 3.0;
+    // c0 = det Q = tr(Q^3) / 3: only the trace of Q Q^2 is needed
+    double c0 = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) c0 = fma(Q.e[a][b].r, Q2.e[b][a].r, fma(-Q.e[a][b].i, Q2.e[b][a].i, c0));
+    c0 *= (1.0 / 3.0);
     const bool neg = c0 < 0;
     if (neg) c0 = -c0;
-    double c0max = 2.0 * pow(c1 / 3.0, 1.5);
+    const double c1_3 = c1 * (1.0 / 3.0);
+    double c0max = 2.0 * c1_3 * sqrt(c1_3);
     double ratio = fmin(c0 / c0max, 1.0);
     double theta = acos(ratio);
     double sq = sqrt(c1);
     double st, ct;
-    sincos(theta / 3.0, &st, &ct);
+    sincos(theta * (1.0 / 3.0), &st, &ct);
     double u = sq * (1.0 / 1.7320508075688772935) * ct;
     double w = sq * st;
     double u2 = u * u, w2 = w * w;
-    double xi0 = (fabs(w) < 0.05) ? 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)) : sin(w) / w;
-    double cw = cos(w);
-    double s2u, c2u, su, cu;
-    sincos(2.0 * u, &s2u, &c2u);
+    double sw, cw;
+    sincos(w, &sw, &cw);
+    double xi0 = (fabs(w) < 0.05) ? 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)) : sw / w;
+    double su, cu;
     sincos(u, &su, &cu);
+    // e^{2iu} from e^{iu} by the double-angle identities
+    double c2u = fma(cu, cu, -su * su), s2u = 2.0 * su * cu;
     dcx e2iu = {c2u, s2u};
     dcx emiu = {cu, -su};
     dcx h0 = (u2 - w2) * e2iu + emiu * dcx{8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0};

@@ -69,6 +69,24 @@ class HMCResult(C.Structure):
         return d
 
 
+REQ_SOLVE, REQ_FORCE = 0, 1
+
+
+class Request(C.Structure):
+    _fields_ = [("gauge_id", C.c_int), ("kind", C.c_int), ("precision", C.c_int), ("kappa", C.c_double),
+                ("beta", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("source_seed", C.c_uint64), ("keep_result", C.c_int)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int), ("iters", C.c_int), ("reliable_updates", C.c_int),
+                ("true_rel_residual", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -117,10 +135,19 @@ SIGNATURES = [
     ("lgt_gaussian_spinor", _I, [_P, _P, _U64, _U32, _U32, _I]),
     ("lgt_hmc_trajectory", _I, [_P, C.POINTER(ActionParams), C.POINTER(HMCParams), _U64, _U32,
                                 C.POINTER(HMCResult)]),
+    ("lgt_server_create", _I, [C.POINTER(Allocator), _SZ, _I, _I, _D, _P, C.POINTER(_P)]),
+    ("lgt_server_destroy", _I, [_P]),
+    ("lgt_server_add_gauge", _I, [_P, C.POINTER(C.c_int), _U64, _D, C.POINTER(C.c_int)]),
+    ("lgt_server_get_links", _I, [_P, _I, _P]),
+    ("lgt_server_submit", _I, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    ("lgt_server_step", _I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("lgt_server_poll", _I, [_P, C.POINTER(Completion), _I, C.POINTER(C.c_int)]),
+    ("lgt_server_result", _I, [_P, C.c_uint64, _P, _SZ]),
+    ("lgt_server_info", _I, [_P, C.POINTER(_SZ), C.POINTER(_SZ), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("lgt_clock", C.c_double, []),
     ("lgt_measure_fp64_peak", _I, [C.POINTER(_D), C.POINTER(_D)]),
     ("lgt_kernel_timing_start", _I, [_I]),
-    ("lgt_kernel_timing_stop", _I, [C.POINTER(_D), C.POINTER(C.c_int64), C.POINTER(_D),
-                                    C.POINTER(C.c_int64)]),
+    ("lgt_kernel_timing_stop", _I, [_D, C.POINTER(_D), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("lgt_launch_count", C.c_int64, [_I]),
 ]
 
@@ -174,11 +201,21 @@ def kernel_timing_start(max_launches=65536):
     check(lib().lgt_kernel_timing_start(max_launches))
 
 
-def kernel_timing_stop():
-    """(ms_fp32, n_fp32, ms_fp64, n_fp64) of the hop launches since kernel_timing_start."""
-    a, b, c, d = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
-    check(lib().lgt_kernel_timing_stop(C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
-    return a.value, b.value, c.value, d.value
+HOP_EPILOGUES = ["hop", "xpay", "xpay_norm", "cg_update", "residual"]
+
+
+def kernel_timing_stop(min_ms=0.0):
+    """Per hop kind since kernel_timing_start: ({(precision, epilogue): (ms, count)},
+    n_short); launches shorter than min_ms are only counted in n_short."""
+    ms = (C.c_double * 10)()
+    n = (C.c_int64 * 10)()
+    short = C.c_int64()
+    check(lib().lgt_kernel_timing_stop(min_ms, ms, n, C.byref(short)))
+    out = {}
+    for k in range(10):
+        if n[k]:
+            out[("fp64" if k >= 5 else "fp32", HOP_EPILOGUES[k % 5])] = (ms[k], n[k])
+    return out, short.value
 
 
 def launch_count(reset=False):

@@ -224,6 +224,29 @@ def test_total_force_link_level_error_cdf(lgt, ora):
     assert np.quantile(eps, 0.999) < 1e-10 and eps.max() < 1e-9
 
 
+@pytest.mark.parametrize("eo", [False, True])
+def test_mixed_total_force(lgt, ora, eo):
+    """Mixed path: FP32 CG with FP64 reliable updates, FP32 force arithmetic
+    accumulated in FP64; within 1e-6 of the FP64 oracle (whole field and per link)."""
+    dims = (8, 6, 4, 10)
+    U = synth.random_links(dims, 0.5, 27)
+    phi = synth.gaussian_spinor(dims, 28, parity_mask=1 if eo else 3)
+    lat = _lat(lgt, dims, U)
+    ap = lgt.action_params(beta=5.8, kappa=0.156, even_odd=eo)
+    pf = lat.pack_spinor(phi, lgt.EVEN if eo else lgt.FULL, lgt.FP64)
+    F, st = lat.force(ap, pf, lgt.solver("mixed", tol=1e-10, delta=1e-4))
+    Fo = ora.gauge_force(dims, U, 5.8) + ora.pf_force(dims, U, 0.156, phi, eo=eo, tol=1e-13)[0]
+    Fg = _np(lat.unpack_momenta(F))
+    assert H.rel(Fg, Fo) < 1e-6
+    eps = np.linalg.norm(Fg - Fo, axis=-1) / np.linalg.norm(Fo, axis=-1)
+    assert np.quantile(eps, 0.999) < 1e-5
+    # the kick applies exactly this force: mom - eps F
+    mom = synth.gaussian_momenta(dims, 29)
+    m = lat.pack_momenta(mom)
+    lat.md_update(m, 0.05, lgt.UPDATE_P, ap, pf, lgt.solver("mixed", tol=1e-10, delta=1e-4))
+    assert H.rel(_np(lat.unpack_momenta(m)), mom - 0.05 * Fo) < 1e-6
+
+
 # ------------------------------------------------------------------ molecular dynamics
 def test_link_update_and_kick(lgt, ora):
     dims = (6, 4, 4, 8)
@@ -305,6 +328,23 @@ def test_md_reversibility_gpu(lgt):
     run()
     assert H.rel(_np(lat.get_links()), U0) < 1e-11
     assert (torch.linalg.norm(mom + m0) / torch.linalg.norm(m0)).item() < 1e-10
+
+
+def test_link_grid_reductions_large_volume(lgt, ora):
+    """Reductions over one thread per link (kinetic energy) use 8 Vh / 128 partial
+    sums; at 16^3 x 48 that exceeds a site-sized buffer.  The energy must match the
+    oracle and a following solve must still converge (reduction state intact)."""
+    dims = (16, 16, 16, 48)
+    lat = lgt.Lattice(dims)
+    lat.random_links(5, 0.5)
+    mom = lat.gaussian_momenta(6, 2)
+    K = lat.kinetic_energy(mom)
+    Ko = ora.momentum_energy(dims, ora.gaussian_momenta(dims, 6, 2))
+    assert abs(K - Ko) / Ko < 1e-13
+    assert abs(lat.plaquette() - ora.plaquette(dims, ora.random_links(dims, 5, 0.5))) < 1e-13
+    b = lat.gaussian_spinor(7, 0, lgt.FIELD_SOURCE, lgt.EVEN)
+    x, st = lat.cg_solve(b, 0.155, True, lgt.solver("mixed", tol=1e-10, max_iter=2000))
+    assert st["true_rel_residual"] <= 1e-10 and st["iters"] < 2000
 
 
 # ------------------------------------------------------------------ full size (bench workload)

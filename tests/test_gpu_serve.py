@@ -1,0 +1,130 @@
+"""Serving: continuous batching of Dirac solves and force evaluations over
+resident gauge fields of different volumes.  Results are checked against the
+oracle, and each result is the same alone and inside a mix of requests."""
+import numpy as np
+import pytest
+import torch
+
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+@pytest.fixture(scope="module")
+def serve():
+    from paper_2602_20516_b300 import serve as S
+    return S
+
+
+def _full_canonical(field, dims):
+    """(2, 12, Vh, 2) device field -> canonical (V, 4, 3) numpy."""
+    from paper_2602_20516_b300 import lgt
+    lat = lgt.Lattice(dims)
+    return lat.unpack_spinor(field, lgt.FULL, lgt.FP64).cpu().numpy()
+
+
+def _mom_canonical(field, dims):
+    from paper_2602_20516_b300 import lgt
+    lat = lgt.Lattice(dims)
+    return lat.unpack_momenta(field).cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_and_force_vs_oracle(serve, ora, precision):
+    srv = serve.Server(4 * GB, max_active=8, batch_iters=4)
+    dims = (6, 4, 4, 8)
+    g = srv.add_gauge(dims, 11, 0.5)
+    Uo = ora.random_links(dims, 11, 0.5)          # the oracle draws the same field itself
+    tol = 1e-12 if precision == "fp64" else 1e-10
+    rs = srv.submit(g, serve.SOLVE, 0.15, precision, tol=tol, source_seed=5, keep_result=True)
+    rf = srv.submit(g, serve.FORCE, 0.15, precision, tol=tol, source_seed=6, beta=5.8, keep_result=True)
+    done = {c["id"]: c for c in srv.run_until_idle()}
+    assert done[rs]["status"] == 0 and done[rf]["status"] == 0
+    bar = 1e-9 if precision == "fp64" else 1e-6
+    # solve: x = D^{-1} b, b from Philox (source field)
+    b = ora.gaussian_spinor(dims, 5, 0, ora.FIELD_SOURCE, 3)
+    xo, _, _ = ora.cg(dims, Uo, 0.15, ora.dirac(dims, Uo, 0.15, b, dagger=True), tol=1e-13)
+    x = _full_canonical(srv.result(rs), dims)
+    assert H.rel(x, xo) < bar
+    # force: gauge + even-odd pseudofermion force with phi_e from Philox
+    phi = ora.gaussian_spinor(dims, 6, 0, ora.FIELD_SOURCE, 1)
+    Fo = ora.gauge_force(dims, Uo, 5.8) + ora.pf_force(dims, Uo, 0.15, phi, eo=True, tol=1e-13)[0]
+    F = _mom_canonical(srv.result(rf), dims)
+    assert H.rel(F, Fo) < bar
+    srv.close()
+
+
+def test_result_same_alone_and_in_mix(serve):
+    """A request's result is bitwise identical whether it runs alone or batched
+    with requests of other volumes and precisions arriving around it."""
+    dims_list = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (8, 8, 8, 16)]
+    probes = [dict(kind=serve.SOLVE, kappa=0.152, precision="mixed", tol=1e-10, source_seed=101),
+              dict(kind=serve.FORCE, kappa=0.149, precision="fp64", tol=1e-10, source_seed=102, beta=5.8)]
+    alone = []
+    for p in probes:
+        srv = serve.Server(16 * GB, max_active=32, batch_iters=8)
+        gids = [srv.add_gauge(d, 20 + k, 0.45) for k, d in enumerate(dims_list)]
+        rid = srv.submit(gids[1], keep_result=True, **p)
+        srv.run_until_idle()
+        alone.append(srv.result(rid).clone())
+        srv.close()
+    srv = serve.Server(16 * GB, max_active=32, batch_iters=8)
+    gids = [srv.add_gauge(d, 20 + k, 0.45) for k, d in enumerate(dims_list)]
+    mix = serve.workload(gids, 24, seed=3)
+    ids = []
+    for k, r in enumerate(mix):
+        srv.submit(**r)
+        if k == 5:
+            ids.append(srv.submit(gids[1], keep_result=True, **probes[0]))
+        if k % 6 == 0:
+            srv.step()
+        if k == 17:
+            ids.append(srv.submit(gids[1], keep_result=True, **probes[1]))
+    done = srv.run_until_idle()
+    assert all(c["status"] == 0 for c in done)
+    for rid, ref in zip(ids, alone):
+        assert torch.equal(srv.result(rid), ref)
+    srv.close()
+
+
+def test_budget_admission_and_refusal(serve):
+    """Under a tight budget requests wait for memory and all finish; a request that
+    can never fit is refused with LGT_ENOMEM."""
+    srv = serve.Server(int(0.25 * GB), max_active=16, batch_iters=8)
+    g_small = srv.add_gauge((8, 8, 8, 8), 1, 0.4)
+    g_mid = srv.add_gauge((16, 16, 16, 16), 2, 0.4)
+    for k in range(12):
+        srv.submit(g_mid if k % 2 else g_small, serve.SOLVE, 0.15, "mixed", source_seed=k + 1)
+    peak_active, peak_used = 0, 0
+    done = []
+    while True:
+        a, q = srv.step()
+        info = srv.info()
+        peak_active = max(peak_active, a)
+        peak_used = max(peak_used, info["used_bytes"])
+        done += srv.poll()
+        if a == 0 and q == 0:
+            break
+    assert len(done) == 12 and all(c["status"] == 0 for c in done)
+    assert peak_used <= 0.25 * GB and peak_active < 12
+    srv.close()
+    # 4 MiB: the 8^4 gauge field (3.1 MiB) fits, a force request (~6 MiB) never can
+    tiny = serve.Server(4 << 20, max_active=4, batch_iters=4)
+    g = tiny.add_gauge((8, 8, 8, 8), 1, 0.4)
+    tiny.submit(g, serve.FORCE, 0.15, "fp64", source_seed=1, beta=5.8)
+    done = tiny.run_until_idle()
+    assert len(done) == 1 and done[0]["status"] == 2   # LGT_ENOMEM
+    tiny.close()
+
+
+def test_poisson_latency_smoke(serve):
+    srv = serve.Server(8 * GB, max_active=32, batch_iters=8)
+    gids = [srv.add_gauge(d, 30 + k, 0.5) for k, d in enumerate([(8, 8, 8, 8), (12, 12, 12, 12)])]
+    reqs = serve.workload(gids, 40, seed=9)
+    thr, _ = serve.saturated(srv, reqs)
+    done = serve.poisson(srv, serve.workload(gids, 60, seed=10), 0.5 * thr, seed=11, warmup=5)
+    st = serve.latency_stats(done)
+    assert st["n"] == 55 and st["p99_ms"] >= st["p50_ms"] > 0
+    srv.close()
