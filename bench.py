@@ -54,8 +54,8 @@ HOP_FLOPS = 1320
 HOP_MIN_MS = 0.010
 # ncu DRAM traffic (read + write) of one FP32 hop launch at 32^3 x 64, and the hash of
 # the kernel sources it was taken from (traffic is reported as null once they change)
-NCU_TRAFFIC = {"bytes": 595180544,
-               "sources_sha256": "433e5646e12b17044d29d6cde82935dae3fb2a69faac405135981dbb89a3f739"}
+NCU_TRAFFIC = {"bytes": 594124544,
+               "sources_sha256": "536d9e3e5c675235ac377096557add97b640d649c97d784a4a95517511f14c6f"}
 HOP_SOURCES = ["paper_2602_20516_b300/csrc/lgt_dirac.cu", "paper_2602_20516_b300/csrc/lgt_spin.cuh",
                "paper_2602_20516_b300/csrc/lgt_common.cuh"]
 

@@ -762,7 +762,7 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
 static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk, const lgt_action_params* ap,
                     const double2* phi, const lgt_solver_params* sp, double coef, int keep, int form, double2* out,
                     lgt_solve_stats* stats) {
-    const bool fp32 = form == 0 && sp && sp->precision == LGT_MIXED;
+    const bool fp32 = form == 0 && sp && sp->precision == LGT_MIXED && !ap->force_fp64;
     if (ap->fermions) {
         if (!phi) return fail(LGT_EINVAL, "null phi");
         TRY(ensure_solver(L));
