@@ -182,18 +182,27 @@ def run_ours(args):
     lat.random_links(SEED + rank, ALPHA)
     phi = lat.gaussian_spinor(SEED + rank, 0, lgt.FIELD_SOURCE, lgt.EVEN)
     mom = lat.gaussian_momenta(SEED + rank, 0)
+    # every phase (mixed, FP64, FP32 forces, e2e) starts from this same state, so
+    # they run the same MD steps on the same fields
+    U_start = lat.get_links()
+    mom_start = mom.clone()
+
+    def restore():
+        lat.set_links(U_start)
+        mom.copy_(mom_start)
     ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True)
     stream = torch.cuda.current_stream()
 
-    def step(sp, stats):
-        s = lat.md_update(mom, EPS, lgt.UPDATE_P, ap, phi, sp)
+    def step(sp, stats, a=ap):
+        s = lat.md_update(mom, EPS, lgt.UPDATE_P, a, phi, sp)
         lat.md_update(mom, EPS, lgt.UPDATE_U)
         stats.append(s)
 
-    def timed(sp, K, W, kernel_timing=False, clocks=None):
+    def timed(sp, K, W, kernel_timing=False, clocks=None, a=ap):
         st = []
+        restore()
         for _ in range(W):
-            step(sp, st)
+            step(sp, st, a)
         st.clear()
         torch.cuda.synchronize()
         barrier()
@@ -206,7 +215,7 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(K):
-            step(sp, st)
+            step(sp, st, a)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -229,16 +238,26 @@ def run_ours(args):
 
     # FP64 path, same workload
     K64 = max(1, min(K, args.fp64_steps))
-    ms64, st64, _, kt64, _ = timed(lgt.solver("fp64", tol=TOL), K64, 1, kernel_timing=True)
+    ms64, st64, _, kt64, _ = timed(lgt.solver("fp64", tol=TOL), K64, W, kernel_timing=True)
     ms64 = max_over_ranks(ms64)
     value64 = world * K64 / (ms64 / 1e3)
     iters64 = statistics.mean(s["iters"] for s in st64)
+
+    # the same workload with FP32 force arithmetic (an option: ~1e-7 force error, moves
+    # Delta H by ~1e-4 relative, so the headline keeps FP64 forces)
+    ap32 = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_fp32=True)
+    K32 = K
+    ms32f, _, _, _, _ = timed(sp_mixed, K32, W, a=ap32)
+    value32f = world * K32 / (max_over_ranks(ms32f) / 1e3)
+    restore()
+    Ff, _ = lat.force(ap32, phi, sp_mixed)
 
     # error of the mixed force against the FP64 path on the same field
     Fm, _ = lat.force(ap, phi, sp_mixed)
     Fd, _ = lat.force(ap, phi, lgt.solver("fp64", tol=TOL))
     force_err = (torch.linalg.norm(Fm - Fd) / torch.linalg.norm(Fd)).item()
-    del Fm, Fd
+    force_err32 = (torch.linalg.norm(Ff - Fd) / torch.linalg.norm(Fd)).item()
+    del Fm, Fd, Ff
 
     # dominant kernel: the FP32 hop, timed with CUDA events on its stream inside the
     # timed region; each epilogue variant counts its own algorithmic bytes
@@ -312,6 +331,8 @@ def run_ours(args):
            "fp64": {"value": value64, "ms_per_step": ms64 / K64, "steps": K64, "cg_iters_per_step": iters64,
                     "mixed_speedup": value / value64,
                     "mixed_force_rel_err_vs_fp64_path": force_err},
+           "fp32_force_arithmetic": {"value": value32f, "ms_per_step": ms32f / K32, "steps": K32,
+                                     "force_rel_err_vs_fp64_path": force_err32},
            "dslash": {"fp32_hop_avg_us": hop32_ms * 1e3, "fp32_hop_GBs_algorithmic": achieved,
                       "fp32_variants": per_variant,
                       "fp32_hop_launches": n32, "skipped_hop_launches": n32_short,
@@ -455,7 +476,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=10,
+                    help="timed steps of the FP64 path (the first ones of the same MD sequence)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -92,9 +92,9 @@ typedef struct {
     double rho;       /* stout parameter */
     int stout_recompute; /* 0: keep every smeared level for the adjoint;
                             1: keep only the top level and recompute the others */
-    int force_fp64;      /* 1: FP64 force arithmetic with the mixed solver too; 0: the
-                            mixed solver's Lie-form forces use FP32 arithmetic with FP64
-                            accumulation (about 1e-7 relative) */
+    int force_fp32;      /* 0: FP64 force arithmetic (default); 1: with the mixed solver,
+                            Lie-form forces use FP32 arithmetic accumulated in FP64 (about
+                            1e-7 relative; moves an MD trajectory's Delta H by ~1e-4) */
 } lgt_action_params;
 
 typedef struct {

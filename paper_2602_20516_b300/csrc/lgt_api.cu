@@ -757,12 +757,13 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
 }
 
 // out = keep*out + coef * (dS_G + dS_f) in Lie (form 0) or G (form 1) layout, on the
-// links the actions see (no smearing here).  With the mixed solver the Lie form is
-// computed in FP32 arithmetic (X, Y, staples, outer products) and accumulated in FP64.
+// links the actions see (no smearing here).  With the mixed solver and force_fp32 the
+// Lie form is computed in FP32 arithmetic (X, Y, staples, outer products) and
+// accumulated in FP64; otherwise every force kernel is FP64.
 static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk, const lgt_action_params* ap,
                     const double2* phi, const lgt_solver_params* sp, double coef, int keep, int form, double2* out,
                     lgt_solve_stats* stats) {
-    const bool fp32 = form == 0 && sp && sp->precision == LGT_MIXED && !ap->force_fp64;
+    const bool fp32 = form == 0 && sp && sp->precision == LGT_MIXED && ap->force_fp32;
     if (ap->fermions) {
         if (!phi) return fail(LGT_EINVAL, "null phi");
         TRY(ensure_solver(L));

@@ -49,7 +49,7 @@ class SolveStats(C.Structure):
 class ActionParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("fermions", C.c_int),
                 ("even_odd", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double),
-                ("stout_recompute", C.c_int), ("force_fp64", C.c_int)]
+                ("stout_recompute", C.c_int), ("force_fp32", C.c_int)]
 
 
 class HMCParams(C.Structure):
@@ -182,9 +182,9 @@ def solver(precision="fp64", tol=1e-10, max_iter=10000, delta=1e-3, check_every=
 
 
 def action_params(beta=0.0, kappa=0.0, fermions=True, even_odd=False, n_stout=0, rho=0.0,
-                  stout_recompute=False, force_fp64=False):
+                  stout_recompute=False, force_fp32=False):
     return ActionParams(beta, kappa, int(fermions), int(even_odd), n_stout, rho, int(stout_recompute),
-                        int(force_fp64))
+                        int(force_fp32))
 
 
 def hmc_params(integrator="leapfrog", n_steps=10, tau=1.0, md_solver=None, action_solver=None):

@@ -225,19 +225,21 @@ def test_total_force_link_level_error_cdf(lgt, ora):
 
 
 @pytest.mark.parametrize("eo", [False, True])
-def test_mixed_total_force(lgt, ora, eo):
-    """Mixed path: FP32 CG with FP64 reliable updates, FP32 force arithmetic
-    accumulated in FP64; within 1e-6 of the FP64 oracle (whole field and per link)."""
+@pytest.mark.parametrize("force_fp32", [False, True])
+def test_mixed_total_force(lgt, ora, eo, force_fp32):
+    """Mixed path: FP32 CG with FP64 reliable updates; FP64 force arithmetic (default)
+    or FP32 force arithmetic accumulated in FP64 (force_fp32).  Within 1e-6 of the
+    FP64 oracle (whole field and per link); the FP64-force path within 1e-7."""
     dims = (8, 6, 4, 10)
     U = synth.random_links(dims, 0.5, 27)
     phi = synth.gaussian_spinor(dims, 28, parity_mask=1 if eo else 3)
     lat = _lat(lgt, dims, U)
-    ap = lgt.action_params(beta=5.8, kappa=0.156, even_odd=eo)
+    ap = lgt.action_params(beta=5.8, kappa=0.156, even_odd=eo, force_fp32=force_fp32)
     pf = lat.pack_spinor(phi, lgt.EVEN if eo else lgt.FULL, lgt.FP64)
     F, st = lat.force(ap, pf, lgt.solver("mixed", tol=1e-10, delta=1e-4))
     Fo = ora.gauge_force(dims, U, 5.8) + ora.pf_force(dims, U, 0.156, phi, eo=eo, tol=1e-13)[0]
     Fg = _np(lat.unpack_momenta(F))
-    assert H.rel(Fg, Fo) < 1e-6
+    assert H.rel(Fg, Fo) < (1e-6 if force_fp32 else 1e-7)
     eps = np.linalg.norm(Fg - Fo, axis=-1) / np.linalg.norm(Fo, axis=-1)
     assert np.quantile(eps, 0.999) < 1e-5
     # the kick applies exactly this force: mom - eps F
@@ -303,6 +305,24 @@ def test_hmc_trajectory_matches_oracle(lgt, ora, integrator, eo):
     assert abs(r["dH"] - ro["dH"]) < 1e-8 * max(1.0, abs(ro["dH"]))
     assert r["accepted"] == ro["accepted"] and r["force_evals"] == ro["force_evals"]
     assert H.rel(_np(lat.get_links()), Uo) < 1e-10
+
+
+def test_hmc_mixed_vs_fp64_delta_h(lgt):
+    """Same start, same seeds: the mixed path (FP32 CG, FP64 reliable updates, FP64
+    forces) reproduces the FP64 path's Delta H within 1e-6 relative; FP32 force
+    arithmetic moves it by O(1e-4) and is only asked to stay within 1e-2."""
+    dims = (8, 8, 8, 8)
+    lat = lgt.Lattice(dims)
+    lat.random_links(4, 0.5)
+    U0 = lat.get_links()
+    dH = {}
+    for name, prec, f32 in (("fp64", "fp64", False), ("mixed", "mixed", False), ("mixed_f32", "mixed", True)):
+        lat.set_links(U0)
+        sp = lgt.solver(prec, tol=1e-10, delta=1e-4)
+        ap = lgt.action_params(beta=5.8, kappa=0.156, even_odd=True, force_fp32=f32)
+        dH[name] = lat.hmc_trajectory(ap, lgt.hmc_params("omelyan", 20, 1.0, sp, sp), 4, 0)["dH"]
+    assert abs(dH["mixed"] - dH["fp64"]) <= 1e-6 * abs(dH["fp64"]) + 1e-9
+    assert abs(dH["mixed_f32"] - dH["fp64"]) <= 1e-2 * abs(dH["fp64"]) + 1e-6
 
 
 def test_md_reversibility_gpu(lgt):
