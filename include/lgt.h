@@ -68,7 +68,10 @@ enum { LGT_OP_HOP = 0,       /* out_p = H_{p,1-p} in_{1-p}, p = out_parity (EVEN
        LGT_OP_D = 1,         /* out = D in on the full lattice */
        LGT_OP_DHAT = 2,      /* out_e = Dhat in_e */
        LGT_OP_DHAT_NORMAL = 3 /* out_e = Dhat^+ Dhat in_e (dagger ignored) */ };
-enum { LGT_LEAPFROG = 0, LGT_OMELYAN2MN = 1 };
+/* integrators: leapfrog (PQP), Omelyan 2MN, Sexton-Weingarten nested leapfrog (the
+ * multiple time-scale integrator of Sec. III B: fermion force on the outer scale,
+ * n_inner gauge-force leapfrog steps per outer step) */
+enum { LGT_LEAPFROG = 0, LGT_OMELYAN2MN = 1, LGT_SEXTON_WEINGARTEN = 2 };
 enum { LGT_FORCE_LIE = 0, LGT_GRAD_G = 1 };
 enum { LGT_UPDATE_U = 0, LGT_UPDATE_P = 1 };
 
@@ -118,6 +121,7 @@ typedef struct {
     double tau;
     lgt_solver_params md_solver;      /* solves inside force evaluations */
     lgt_solver_params action_solver;  /* solve of the final action */
+    int n_inner;                      /* LGT_SEXTON_WEINGARTEN: gauge steps per outer step */
 } lgt_hmc_params;
 
 typedef struct {

@@ -35,7 +35,7 @@ class HMCParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("eo", C.c_int),
                 ("fermions", C.c_int), ("integrator", C.c_int), ("n_steps", C.c_int),
                 ("tau", C.c_double), ("tol_md", C.c_double), ("tol_action", C.c_double),
-                ("max_iter", C.c_int)]
+                ("max_iter", C.c_int), ("n_inner", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double)]
 
 
 class HMCResult(C.Structure):
@@ -84,6 +84,8 @@ def lib():
             "ora_stout_forward": (None, [_ip, _cp, C.c_double, _cp]),
             "ora_stout_backward": (None, [_ip, _cp, C.c_double, _cp, _cp]),
             "ora_md_force": (C.c_int, [_ip, _cp, C.POINTER(HMCParams), _cp, _dp]),
+            "ora_md_force_part": (C.c_int, [_ip, _cp, C.POINTER(HMCParams), _cp, C.c_int, _dp]),
+            "ora_hamiltonian": (C.c_double, [_ip, _cp, _dp, _cp, C.POINTER(HMCParams)]),
             "ora_md_integrate": (C.c_int, [_ip, _cp, _dp, _cp, C.POINTER(HMCParams)]),
             "ora_hmc_trajectory": (C.c_int, [_ip, _cp, C.POINTER(HMCParams), C.c_uint64, C.c_uint32, C.POINTER(HMCResult)]),
         }
@@ -295,18 +297,25 @@ def stout_backward(dims, U, rho, Gout):
 
 
 # ---------------------------------------------------------------- HMC
+INTEGRATORS = {"leapfrog": 0, "omelyan": 1, "sexton_weingarten": 2}
+
+
 def hmc_params(beta, kappa, eo=False, fermions=True, integrator="leapfrog", n_steps=10,
-               tau=1.0, tol_md=1e-12, tol_action=1e-12, max_iter=10000):
-    return HMCParams(beta, kappa, int(eo), int(fermions),
-                     0 if integrator == "leapfrog" else 1, n_steps, tau, tol_md, tol_action,
-                     max_iter)
+               tau=1.0, tol_md=1e-12, tol_action=1e-12, max_iter=10000, n_inner=1, n_stout=0, rho=0.0):
+    return HMCParams(beta, kappa, int(eo), int(fermions), INTEGRATORS[integrator], n_steps, tau, tol_md,
+                     tol_action, max_iter, n_inner, n_stout, rho)
 
 
-def md_force(dims, U, params, phi):
+def md_force(dims, U, params, phi, part=0):
+    """MD force (Lie components); part 0 all, 1 gauge only, 2 fermion only."""
     d = _dims(dims)
     F = np.zeros((volume(d), 4, 8))
-    lib().ora_md_force(d, _c(U), C.byref(params), _c(phi), F)
+    lib().ora_md_force_part(d, _c(U), C.byref(params), _c(phi), part, F)
     return F
+
+
+def hamiltonian(dims, U, mom, phi, params):
+    return lib().ora_hamiltonian(_dims(dims), _c(U), _c(mom, np.float64), _c(phi), C.byref(params))
 
 
 def md_integrate(dims, U, mom, phi, params):

@@ -1,6 +1,10 @@
 /*
  * ora_hmc.c -- molecular dynamics and one HMC trajectory with the left update
- * of Eq. S2.1 / S2.2, leapfrog (PQP) or Omelyan 2MN, Metropolis on Delta H.
+ * of Eq. S2.1 / S2.2: leapfrog (PQP), Omelyan 2MN, or a Sexton-Weingarten
+ * nested leapfrog (gauge force on the inner time scale), Metropolis on Delta H.
+ * With stout smearing the pseudofermion action sees the smeared links and its
+ * force is taken back through every level (the reverse recursion of Eq. 3);
+ * the gauge action sees the thin links.
  * Test infrastructure only (see oracle.h).
  */
 #include "oracle.h"
@@ -9,21 +13,82 @@
 #include <stdlib.h>
 #include <string.h>
 
-int ora_md_force(const int d[4], const ocplx *U, const ora_hmc_params *p, const ocplx *phi,
-                 double *F)
+/* levels[0] = U, levels[k] = stout(levels[k-1]); caller frees levels[1..n] */
+static ocplx **smear_levels(const int d[4], const ocplx *U, int n, double rho)
 {
-    long n = ora_volume(d) * 32;
-    memset(F, 0, n * sizeof(double));
-    ora_gauge_force(d, U, p->beta, 1.0, F);
-    if (!p->fermions) return 0;
-    int it = ora_pf_force(d, U, p->kappa, p->eo, phi, p->tol_md, p->max_iter, 1.0, F);
+    long V = ora_volume(d);
+    ocplx **lv = malloc(sizeof(ocplx *) * (n + 1));
+    lv[0] = (ocplx *)U;
+    for (int k = 1; k <= n; ++k) {
+        lv[k] = malloc(sizeof(ocplx) * 36 * V);
+        ora_stout_forward(d, lv[k - 1], rho, lv[k]);
+    }
+    return lv;
+}
+
+static void free_levels(ocplx **lv, int n)
+{
+    for (int k = 1; k <= n; ++k) free(lv[k]);
+    free(lv);
+}
+
+int ora_md_force_part(const int d[4], const ocplx *U, const ora_hmc_params *p, const ocplx *phi,
+                      int part, double *F)
+{
+    long V = ora_volume(d);
+    memset(F, 0, V * 32 * sizeof(double));
+    if (part != 2 && p->beta != 0.0) ora_gauge_force(d, U, p->beta, 1.0, F);
+    if (part == 1 || !p->fermions) return 0;
+    int it;
+    if (p->n_stout == 0) {
+        it = ora_pf_force(d, U, p->kappa, p->eo, phi, p->tol_md, p->max_iter, 1.0, F);
+    } else {
+        ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
+        ocplx *G = malloc(sizeof(ocplx) * 36 * V);
+        ocplx *G2 = malloc(sizeof(ocplx) * 36 * V);
+        double *Ff = malloc(sizeof(double) * 32 * V);
+        it = ora_pf_action_grad(d, lv[p->n_stout], p->kappa, p->eo, phi, p->tol_md, p->max_iter, G);
+        for (int k = p->n_stout; k >= 1; --k) {
+            ora_stout_backward(d, lv[k - 1], p->rho, G, G2);
+            ocplx *t = G; G = G2; G2 = t;
+        }
+        ora_grad_to_force(d, U, G, Ff);
+        for (long i = 0; i < V * 32; ++i) F[i] += Ff[i];
+        free(G); free(G2); free(Ff);
+        free_levels(lv, p->n_stout);
+    }
     return it < 0 ? -it : it;
 }
 
-static int kick(const int d[4], const ocplx *U, double *mom, const ocplx *phi,
-                const ora_hmc_params *p, double eps, double *F, int *evals)
+int ora_md_force(const int d[4], const ocplx *U, const ora_hmc_params *p, const ocplx *phi,
+                 double *F)
 {
-    int it = ora_md_force(d, U, p, phi, F);
+    return ora_md_force_part(d, U, p, phi, 0, F);
+}
+
+static double pf_action_smeared(const int d[4], const ocplx *U, const ora_hmc_params *p,
+                                const ocplx *phi, int *it)
+{
+    if (p->n_stout == 0) return ora_pf_action(d, U, p->kappa, p->eo, phi, p->tol_action, p->max_iter, it);
+    ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
+    double S = ora_pf_action(d, lv[p->n_stout], p->kappa, p->eo, phi, p->tol_action, p->max_iter, it);
+    free_levels(lv, p->n_stout);
+    return S;
+}
+
+double ora_hamiltonian(const int d[4], const ocplx *U, const double *mom, const ocplx *phi,
+                       const ora_hmc_params *p)
+{
+    int it;
+    double H = ora_momentum_energy(d, mom) + ora_gauge_action(d, U, p->beta);
+    if (p->fermions) H += pf_action_smeared(d, U, p, phi, &it);
+    return H;
+}
+
+static int kick(const int d[4], const ocplx *U, double *mom, const ocplx *phi,
+                const ora_hmc_params *p, double eps, int part, double *F, int *evals)
+{
+    int it = ora_md_force_part(d, U, p, phi, part, F);
     ora_kick(d, mom, F, eps);
     ++*evals;
     return it;
@@ -37,20 +102,34 @@ static int integrate(const int d[4], ocplx *U, double *mom, const ocplx *phi,
     double eps = p->tau / p->n_steps;
     int iters = 0;
     if (p->integrator == 0) {
-        iters += kick(d, U, mom, phi, p, 0.5 * eps, F, evals);
+        iters += kick(d, U, mom, phi, p, 0.5 * eps, 0, F, evals);
         for (int i = 0; i < p->n_steps; ++i) {
             ora_update_links(d, U, mom, eps);
-            iters += kick(d, U, mom, phi, p, (i + 1 < p->n_steps) ? eps : 0.5 * eps, F, evals);
+            iters += kick(d, U, mom, phi, p, (i + 1 < p->n_steps) ? eps : 0.5 * eps, 0, F, evals);
         }
-    } else {
+    } else if (p->integrator == 1) {
         const double lam = 0.1931833275037836;
-        iters += kick(d, U, mom, phi, p, lam * eps, F, evals);
+        iters += kick(d, U, mom, phi, p, lam * eps, 0, F, evals);
         for (int i = 0; i < p->n_steps; ++i) {
             ora_update_links(d, U, mom, 0.5 * eps);
-            iters += kick(d, U, mom, phi, p, (1.0 - 2.0 * lam) * eps, F, evals);
+            iters += kick(d, U, mom, phi, p, (1.0 - 2.0 * lam) * eps, 0, F, evals);
             ora_update_links(d, U, mom, 0.5 * eps);
             iters += kick(d, U, mom, phi, p, (i + 1 < p->n_steps) ? 2.0 * lam * eps : lam * eps,
-                          F, evals);
+                          0, F, evals);
+        }
+    } else {
+        /* Sexton-Weingarten: outer leapfrog with the fermion force; every outer
+         * step runs n_inner leapfrog steps of the gauge force */
+        const int m = p->n_inner > 0 ? p->n_inner : 1;
+        const double ein = eps / m;
+        iters += kick(d, U, mom, phi, p, 0.5 * eps, 2, F, evals);
+        for (int i = 0; i < p->n_steps; ++i) {
+            kick(d, U, mom, phi, p, 0.5 * ein, 1, F, evals);
+            for (int j = 0; j < m; ++j) {
+                ora_update_links(d, U, mom, ein);
+                kick(d, U, mom, phi, p, (j + 1 < m) ? ein : 0.5 * ein, 1, F, evals);
+            }
+            iters += kick(d, U, mom, phi, p, (i + 1 < p->n_steps) ? eps : 0.5 * eps, 2, F, evals);
         }
     }
     free(F);
@@ -81,9 +160,11 @@ int ora_hmc_trajectory(const int d[4], ocplx *U, const ora_hmc_params *p, uint64
     if (p->fermions) {
         int mask = p->eo ? 1 : 3;
         ora_gaussian_spinor(d, seed, traj, ORA_FIELD_XI, mask, xi);
-        /* phi = M^+ xi, so S_f(old) = xi^+ xi exactly */
-        if (p->eo) ora_dhat(d, U, p->kappa, xi, phi, 1);
-        else ora_dirac(d, U, p->kappa, xi, phi, 1);
+        /* phi = M^+ xi on the links the pseudofermion action sees: S_f(old) = xi^+ xi */
+        ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
+        if (p->eo) ora_dhat(d, lv[p->n_stout], p->kappa, xi, phi, 1);
+        else ora_dirac(d, lv[p->n_stout], p->kappa, xi, phi, 1);
+        free_levels(lv, p->n_stout);
         res->Sf_old = ora_norm2(d, xi, mask);
     }
     int evals = 0;
@@ -93,7 +174,7 @@ int ora_hmc_trajectory(const int d[4], ocplx *U, const ora_hmc_params *p, uint64
     res->Sg_new = ora_gauge_action(d, U, p->beta);
     if (p->fermions) {
         int it = 0;
-        res->Sf_new = ora_pf_action(d, U, p->kappa, p->eo, phi, p->tol_action, p->max_iter, &it);
+        res->Sf_new = pf_action_smeared(d, U, p, phi, &it);
         res->cg_iters += it < 0 ? -it : it;
     }
     res->dH = (res->K_new + res->Sg_new + res->Sf_new) - (res->K_old + res->Sg_old + res->Sf_old);

@@ -129,12 +129,22 @@ typedef struct {
     double beta, kappa;
     int eo;              /* 0: full-lattice pseudofermion, 1: even-odd */
     int fermions;        /* 0: pure gauge */
-    int integrator;      /* 0: leapfrog (PQP), 1: Omelyan 2MN */
+    int integrator;      /* 0: leapfrog (PQP), 1: Omelyan 2MN, 2: Sexton-Weingarten */
     int n_steps;
     double tau;
     double tol_md, tol_action;
     int max_iter;
+    int n_inner;         /* Sexton-Weingarten: gauge-force steps per outer step */
+    int n_stout;         /* stout levels in front of the Wilson operator (S_G: thin links) */
+    double rho;
 } ora_hmc_params;
+
+/* parts of the MD force: 0 all, 1 gauge only, 2 fermion only */
+int ora_md_force_part(const int d[4], const ocplx *U, const ora_hmc_params *p, const ocplx *phi,
+                      int part, double *F);
+/* H = K + S_G + S_f(smeared links) for given momenta and phi (S_f by the variational form) */
+double ora_hamiltonian(const int d[4], const ocplx *U, const double *mom, const ocplx *phi,
+                       const ora_hmc_params *p);
 
 typedef struct {
     double dH, Sg_old, Sg_new, Sf_old, Sf_new, K_old, K_new, plaquette;

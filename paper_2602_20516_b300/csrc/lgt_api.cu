@@ -881,7 +881,8 @@ extern "C" int lgt_force(lgt_lattice_t L, const lgt_action_params* ap, const dou
 // mom -= eps F
 static int kick(lgt_lattice* L, double2* mom, double eps, const lgt_action_params* ap, const double2* phi,
                 const lgt_solver_params* sp, lgt_solve_stats* stats) {
-    if (ap->n_stout == 0) return force_on(L, L->thin, L->thin, ap, phi, sp, -eps, 1, 0, mom, stats);
+    // the gauge action always sees thin links: only a fermion part goes through smearing
+    if (ap->n_stout == 0 || !ap->fermions) return force_on(L, L->thin, L->thin, ap, phi, sp, -eps, 1, 0, mom, stats);
     TRY(ensure_md(L));
     TRY(force_grad_stout(L, ap, phi, sp, L->G, stats));
     CK(grad_to_lie(L->F, L->G, L->thin.U, L->g, L->st));
@@ -950,6 +951,30 @@ static int integrate(lgt_lattice* L, const lgt_action_params* ap, const lgt_hmc_
             TRY(K((1.0 - 2.0 * lam) * eps));
             TRY(Uup(0.5 * eps));
             TRY(K(i + 1 < hp->n_steps ? 2.0 * lam * eps : lam * eps));
+        }
+    } else if (hp->integrator == LGT_SEXTON_WEINGARTEN) {
+        // outer leapfrog with the fermion force; each outer step runs n_inner leapfrog
+        // steps of the gauge force (the cheap, stiff part) at eps / n_inner
+        lgt_action_params apF = *ap, apG = *ap;
+        apF.beta = 0.0;
+        apG.fermions = 0;
+        const int m = hp->n_inner > 0 ? hp->n_inner : 1;
+        const double ein = eps / m;
+        auto KP = [&](const lgt_action_params* a, double e) -> int {
+            s = lgt_solve_stats{0, 0, 0.0, 0.0};
+            int r = kick(L, L->mom, e, a, phi, &hp->md_solver, &s);
+            add_stats(tot, s);
+            ++*evals;
+            return r;
+        };
+        TRY(KP(&apF, 0.5 * eps));
+        for (int i = 0; i < hp->n_steps; ++i) {
+            TRY(KP(&apG, 0.5 * ein));
+            for (int j = 0; j < m; ++j) {
+                TRY(Uup(ein));
+                TRY(KP(&apG, j + 1 < m ? ein : 0.5 * ein));
+            }
+            TRY(KP(&apF, i + 1 < hp->n_steps ? eps : 0.5 * eps));
         }
     } else {
         return fail(LGT_EINVAL, "integrator %d", hp->integrator);

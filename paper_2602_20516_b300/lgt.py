@@ -54,7 +54,7 @@ class ActionParams(C.Structure):
 
 class HMCParams(C.Structure):
     _fields_ = [("integrator", C.c_int), ("n_steps", C.c_int), ("tau", C.c_double),
-                ("md_solver", SolverParams), ("action_solver", SolverParams)]
+                ("md_solver", SolverParams), ("action_solver", SolverParams), ("n_inner", C.c_int)]
 
 
 class HMCResult(C.Structure):
@@ -187,9 +187,12 @@ def action_params(beta=0.0, kappa=0.0, fermions=True, even_odd=False, n_stout=0,
                         int(force_fp32))
 
 
-def hmc_params(integrator="leapfrog", n_steps=10, tau=1.0, md_solver=None, action_solver=None):
-    integ = {"leapfrog": LEAPFROG, "omelyan": OMELYAN2MN}[integrator]
-    return HMCParams(integ, n_steps, tau, md_solver or solver(), action_solver or solver())
+SEXTON_WEINGARTEN = 2
+
+
+def hmc_params(integrator="leapfrog", n_steps=10, tau=1.0, md_solver=None, action_solver=None, n_inner=1):
+    integ = {"leapfrog": LEAPFROG, "omelyan": OMELYAN2MN, "sexton_weingarten": SEXTON_WEINGARTEN}[integrator]
+    return HMCParams(integ, n_steps, tau, md_solver or solver(), action_solver or solver(), n_inner)
 
 
 def measure_fp64_peak():

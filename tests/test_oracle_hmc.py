@@ -87,3 +87,61 @@ def test_trajectory_heatbath_and_metropolis(ora):
     if not r["accepted"]:
         assert H.rel(U1, U) < 1e-14
     assert np.abs(U1 @ np.conj(np.swapaxes(U1, -1, -2)) - np.eye(3)).max() < 1e-14
+
+
+# ------------------------------------------------------------------ stout + Sexton-Weingarten
+def _sw_params(ora, n_steps, n_inner=10, tau=1.0, tol=1e-13):
+    return ora.hmc_params(5.7, 0.15, eo=False, integrator="sexton_weingarten", n_steps=n_steps,
+                          tau=tau, tol_md=tol, tol_action=tol, n_inner=n_inner, n_stout=1, rho=0.3)
+
+
+def test_stout_md_force_finite_difference(ora):
+    """The MD force of S_G(U) + S_f(stout(U)) (rho 0.3) against central differences
+    of that action in Lie directions."""
+    U, _ = _setup(seed=6)
+    phi = synth.gaussian_spinor(D4, 7)
+    p = _sw_params(ora, 4)
+    F = ora.md_force(D4, U, p, phi)
+    zero = np.zeros((256, 4, 8))
+    h = 1e-4   # |S| ~ 7e3: rounding / h and truncation h^2 balance near here
+    for (s, mu, a) in ((0, 0, 1), (77, 2, 4), (255, 3, 7), (130, 1, 0)):
+        Sp = ora.hamiltonian(D4, H.lie_perturb(U, s, mu, a, h), zero, phi, p)
+        Sm = ora.hamiltonian(D4, H.lie_perturb(U, s, mu, a, -h), zero, phi, p)
+        assert abs((Sp - Sm) / (2 * h) - F[s, mu, a]) < 5e-7 * max(1.0, abs(F[s, mu, a]))
+    # the parts add up
+    Fg = ora.md_force(D4, U, p, phi, part=1)
+    Ff = ora.md_force(D4, U, p, phi, part=2)
+    assert H.rel(Fg + Ff, F) < 1e-14
+
+
+def test_sexton_weingarten_reversible_and_reduces_to_leapfrog(ora):
+    U, mom = _setup(seed=8)
+    phi = synth.gaussian_spinor(D4, 9)
+    p = _sw_params(ora, 3, n_inner=4, tau=0.5, tol=1e-14)
+    U1, m1, _ = ora.md_integrate(D4, U, mom, phi, p)
+    U2, m2, _ = ora.md_integrate(D4, U1, -m1, phi, p)
+    assert H.rel(U2, U) < 1e-11 and H.rel(-m2, mom) < 1e-10
+    # one inner step: the same kicks as leapfrog, merged differently
+    p1 = _sw_params(ora, 4, n_inner=1, tau=0.5, tol=1e-14)
+    pl = ora.hmc_params(5.7, 0.15, integrator="leapfrog", n_steps=4, tau=0.5, tol_md=1e-14, n_stout=1, rho=0.3)
+    Ua, ma, _ = ora.md_integrate(D4, U, mom, phi, p1)
+    Ub, mb, _ = ora.md_integrate(D4, U, mom, phi, pl)
+    assert H.rel(Ua, Ub) < 1e-12 and H.rel(ma, mb) < 1e-11
+
+
+def test_sexton_weingarten_stout_delta_h_dt_squared(ora):
+    """The paper's second dynamical check (stout rho 0.3, Sexton-Weingarten with 10
+    inner steps): |Delta H| scales as dt^2 in the outer step."""
+    global ORA
+    ORA = ora
+    U, mom = _setup(seed=10)
+    phi = synth.gaussian_spinor(D4, 11)
+    ns = [4, 8, 16]
+    dh = []
+    for n in ns:
+        p = _sw_params(ora, n)
+        H0 = ora.hamiltonian(D4, U, mom, phi, p)
+        U1, m1, _ = ora.md_integrate(D4, U, mom, phi, p)
+        dh.append(abs(ora.hamiltonian(D4, U1, m1, phi, p) - H0))
+    slope = np.polyfit(np.log(1.0 / np.array(ns)), np.log(dh), 1)[0]
+    assert abs(slope - 2) < 0.25, (dh, slope)
