@@ -7,7 +7,9 @@ oracle as the baseline.
 
 One step = one MD update: a force evaluation from scratch (CG on Dhat^+ Dhat from a
 zero guess to tol 1e-10, X/Y vectors, fermion and gauge force fused into the
-momentum kick) followed by the link update U <- exp(i eps P) U.
+momentum kick) followed by the link update U <- exp(i eps P) U.  The mixed path
+runs the CG in FP32 with FP64 reliable updates and the forces in double-float
+(FP32-pair) arithmetic accumulated in FP64; the FP64 path is FP64 throughout.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --kernel hop32|hop64 [--reps R]   # a few hop launches, for ncu
@@ -32,9 +34,13 @@ METRIC = "force evals/s + Dslash HBM GB/s at 32^3×64, mixed vs FP64; p99 solve 
 UNIT = "force evals/s"
 DIMS = (32, 32, 32, 64)
 # DELTA: reliable-update threshold of the mixed CG (|r| < DELTA max|r| triggers an FP64
-# residual replacement); on this workload the iteration count is the same from 0.1 to
-# 1e-4 while the FP64 updates drop from 10 to 3 per solve
-BETA, KAPPA, ALPHA, TOL, DELTA = 5.8, 0.156, 0.5, 1e-10, 1e-4
+# residual replacement).  Measured on this workload (force from a zero guess at the
+# seeded start): 146 inner iterations for every DELTA from 1e-3 to 3e-5 with 4 -> 3 FP64
+# updates; 3e-6 needs 147 iterations and 2 updates (the fastest); 1e-6 needs 158
+BETA, KAPPA, ALPHA, TOL, DELTA = 5.8, 0.156, 0.5, 1e-10, 3e-6
+# force arithmetic of the mixed path: double-float (FP32 pairs, ~48 bits) accumulated
+# in FP64; FP64 and FP32 force arithmetic are timed beside it
+FORCE_ARITH = "df64"
 EPS = 1.0 / 20
 SEED = 4
 # FP64 CG iterations of this workload (Dhat^+Dhat, tol 1e-10, zero guess): used only to
@@ -77,8 +83,8 @@ def measured_peaks():
 
 def config_block(args):
     return {"workload": "32^3x64 Nf=2 Wilson even-odd MD step: mixed CG (FP32 inner, FP64 reliable "
-                        "updates) tol 1e-10 from zero guess + fermion/gauge force fused into the momentum "
-                        "kick + link update",
+                        "updates) tol 1e-10 from zero guess + fermion/gauge force (double-float arithmetic, "
+                        "FP64 accumulation) into the momentum kick + FP64 link update",
             "lattice": list(DIMS), "beta": BETA, "kappa": KAPPA, "alpha": ALPHA, "tol": TOL,
             "delta": DELTA, "seed": SEED, "eps": EPS,
             "l2": "inputs larger than L2 (FP64 links 1.21 GB + FP32 links 0.40 GB per replica)",
@@ -190,7 +196,9 @@ def run_ours(args):
     def restore():
         lat.set_links(U_start)
         mom.copy_(mom_start)
-    ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True)
+    # headline mixed path: FP32 CG with FP64 reliable updates, forces in double-float
+    # (FP32-pair) arithmetic accumulated in FP64; the FP64 path ignores force_arith
+    ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith=FORCE_ARITH)
     stream = torch.cuda.current_stream()
 
     def step(sp, stats, a=ap):
@@ -243,21 +251,25 @@ def run_ours(args):
     value64 = world * K64 / (ms64 / 1e3)
     iters64 = statistics.mean(s["iters"] for s in st64)
 
-    # the same workload with FP32 force arithmetic (an option: ~1e-7 force error, moves
-    # Delta H by ~1e-4 relative, so the headline keeps FP64 forces)
-    ap32 = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_fp32=True)
-    K32 = K
-    ms32f, _, _, _, _ = timed(sp_mixed, K32, W, a=ap32)
-    value32f = world * K32 / (max_over_ranks(ms32f) / 1e3)
-    restore()
-    Ff, _ = lat.force(ap32, phi, sp_mixed)
+    # the same workload with the other force arithmetics of the mixed path: FP64, and
+    # FP32 (~1e-7 force error, moves Delta H by ~1e-4 relative)
+    variants = {}
+    fd = None
+    for arith in ("fp64", "fp32"):
+        apv = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith=arith)
+        msv, _, _, _, _ = timed(sp_mixed, K, W, a=apv)
+        restore()
+        Fv, _ = lat.force(apv, phi, sp_mixed)
+        if fd is None:
+            fd, _ = lat.force(ap, phi, lgt.solver("fp64", tol=TOL))
+        variants[arith] = {"value": world * K / (max_over_ranks(msv) / 1e3), "ms_per_step": msv / K, "steps": K,
+                           "force_rel_err_vs_fp64_path": (torch.linalg.norm(Fv - fd) / torch.linalg.norm(fd)).item()}
+        del Fv
 
-    # error of the mixed force against the FP64 path on the same field
+    # error of the headline mixed force against the FP64 path on the same field
     Fm, _ = lat.force(ap, phi, sp_mixed)
-    Fd, _ = lat.force(ap, phi, lgt.solver("fp64", tol=TOL))
-    force_err = (torch.linalg.norm(Fm - Fd) / torch.linalg.norm(Fd)).item()
-    force_err32 = (torch.linalg.norm(Ff - Fd) / torch.linalg.norm(Fd)).item()
-    del Fm, Fd, Ff
+    force_err = (torch.linalg.norm(Fm - fd) / torch.linalg.norm(fd)).item()
+    del Fm, fd
 
     # dominant kernel: the FP32 hop, timed with CUDA events on its stream inside the
     # timed region; each epilogue variant counts its own algorithmic bytes
@@ -311,6 +323,8 @@ def run_ours(args):
                "steps": Ke, "step": "upload canonical links + phi (pinned host), force (mixed CG), "
                                    "download canonical force"}
 
+    multi = run_multi_rhs(lat, stream) if not args.no_multi else None
+
     serving = None
     if args.serve_requests > 0:
         free, total = torch.cuda.mem_get_info()
@@ -325,14 +339,13 @@ def run_ours(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64 (mixed)", "data": "synthetic: seeded links exp(i 0.5 H), Gaussian pseudofermion",
+           "dtype": "f32 CG + f64 reliable updates + df64 forces (mixed)", "data": "synthetic: seeded links exp(i 0.5 H), Gaussian pseudofermion",
            "config": config_block(args),
            "cg_iters_per_step": iters, "reliable_updates_per_step": rel,
            "fp64": {"value": value64, "ms_per_step": ms64 / K64, "steps": K64, "cg_iters_per_step": iters64,
                     "mixed_speedup": value / value64,
                     "mixed_force_rel_err_vs_fp64_path": force_err},
-           "fp32_force_arithmetic": {"value": value32f, "ms_per_step": ms32f / K32, "steps": K32,
-                                     "force_rel_err_vs_fp64_path": force_err32},
+           "force_arith": FORCE_ARITH, "force_arith_variants": variants,
            "dslash": {"fp32_hop_avg_us": hop32_ms * 1e3, "fp32_hop_GBs_algorithmic": achieved,
                       "fp32_variants": per_variant,
                       "fp32_hop_launches": n32, "skipped_hop_launches": n32_short,
@@ -346,12 +359,58 @@ def run_ours(args):
                         "traffic": traffic, "traffic_kernel": "plain FP32 hop (ncu capture)",
                         "algorithmic_bytes_per_launch": bytes32 / max(n32, 1),
                         "algorithmic_bytes_plain_hop": HOP_BYTES["fp32"] * lat.Vh},
+           "multi_rhs": multi,
            "serving": serving,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- several right-hand sides
+def run_multi_rhs(lat, stream, reps=50):
+    """FP32 hop on K = 1..4 sources with one load of each link (lgt_hop_multi), and
+    four mixed-precision solves at once (lgt_cg_solve_multi) against one at a time;
+    algorithmic bytes per site of a K-source hop: 8 x 48 + K x (96 + 96)."""
+    import torch
+    from paper_2602_20516_b300 import lgt
+    ins = [lat.pack_spinor(lat.unpack_spinor(lat.gaussian_spinor(SEED + 100 + k, 0, lgt.FIELD_SOURCE, lgt.ODD),
+                                             lgt.ODD, lgt.FP64), lgt.ODD, lgt.FP32) for k in range(4)]
+    hop = {}
+    for K in (1, 2, 3, 4):
+        outs = [lat.spinor_field(lgt.EVEN, lgt.FP32) for _ in range(K)]
+        for _ in range(3):
+            lat.hop_multi(ins[:K], lgt.EVEN, False, outs)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            lat.hop_multi(ins[:K], lgt.EVEN, False, outs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = 1e3 * e0.elapsed_time(e1) / reps
+        hop[K] = {"us": us, "us_per_source": us / K,
+                  "GBs_algorithmic": (8 * 48 + K * 192) * lat.Vh / (us * 1e-6) / 1e9}
+    del ins, outs
+    phis = [lat.gaussian_spinor(SEED + 200 + k, 0, lgt.FIELD_SOURCE, lgt.EVEN) for k in range(4)]
+    kap = [0.150, 0.152, 0.154, 0.156]
+    sp = lgt.solver("mixed", tol=TOL, delta=DELTA)
+    lat.cg_solve_multi(phis, kap, sp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, sts = lat.cg_solve_multi(phis, kap, sp)
+    torch.cuda.synchronize()
+    t_multi = time.perf_counter() - t0
+    t_single = 0.0
+    for k in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.cg_solve(phis[k], kap[k], True, sp)
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t0
+    return {"hop_fp32": hop, "solve4": {"kappa": kap, "seconds_together": t_multi, "seconds_one_by_one": t_single,
+                                        "iters": [s["iters"] for s in sts], "speedup": t_single / t_multi}}
 
 
 # ---------------------------------------------------------------- serving (p50/p99 latency)
@@ -481,6 +540,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-multi", action="store_true", help="skip the several-sources measurement")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests per arrival rate in the serving measurement (0 skips it)")
     ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")

@@ -74,6 +74,10 @@ enum { LGT_OP_HOP = 0,       /* out_p = H_{p,1-p} in_{1-p}, p = out_parity (EVEN
 enum { LGT_LEAPFROG = 0, LGT_OMELYAN2MN = 1, LGT_SEXTON_WEINGARTEN = 2 };
 enum { LGT_FORCE_LIE = 0, LGT_GRAD_G = 1 };
 enum { LGT_UPDATE_U = 0, LGT_UPDATE_P = 1 };
+/* deepest stout chain in front of the Wilson operator */
+#define LGT_MAX_STOUT 16
+/* force arithmetic of the mixed-precision path (lgt_action_params.force_arith) */
+enum { LGT_ARITH_FP64 = 0, LGT_ARITH_FP32 = 1, LGT_ARITH_DF64 = 2 };
 
 typedef struct lgt_lattice *lgt_lattice_t;
 
@@ -91,13 +95,23 @@ typedef struct {
     double kappa;     /* hopping parameter of D */
     int fermions;     /* 1: include S_f, 0: pure gauge */
     int even_odd;     /* 1: S_f = phi_e^+ (Dhat^+Dhat)^{-1} phi_e; 0: full lattice */
-    int n_stout;      /* stout levels in front of D (0 .. 4); S_G sees thin links */
+    int n_stout;      /* stout levels in front of D (0 .. LGT_MAX_STOUT); S_G sees thin links */
     double rho;       /* stout parameter */
-    int stout_recompute; /* 0: keep every smeared level for the adjoint;
-                            1: keep only the top level and recompute the others */
-    int force_fp32;      /* 0: FP64 force arithmetic (default); 1: with the mixed solver,
-                            Lie-form forces use FP32 arithmetic accumulated in FP64 (about
-                            1e-7 relative; moves an MD trajectory's Delta H by ~1e-4) */
+    int stout_recompute; /* storage of the smeared levels for the adjoint (every choice
+                            gives the same gradient, bit for bit):
+                            0: keep every level (n fields);
+                            1: keep only the top level, recompute each level's input from
+                               the thin links (2 fields, n(n-1)/2 extra smearing steps);
+                            c >= 2: keep every c-th level as a checkpoint and recompute
+                               each segment once from it (about n/c + c fields, fewer
+                               than n extra smearing steps) */
+    int force_arith;     /* arithmetic of Lie-form forces when the solver is LGT_MIXED
+                            (with LGT_FP64 solves every force kernel is FP64):
+                            LGT_ARITH_FP64 (0, default) FP64;
+                            LGT_ARITH_FP32 FP32 accumulated in FP64 (about 1e-7 relative;
+                              moves an MD trajectory's Delta H by ~1e-4);
+                            LGT_ARITH_DF64 double-float: products carried as pairs of FP32
+                              numbers (about 48 bits, ~1e-13 relative), accumulated in FP64 */
 } lgt_action_params;
 
 typedef struct {
@@ -106,6 +120,13 @@ typedef struct {
     int max_iter;     /* iteration cap -> LGT_ENOCONV */
     double delta;     /* mixed: reliable update when |r| < delta * max|r| since the last one */
     int check_every;  /* iterations enqueued between host checks (0 -> default 16) */
+    int chrono;       /* even-odd solves: 0 starts from x = 0; N = 1..LGT_MAX_RHS starts
+                         from the combination of the handle's last N solutions of the same
+                         operator (same kappa) that minimises the A-norm of the error
+                         (chronological inverter, Brower et al., Nucl. Phys. B484 (1997)
+                         353), each converged solve being recorded; the FP64 residual of
+                         the guess is the first reliable update.  The history is cleared
+                         by lgt_chrono_reset and at the start of lgt_hmc_trajectory. */
 } lgt_solver_params;
 
 typedef struct {
@@ -211,6 +232,31 @@ int lgt_dslash(lgt_lattice_t lat, const void *in, void *out, int op, int out_par
 int lgt_cg_solve(lgt_lattice_t lat, const double *b, double *x, double kappa, int even_odd,
                  const lgt_solver_params *sp, lgt_solve_stats *stats);
 
+/* Forget the solutions kept for chronological initial guesses (lgt_solver_params.chrono),
+ * e.g. when the pseudofermion source changes.  Not in the paper. */
+int lgt_chrono_reset(lgt_lattice_t lat);
+
+/* Several right-hand sides on the handle's links (not in the paper: the solve of
+ * Eq. S3.4 repeated for nrhs sources, as a serving or multi-source workload needs).
+ * Solves A_k x_k = b_k, A_k = Dhat_k^+ Dhat_k on even sites with kappa[k], for
+ * k < nrhs <= LGT_MAX_RHS; b[k], x[k] are host arrays of device pointers to FP64
+ * even half fields (distinct; x[k] aliases nothing), stats (NULL or nrhs entries).
+ * LGT_MIXED: every FP32 operator application covers all running systems with one
+ * load of each link (the hop moves 8 links + nrhs spinor pairs per site instead of
+ * nrhs times 8 links + 1 pair); each system keeps its own scalars, stop test and
+ * FP64 reliable updates, so its solution and counts equal those of lgt_cg_solve
+ * alone.  LGT_FP64: the systems are solved one after another (the FP64 hop is
+ * bound by FP64 arithmetic, which sharing link loads does not reduce).  The first
+ * failing system's status is returned after all systems finished.  Synchronous. */
+#define LGT_MAX_RHS 4
+int lgt_cg_solve_multi(lgt_lattice_t lat, int nrhs, const double *const *b, double *const *x,
+                       const double *kappa, const lgt_solver_params *sp, lgt_solve_stats *stats);
+/* out_k = H_{p,1-p} in_k (dagger: H^+) for k < nrhs FP32 half fields (host arrays of
+ * device pointers), with one load of each FP32 link for all of them; the result of
+ * each equals lgt_dslash(LGT_OP_HOP, LGT_FP32) on that field.  Asynchronous. */
+int lgt_hop_multi(lgt_lattice_t lat, int nrhs, const void *const *in, void *const *out, int out_parity,
+                  int dagger);
+
 /* ------------------------------------------------------------------ actions */
 /* S_G (beta from ap) and S_f = phi^+ A^{-1} phi evaluated as 2 Re(phi^+ chi) - |M chi|^2
  * (A chi = phi), phi an FP64 device field (even half for even_odd, else full).
@@ -238,12 +284,14 @@ int lgt_grad_to_lie(lgt_lattice_t lat, const double *G_field, double *F_mom);
 /* ------------------------------------------------------------------ stout smearing */
 /* n_levels of stout smearing (Morningstar-Peardon, the "smear" steps of Fig. 1)
  * of the handle's gauge field, written in canonical layout to out_canonical
- * (device, complex128 [V][4][3][3]).  Synchronous. */
+ * (device, complex128 [V][4][3][3]); recompute selects the storage of the levels
+ * as lgt_action_params.stout_recompute.  Synchronous. */
 int lgt_stout_smear(lgt_lattice_t lat, double rho, int n_levels, int recompute, double *out_canonical);
 /* Adjoint of that smearing (the reverse recursion of Eq. 3 through each level):
  * given the real-component gradient (Eq. S2.11) w.r.t. the top level, write the
- * gradient w.r.t. the handle's thin links (both canonical, device).  recompute = 1
- * keeps only the top level and recomputes intermediate levels.  Synchronous. */
+ * gradient w.r.t. the handle's thin links (both canonical, device).  recompute as
+ * lgt_action_params.stout_recompute (0 stored, 1 recomputed from the thin links,
+ * c >= 2 checkpoints every c levels); the result does not depend on it.  Synchronous. */
 int lgt_stout_backward(lgt_lattice_t lat, double rho, int n_levels, int recompute,
                        const double *G_top_canonical, double *G_thin_canonical);
 

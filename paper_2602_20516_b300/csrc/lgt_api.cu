@@ -91,6 +91,8 @@ static void philox_host(const uint32_t ctr[4], uint64_t seed, uint32_t out[4]) {
 }
 
 // ---------------------------------------------------------------- handle
+constexpr int MAX_STOUT = LGT_MAX_STOUT;   // stout levels in front of D
+
 struct Links {
     double2* U;
     float4* U12;
@@ -108,18 +110,47 @@ struct lgt_lattice {
     Links thin;
     // solver workspace (full fields; even-odd solves use the even half)
     double2 *r, *p, *u, *t, *X, *Y, *b;
+    // force vectors taken from the solver's final true residual: when cap_X / cap_Y
+    // are set, the FP64 residual of a converged solve leaves X = (x_e, kappa H_oe x_e)
+    // and Y = (Dhat x_e, kappa (H^+)_oe Dhat x_e) (full lattice: Y = D x) in them, and
+    // cap_valid says so
+    double2 *cap_X, *cap_Y;
+    bool cap_valid;
     float4 *r32, *p32, *x32, *u32, *t32, *X32, *Y32;
     bool have_solver;
+    // double-float copies for LGT_ARITH_DF64 forces: links, X, Y
+    float4 *Udf, *Xdf, *Ydf;
+    // several right-hand sides (lgt_cg_solve_multi): per system FP32 even/odd half
+    // fields, an FP64 residual, scalars, reduction partials and counter
+    struct {
+        float4 *x32[KMAX_RHS], *r32[KMAX_RHS], *p32[KMAX_RHS], *u32[KMAX_RHS], *t32[KMAX_RHS];
+        double2* r64[KMAX_RHS];
+        double* partials[KMAX_RHS];
+        unsigned* counter;   // KMAX_RHS counters, 64 B apart
+        Scalars* s;          // device [KMAX_RHS]
+        Scalars* hs;         // pinned mirror
+        bool ready;
+    } mw;
+    // chronological initial guesses: the last solutions (FP64 even halves) of the
+    // operator with kappa ch.kappa, newest at hist[(head - 1) mod CHRONO_MAX]
+    struct {
+        double2* hist[CHRONO_MAX];
+        int n, head;
+        double kappa;
+        double2 *G, *g, *c;   // device: Gram matrix, projections, coefficients
+        int* used;
+        double2* partials;
+        unsigned* counter;
+        long cap;
+    } ch;
     // HMC / force workspace
     double2 *mom, *Ubak, *phi, *xi, *F, *G;
     bool have_md;
-    // stout stack: stored levels 1..n (FP64), or top + one scratch field when the
-    // intermediate levels are recomputed; FP32 copy of the top level only;
-    // gradient ping-pong and the per-link G_C scratch of the adjoint
-    double2* smeared[5];
-    int n_smeared_alloc;
-    double2* stout_top;
-    double2* stout_tmp;
+    // stout stack: a pool of FP64 link fields holding the smeared levels the adjoint
+    // needs (placement by StoutPlan), the FP32 copy of the top level, gradient
+    // ping-pong and the per-link G_C scratch of the adjoint
+    double2* sbuf[MAX_STOUT];
+    int n_sbuf;
     float4* stout_top12;
     double2* sgrad[3];
     // reductions
@@ -170,6 +201,47 @@ static int ensure_solver(lgt_lattice* L) {
     return LGT_OK;
 }
 
+static int ensure_df(lgt_lattice* L) {
+    if (L->Udf) return LGT_OK;
+    TRY(A(L, links64(L), &L->Udf));
+    TRY(A(L, spinor64_full(L), &L->Xdf));
+    TRY(A(L, spinor64_full(L), &L->Ydf));
+    return LGT_OK;
+}
+
+static int ensure_multi(lgt_lattice* L) {
+    if (L->mw.ready) return LGT_OK;
+    const size_t h32 = (size_t)6 * L->g.Vh * sizeof(float4), h64 = (size_t)12 * L->g.Vh * sizeof(double2);
+    for (int k = 0; k < KMAX_RHS; ++k) {
+        TRY(A(L, h32, &L->mw.x32[k])); TRY(A(L, h32, &L->mw.r32[k])); TRY(A(L, h32, &L->mw.p32[k]));
+        TRY(A(L, h32, &L->mw.u32[k])); TRY(A(L, h32, &L->mw.t32[k])); TRY(A(L, h64, &L->mw.r64[k]));
+        TRY(A(L, sizeof(double) * (size_t)L->n_partials, &L->mw.partials[k]));
+    }
+    TRY(A(L, 64 * KMAX_RHS, &L->mw.counter));
+    TRY(A(L, sizeof(Scalars) * KMAX_RHS, &L->mw.s));
+    if (!L->mw.hs && cudaMallocHost((void**)&L->mw.hs, sizeof(Scalars) * KMAX_RHS) != cudaSuccess)
+        return fail(LGT_ENOMEM, "cudaMallocHost failed");
+    CK(cudaMemsetAsync(L->mw.counter, 0, 64 * KMAX_RHS, L->st));
+    L->mw.ready = true;
+    return LGT_OK;
+}
+
+static int ensure_chrono(lgt_lattice* L) {
+    if (L->ch.G) return LGT_OK;
+    const size_t h64 = (size_t)12 * L->g.Vh * sizeof(double2);
+    for (int k = 0; k < CHRONO_MAX; ++k) TRY(A(L, h64, &L->ch.hist[k]));
+    TRY(A(L, sizeof(double2) * CDOT_MAX, &L->ch.G));
+    TRY(A(L, sizeof(double2) * CHRONO_MAX, &L->ch.g));
+    TRY(A(L, sizeof(double2) * CHRONO_MAX, &L->ch.c));
+    TRY(A(L, 64, &L->ch.used));
+    L->ch.cap = (long)CDOT_MAX * ((L->g.Vh + NT - 1) / NT);
+    TRY(A(L, sizeof(double2) * (size_t)L->ch.cap, &L->ch.partials));
+    TRY(A(L, sizeof(unsigned) * CDOT_MAX, &L->ch.counter));
+    CK(cudaMemsetAsync(L->ch.counter, 0, sizeof(unsigned) * CDOT_MAX, L->st));
+    L->ch.n = L->ch.head = 0;
+    return LGT_OK;
+}
+
 static int ensure_md(lgt_lattice* L) {
     if (L->have_md) return LGT_OK;
     TRY(A(L, mom_bytes(L), &L->mom));
@@ -182,21 +254,48 @@ static int ensure_md(lgt_lattice* L) {
     return LGT_OK;
 }
 
-static int ensure_stout(lgt_lattice* L, int n, bool recompute) {
-    if (n > 4) return fail(LGT_EINVAL, "n_stout = %d > 4", n);
+// Where the smeared levels live for n levels and mode m = stout_recompute:
+//   m = 0  every level k in sbuf[k-1];
+//   m = 1  only the top level (sbuf[0]) and one scratch field (sbuf[1]); the input
+//          of each level is recomputed from the thin links in the adjoint (work
+//          O(n^2) smearing steps, memory O(1));
+//   m = c >= 2  checkpoints: levels c, 2c, ... below n in sbuf[0 .. nck), the top in
+//          sbuf[nck], and c - 1 segment fields after it; the adjoint recomputes
+//          each segment once from its checkpoint (about n extra smearing steps,
+//          memory n/c + c levels).
+// Every mode runs the same forward kernels on the same inputs, so the levels, and
+// with them the gradients, are identical bit for bit.
+struct StoutPlan {
+    int n, m, c, nck;
+    int buffers() const {
+        if (m == 0) return n;
+        if (m == 1) return n > 1 ? 2 : 1;
+        return nck + 1 + std::min(c - 1, n - 1);
+    }
+    // field of level k (1..n) as written by the forward pass
+    int slot(int k) const {
+        if (m == 0) return k - 1;
+        if (m == 1) return ((n - k) % 2 == 0) ? 0 : 1;
+        if (k == n) return nck;
+        if (k % c == 0) return k / c - 1;
+        return nck + (k % c);
+    }
+};
+static StoutPlan stout_plan(int n, int m) {
+    StoutPlan P{n, m, m >= 2 ? m : 0, 0};
+    if (m >= 2) P.nck = (n - 1) / m;
+    return P;
+}
+
+static int ensure_stout(lgt_lattice* L, int n, int m) {
+    if (n < 0 || n > MAX_STOUT) return fail(LGT_EINVAL, "n_stout = %d outside 0..%d", n, MAX_STOUT);
+    if (m < 0) return fail(LGT_EINVAL, "stout_recompute = %d", m);
     if (n == 0) return LGT_OK;
     if (!L->stout_top12) TRY(A(L, links12(L), &L->stout_top12));
     if (!L->sgrad[0])
         for (int k = 0; k < 3; ++k) TRY(A(L, links64(L), &L->sgrad[k]));
-    if (recompute) {
-        if (!L->stout_top) TRY(A(L, links64(L), &L->stout_top));
-        if (!L->stout_tmp) TRY(A(L, links64(L), &L->stout_tmp));
-    } else {
-        while (L->n_smeared_alloc < n) {
-            int k = ++L->n_smeared_alloc;
-            TRY(A(L, links64(L), &L->smeared[k]));
-        }
-    }
+    const int need = stout_plan(n, m).buffers();
+    while (L->n_sbuf < need) TRY(A(L, links64(L), &L->sbuf[L->n_sbuf++]));
     return LGT_OK;
 }
 
@@ -264,7 +363,6 @@ extern "C" int lgt_create_lattice(const int dims[4], const lgt_allocator* alloc,
         lgt_destroy_lattice(L);
         return fail(LGT_ECUDA, "lattice initialisation: %s", cudaGetErrorString(e));
     }
-    L->smeared[0] = L->thin.U;
     *out = L;
     return LGT_OK;
 }
@@ -277,6 +375,7 @@ extern "C" int lgt_destroy_lattice(lgt_lattice_t L) {
         else cudaFree(p);
     }
     if (L->hs) cudaFreeHost(L->hs);
+    if (L->mw.hs) cudaFreeHost(L->mw.hs);
     delete L;
     return LGT_OK;
 }
@@ -512,28 +611,102 @@ static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, dou
     return LGT_OK;
 }
 
-// FP64 true residual res = b - A x, |res|^2 -> slot 0
+// FP64 true residual res = b - A x, |res|^2 -> slot 0.  With L->cap_X / cap_Y set
+// (x is then the even half of cap_X), the intermediate vectors of A x are written
+// where the fermion force reads them:
+//   even-odd: X_o = kappa H_oe x, eta = x - kappa H_eo X_o (= Dhat x), Y_o = kappa (H^+)_oe eta,
+//             A x = eta - kappa (H^+)_eo Y_o;
+//   full:     Y = D x, A x = D^+ Y.
 static int true_residual(lgt_lattice* L, const Links& lk, bool eo, double kappa, const double2* b, const double2* x,
                          double2* res) {
+    const bool cap = L->cap_X && L->cap_Y;
     if (eo) {
-        TRY(hop1(L, lk, true, false, 1, x, L->t, 1.0));
-        TRY(hop1(L, lk, true, false, 0, L->t, L->u, -kappa * kappa, EPI_XPAY, x));
-        TRY(hop1(L, lk, true, true, 1, L->u, L->t, 1.0));
+        double2* Xo = cap ? (double2*)half(L->cap_X, L, true, 1) : L->t;
+        double2* Ye = cap ? L->cap_Y : L->u;
+        double2* Yo = cap ? (double2*)half(L->cap_Y, L, true, 1) : L->t;
+        TRY(hop1(L, lk, true, false, 1, x, Xo, kappa));
+        TRY(hop1(L, lk, true, false, 0, Xo, Ye, -kappa, EPI_XPAY, x));
+        TRY(hop1(L, lk, true, true, 1, Ye, Yo, kappa));
         HopArgs A = hop_base(L, lk, true);
-        A.parity = 0; A.in[1] = L->t; A.y[0] = L->u; A.a = -kappa * kappa; A.out[0] = res; A.pv[0] = b;
+        A.parity = 0; A.in[1] = Yo; A.y[0] = Ye; A.a = -kappa; A.out[0] = res; A.pv[0] = b;
         A.red_op = RED_STORE; A.red_slot = 0;
         CK(timed_hop(A, true, true, EPI_RESID, L->st));
     } else {
-        TRY(dfull(L, lk, true, false, x, L->u, kappa));
+        double2* Yf = cap ? L->cap_Y : L->u;
+        TRY(dfull(L, lk, true, false, x, Yf, kappa));
         HopArgs A = hop_base(L, lk, true);
         A.parity = 2;
         for (int q = 0; q < 2; ++q) {
-            A.in[q] = half(L->u, L, true, q); A.y[q] = half(L->u, L, true, q);
+            A.in[q] = half(Yf, L, true, q); A.y[q] = half(Yf, L, true, q);
             A.out[q] = half(res, L, true, q); A.pv[q] = half(b, L, true, q);
         }
         A.a = -kappa; A.red_op = RED_STORE; A.red_slot = 0;
         CK(timed_hop(A, true, true, EPI_RESID, L->st));
     }
+    return LGT_OK;
+}
+
+// Chronological initial guess for Dhat^+Dhat x = b on even sites (kappa): with the
+// last N kept solutions v_i, x = sum c_i v_i with (V^+ A V) c = V^+ b.  The products
+// A v_i use the FP32 operator on all of them at once (a guess needs no more); the
+// solve that follows starts from the FP64 residual of x.  *used = false (x untouched)
+// when nothing of this operator is kept.
+static int chrono_guess(lgt_lattice* L, const Links& lk, const double2* b, double2* x, double kappa, int want,
+                        bool* used) {
+    *used = false;
+    auto& C = L->ch;
+    if (C.n == 0 || C.kappa != kappa) return LGT_OK;
+    TRY(ensure_multi(L));
+    auto& W = L->mw;
+    const int N = std::min(want, C.n);
+    const double2* v[CHRONO_MAX];
+    for (int i = 0; i < N; ++i) v[i] = C.hist[(C.head - 1 - i + 2 * CHRONO_MAX) % CHRONO_MAX];   // newest first
+    // w_i = A v_i in FP32: t = H_oe v, u = v - kappa^2 H_eo t, t = H^+_oe u, w = u - kappa^2 H^+_eo t
+    for (int i = 0; i < N; ++i) CK(blas_d2f(W.p32[i], v[i], L->g.Vh, L->g.Vh, L->st));
+    HopArgsM H;
+    memset(&H, 0, sizeof H);
+    H.U = lk.U12;
+    H.g = L->g;
+    H.nrhs = N;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool dag = pass == 1;
+        H.parity = 1;
+        for (int i = 0; i < N; ++i) { H.in[i] = dag ? W.u32[i] : W.p32[i]; H.out[i] = W.t32[i]; H.a[i] = 1.0; }
+        CK(launch_hop_multi(H, false, dag, EPI_HOP, L->st));
+        H.parity = 0;
+        for (int i = 0; i < N; ++i) {
+            H.in[i] = W.t32[i];
+            H.y[i] = dag ? W.u32[i] : W.p32[i];
+            H.out[i] = dag ? W.r32[i] : W.u32[i];
+            H.a[i] = -kappa * kappa;
+        }
+        CK(launch_hop_multi(H, false, dag, EPI_XPAY, L->st));
+    }
+    CdotArgs D;
+    memset(&D, 0, sizeof D);
+    D.Vh = L->g.Vh;
+    D.partials = C.partials;
+    D.counter = C.counter;
+    D.capacity = C.cap;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) { D.a[i * N + j] = v[i]; D.b[i * N + j] = W.r32[j]; }
+    D.out = C.G;
+    CK(cdot_many(D, N * N, true, L->st));
+    for (int i = 0; i < N; ++i) { D.a[i] = v[i]; D.b[i] = b; }
+    D.out = C.g;
+    CK(cdot_many(D, N, false, L->st));
+    CK(chrono_solve(C.G, C.g, C.c, N, C.used, L->st));
+    CK(chrono_combine(x, v, C.c, N, L->g.Vh, L->st));
+    *used = true;
+    return LGT_OK;
+}
+static int chrono_record(lgt_lattice* L, const double2* x, double kappa) {
+    auto& C = L->ch;
+    if (C.n > 0 && C.kappa != kappa) C.n = C.head = 0;
+    C.kappa = kappa;
+    CK(cudaMemcpyAsync(C.hist[C.head], x, (size_t)12 * L->g.Vh * sizeof(double2), cudaMemcpyDeviceToDevice, L->st));
+    C.head = (C.head + 1) % CHRONO_MAX;
+    C.n = std::min(C.n + 1, CHRONO_MAX);
     return LGT_OK;
 }
 
@@ -544,6 +717,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     if (sp->precision != LGT_FP64 && sp->precision != LGT_MIXED) return fail(LGT_EINVAL, "solver precision %d", sp->precision);
     if (!(sp->tol > 0) || sp->max_iter <= 0) return fail(LGT_EINVAL, "tol and max_iter must be positive");
     TRY(ensure_solver(L));
+    L->cap_valid = false;
     const int n = eo ? L->g.Vh : 2 * L->g.Vh;
     const int K = sp->check_every > 0 ? sp->check_every : 16;
     const bool mixed = sp->precision == LGT_MIXED;
@@ -562,23 +736,43 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     }
     const double target = sp->tol * sp->tol * bb;
     Scalars* hs = L->hs;
+    // start: x = 0, r = b; or the chronological guess x0 with its FP64 residual
+    bool guess = false;
+    if (eo && sp->chrono > 0) {
+        TRY(ensure_chrono(L));
+        TRY(chrono_guess(L, lk, b, x, kappa, std::min(sp->chrono, CHRONO_MAX), &guess));
+    }
+    double rr0 = bb;
+    if (guess) {
+        TRY(true_residual(L, lk, eo, kappa, b, x, L->r));
+        TRY(sync_scalars(L));
+        rr0 = hs->slot[0];
+        st.reliable_updates += 1;
+        if (!std::isfinite(rr0)) return fail(LGT_ENAN, "non-finite residual of the initial guess");
+    } else {
+        CK(cudaMemcpyAsync(L->r, b, b64, cudaMemcpyDeviceToDevice, L->st));
+    }
     memset(hs, 0, sizeof(Scalars));
-    hs->rr = bb;
-    hs->rr_max = bb;
+    hs->rr = rr0;
+    hs->rr_max = rr0;
     hs->target = target;
     hs->delta2 = mixed ? sp->delta * sp->delta : 0.0;
-    CK(cudaMemcpyAsync(L->r, b, b64, cudaMemcpyDeviceToDevice, L->st));
     if (mixed) {
-        CK(blas_d2f(L->r32, b, n, L->g.Vh, L->st));
+        CK(blas_d2f(L->r32, L->r, n, L->g.Vh, L->st));
         CK(cudaMemcpyAsync(L->p32, L->r32, b32, cudaMemcpyDeviceToDevice, L->st));
         CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
     } else {
-        CK(cudaMemcpyAsync(L->p, b, b64, cudaMemcpyDeviceToDevice, L->st));
+        CK(cudaMemcpyAsync(L->p, L->r, b64, cudaMemcpyDeviceToDevice, L->st));
     }
     TRY(push_scalars(L));
-    double rr_true = bb;
+    double rr_true = rr0;
     int rc = LGT_OK;
-    for (;;) {
+    const bool record = eo && sp->chrono > 0;
+    if (guess && rr0 <= target) {   // the guess already solves the system
+        L->cap_valid = L->cap_X && L->cap_Y && (const double2*)x == L->cap_X;
+        if (record) TRY(chrono_record(L, x, kappa));
+    }
+    for (; !(guess && rr0 <= target);) {
         for (int k = 0; k < K; ++k) {
             if (mixed) TRY(cg_iteration(L, lk, false, eo, kappa, L->x32, L->r32, L->p32, L->u32, L->t32));
             else TRY(cg_iteration(L, lk, true, eo, kappa, x, L->r, L->p, L->u, L->t));
@@ -596,7 +790,11 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
             rr_true = hs->slot[0];
             st.reliable_updates += 1;
             if (!std::isfinite(rr_true)) { rc = fail(LGT_ENAN, "non-finite true residual"); break; }
-            if (rr_true <= target) break;
+            if (rr_true <= target) {
+                L->cap_valid = L->cap_X && L->cap_Y && (const double2*)x == L->cap_X;
+                if (record) TRY(chrono_record(L, x, kappa));
+                break;
+            }
             if (hit_cap) {
                 rc = fail(LGT_ENOCONV, "CG reached max_iter=%d, true relative residual %.3e", sp->max_iter,
                           std::sqrt(rr_true / bb));
@@ -631,45 +829,227 @@ extern "C" int lgt_cg_solve(lgt_lattice_t L, const double* b, double* x, double 
     return cg_core(L, L->thin, (const double2*)b, (double2*)x, kappa, even_odd != 0, sp, stats);
 }
 
+extern "C" int lgt_chrono_reset(lgt_lattice_t L) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    L->ch.n = L->ch.head = 0;
+    return LGT_OK;
+}
+
+// ---------------------------------------------------------------- several right-hand sides
+// launch arguments for the running systems sys[0..n): slot j holds system sys[j]
+static HopArgsM hop_multi_base(lgt_lattice* L, int n, const int* sys) {
+    HopArgsM a;
+    memset(&a, 0, sizeof a);
+    a.U = L->thin.U12;
+    a.g = L->g;
+    a.nrhs = n;
+    a.skip = 1;
+    a.red_capacity = L->n_partials;
+    for (int j = 0; j < n; ++j) {
+        const int k = sys[j];
+        a.s[j] = L->mw.s + k;
+        a.partials[j] = L->mw.partials[k];
+        a.counter[j] = (unsigned*)((char*)L->mw.counter + 64 * k);
+        a.a[j] = 1.0;
+    }
+    return a;
+}
+
+// One FP32 CG iteration of the running systems sys[0..n) (A_k = Dhat_k^+ Dhat_k, even
+// sites): the kernel sequence of cg_iteration, each launch covering all of them.
+static int cg_iteration_multi(lgt_lattice* L, int n, const int* sys, const double* kappa) {
+    auto& W = L->mw;
+    HopArgsM A = hop_multi_base(L, n, sys);
+    A.parity = 1;
+    for (int j = 0; j < n; ++j) { A.in[j] = W.p32[sys[j]]; A.out[j] = W.t32[sys[j]]; }
+    CK(launch_hop_multi(A, false, false, EPI_HOP, L->st));
+    A = hop_multi_base(L, n, sys);
+    A.parity = 0; A.red_op = RED_PAP;
+    for (int j = 0; j < n; ++j) {
+        const int k = sys[j];
+        A.in[j] = W.t32[k]; A.out[j] = W.u32[k]; A.y[j] = W.p32[k]; A.a[j] = -kappa[k] * kappa[k];
+    }
+    CK(launch_hop_multi(A, false, false, EPI_XPAY_NORM, L->st));
+    A = hop_multi_base(L, n, sys);
+    A.parity = 1;
+    for (int j = 0; j < n; ++j) { A.in[j] = W.u32[sys[j]]; A.out[j] = W.t32[sys[j]]; }
+    CK(launch_hop_multi(A, false, true, EPI_HOP, L->st));
+    A = hop_multi_base(L, n, sys);
+    A.parity = 0; A.red_op = RED_RR;
+    for (int j = 0; j < n; ++j) {
+        const int k = sys[j];
+        A.in[j] = W.t32[k]; A.y[j] = W.u32[k]; A.a[j] = -kappa[k] * kappa[k];
+        A.x[j] = W.x32[k]; A.r[j] = W.r32[k]; A.pv[j] = W.p32[k];
+    }
+    CK(launch_hop_multi(A, false, true, EPI_CG, L->st));
+    PUpdateM P;
+    memset(&P, 0, sizeof P);
+    P.nrhs = n;
+    for (int j = 0; j < n; ++j) {
+        const int k = sys[j];
+        P.p[j] = W.p32[k]; P.r[j] = W.r32[k];
+        P.red[j] = RedArgs{W.s + k, W.partials[k], (unsigned*)((char*)W.counter + 64 * k), L->n_partials};
+    }
+    CK(blas_cg_p_update_multi(P, L->g.Vh, false, L->st));
+    return LGT_OK;
+}
+
+// Mixed-precision CG on nrhs systems sharing the handle's links: each system has
+// its own kappa, scalars, stop test and FP64 reliable updates (as cg_core), and
+// the FP32 operator applications of all running systems share every link load.
+// A system's iterates are the ones cg_core produces for it alone.
+static int cg_multi(lgt_lattice* L, int nrhs, const double2* const* b, double2* const* x, const double* kappa,
+                    const lgt_solver_params* sp, lgt_solve_stats* stats) {
+    auto t0 = std::chrono::steady_clock::now();
+    TRY(ensure_solver(L));
+    TRY(ensure_multi(L));
+    auto& W = L->mw;
+    const int n = L->g.Vh;
+    const int K = sp->check_every > 0 ? sp->check_every : 16;
+    const size_t b64 = (size_t)n * 12 * sizeof(double2), b32 = (size_t)n * 6 * sizeof(float4);
+    L->cap_valid = false;
+    for (int k = 0; k < nrhs; ++k) CK(blas_norm2(b[k], n, L->g.Vh, true, red(L), k, L->st));
+    TRY(sync_scalars(L));
+    double bb[KMAX_RHS], rr_true[KMAX_RHS];
+    int rel[KMAX_RHS];
+    bool fin[KMAX_RHS];
+    int rc = LGT_OK;
+    memset(W.hs, 0, sizeof(Scalars) * KMAX_RHS);
+    for (int k = 0; k < nrhs; ++k) {
+        bb[k] = L->hs->slot[k];
+        rr_true[k] = bb[k];
+        rel[k] = 0;
+        CK(cudaMemsetAsync(x[k], 0, b64, L->st));
+        if (!std::isfinite(bb[k])) return fail(LGT_ENAN, "right-hand side %d is not finite", k);
+        fin[k] = bb[k] == 0.0;
+        Scalars& h = W.hs[k];
+        h.rr = h.rr_max = bb[k];
+        h.target = sp->tol * sp->tol * bb[k];
+        h.delta2 = sp->delta * sp->delta;
+        h.done = fin[k] ? 2 : 0;
+        CK(cudaMemcpyAsync(W.r64[k], b[k], b64, cudaMemcpyDeviceToDevice, L->st));
+        CK(blas_d2f(W.r32[k], b[k], n, L->g.Vh, L->st));
+        CK(cudaMemcpyAsync(W.p32[k], W.r32[k], b32, cudaMemcpyDeviceToDevice, L->st));
+        CK(cudaMemsetAsync(W.x32[k], 0, b32, L->st));
+    }
+    CK(cudaMemcpyAsync(W.s, W.hs, sizeof(Scalars) * KMAX_RHS, cudaMemcpyHostToDevice, L->st));
+    for (;;) {
+        // the launches of this batch cover the systems still running at its start
+        int sys[KMAX_RHS], nrun = 0;
+        for (int k = 0; k < nrhs; ++k)
+            if (!fin[k]) sys[nrun++] = k;
+        if (nrun == 0) break;
+        for (int it = 0; it < K; ++it) TRY(cg_iteration_multi(L, nrun, sys, kappa));
+        CK(cudaMemcpyAsync(W.hs, W.s, sizeof(Scalars) * KMAX_RHS, cudaMemcpyDeviceToHost, L->st));
+        CK(cudaStreamSynchronize(L->st));
+        for (int k = 0; k < nrhs; ++k) {
+            if (fin[k]) continue;
+            Scalars& h = W.hs[k];
+            if (h.nan) {
+                if (rc == LGT_OK) rc = fail(LGT_ENAN, "non-finite value in CG of system %d", k);
+                fin[k] = true; h.done = 2;
+                continue;
+            }
+            const bool hit_cap = h.iters >= sp->max_iter;
+            if (!(h.done || hit_cap)) continue;
+            CK(blas_add_f2d(x[k], W.x32[k], n, L->g.Vh, L->st));
+            CK(cudaMemsetAsync(W.x32[k], 0, b32, L->st));
+            TRY(true_residual(L, L->thin, true, kappa[k], b[k], x[k], W.r64[k]));
+            TRY(sync_scalars(L));
+            rr_true[k] = L->hs->slot[0];
+            rel[k] += 1;
+            if (!std::isfinite(rr_true[k])) {
+                if (rc == LGT_OK) rc = fail(LGT_ENAN, "non-finite true residual of system %d", k);
+                fin[k] = true; h.done = 2;
+            } else if (rr_true[k] <= h.target) {
+                fin[k] = true; h.done = 2;
+            } else if (hit_cap) {
+                if (rc == LGT_OK)
+                    rc = fail(LGT_ENOCONV, "CG of system %d reached max_iter=%d, true relative residual %.3e", k,
+                              sp->max_iter, std::sqrt(rr_true[k] / bb[k]));
+                fin[k] = true; h.done = 2;
+            } else {
+                CK(blas_d2f(W.r32[k], W.r64[k], n, L->g.Vh, L->st));
+                h.rr = h.rr_max = rr_true[k];
+                h.done = 0;
+            }
+        }
+        CK(cudaMemcpyAsync(W.s, W.hs, sizeof(Scalars) * KMAX_RHS, cudaMemcpyHostToDevice, L->st));
+    }
+    CK(cudaStreamSynchronize(L->st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats)
+        for (int k = 0; k < nrhs; ++k)
+            stats[k] = lgt_solve_stats{W.hs[k].iters, rel[k], bb[k] > 0 ? std::sqrt(rr_true[k] / bb[k]) : 0.0, secs};
+    return rc;
+}
+
+extern "C" int lgt_cg_solve_multi(lgt_lattice_t L, int nrhs, const double* const* b, double* const* x,
+                                  const double* kappa, const lgt_solver_params* sp, lgt_solve_stats* stats) {
+    if (!L || !b || !x || !kappa || !sp) return fail(LGT_EINVAL, "null argument");
+    if (nrhs < 1 || nrhs > KMAX_RHS) return fail(LGT_EINVAL, "nrhs = %d outside 1..%d", nrhs, KMAX_RHS);
+    if (sp->precision != LGT_FP64 && sp->precision != LGT_MIXED) return fail(LGT_EINVAL, "solver precision %d", sp->precision);
+    if (!(sp->tol > 0) || sp->max_iter <= 0) return fail(LGT_EINVAL, "tol and max_iter must be positive");
+    for (int k = 0; k < nrhs; ++k) {
+        if (!b[k] || !x[k]) return fail(LGT_EINVAL, "null field of system %d", k);
+        for (int j = 0; j < nrhs; ++j)
+            if ((const double*)x[k] == b[j] || (j != k && x[k] == x[j]))
+                return fail(LGT_EINVAL, "solution %d aliases another field", k);
+    }
+    if (sp->precision == LGT_FP64) {   // FP64 arithmetic bounds the FP64 hop: solve one after another
+        for (int k = 0; k < nrhs; ++k)
+            TRY(cg_core(L, L->thin, (const double2*)b[k], (double2*)x[k], kappa[k], true, sp, stats ? stats + k : nullptr));
+        return LGT_OK;
+    }
+    return cg_multi(L, nrhs, (const double2* const*)b, (double2* const*)x, kappa, sp, stats);
+}
+
+extern "C" int lgt_hop_multi(lgt_lattice_t L, int nrhs, const void* const* in, void* const* out, int out_parity,
+                             int dagger) {
+    if (!L || !in || !out) return fail(LGT_EINVAL, "null argument");
+    if (nrhs < 1 || nrhs > KMAX_RHS) return fail(LGT_EINVAL, "nrhs = %d outside 1..%d", nrhs, KMAX_RHS);
+    if (out_parity != LGT_EVEN && out_parity != LGT_ODD) return fail(LGT_EINVAL, "hop needs EVEN or ODD");
+    HopArgsM A;
+    memset(&A, 0, sizeof A);
+    A.U = L->thin.U12;
+    A.g = L->g;
+    A.parity = out_parity;
+    A.nrhs = nrhs;
+    for (int k = 0; k < nrhs; ++k) {
+        if (!in[k] || !out[k]) return fail(LGT_EINVAL, "null field of system %d", k);
+        A.in[k] = in[k]; A.out[k] = out[k]; A.a[k] = 1.0;
+    }
+    CK(launch_hop_multi(A, false, dagger != 0, EPI_HOP, L->st));
+    return LGT_OK;
+}
+
 // ---------------------------------------------------------------- smearing
 static int check_action(const lgt_action_params* ap) {
     if (!ap) return fail(LGT_EINVAL, "null action parameters");
-    if (ap->n_stout < 0 || ap->n_stout > 4) return fail(LGT_EINVAL, "n_stout = %d outside 0..4", ap->n_stout);
+    if (ap->n_stout < 0 || ap->n_stout > MAX_STOUT)
+        return fail(LGT_EINVAL, "n_stout = %d outside 0..%d", ap->n_stout, MAX_STOUT);
+    if (ap->stout_recompute < 0) return fail(LGT_EINVAL, "stout_recompute = %d", ap->stout_recompute);
+    if (ap->force_arith < LGT_ARITH_FP64 || ap->force_arith > LGT_ARITH_DF64)
+        return fail(LGT_EINVAL, "force_arith = %d", ap->force_arith);
     return LGT_OK;
 }
-// Smear the thin links through levels 1..n.  Stored mode keeps every level in
-// smeared[k]; recompute mode keeps only the top level (stout_top), alternating
-// with stout_tmp so that level n lands in stout_top.
-static int smear_to(lgt_lattice* L, int n, double rho, bool recompute, double2** level_n) {
+// Smear the thin links through levels 1..n into the fields of the plan.
+static int smear_to(lgt_lattice* L, const StoutPlan& P, double rho, double2** level_n) {
     const double2* src = L->thin.U;
-    for (int k = 1; k <= n; ++k) {
-        double2* dst = recompute ? (((n - k) % 2 == 0) ? L->stout_top : L->stout_tmp) : L->smeared[k];
+    for (int k = 1; k <= P.n; ++k) {
+        double2* dst = L->sbuf[P.slot(k)];
         CK(stout_forward(src, dst, L->g, rho, L->st));
         src = dst;
     }
     *level_n = (double2*)src;
     return LGT_OK;
 }
-// U_{k} for the adjoint of level k+1 in recompute mode: recomputed into stout_tmp
-// (stout_top is free once the top-level gradient exists)
-static int recompute_level(lgt_lattice* L, int k, double rho, const double2** out) {
-    if (k == 0) { *out = L->thin.U; return LGT_OK; }
-    const double2* src = L->thin.U;
-    for (int j = 1; j <= k; ++j) {
-        double2* dst = ((k - j) % 2 == 0) ? L->stout_tmp : L->stout_top;
-        CK(stout_forward(src, dst, L->g, rho, L->st));
-        src = dst;
-    }
-    *out = src;
-    return LGT_OK;
-}
 // links seen by the Dirac operator: thin, or the top stout level (+ its FP32 copy)
 static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out) {
     if (ap->n_stout == 0) { *out = L->thin; return LGT_OK; }
-    const bool rc = ap->stout_recompute != 0;
-    TRY(ensure_stout(L, ap->n_stout, rc));
+    TRY(ensure_stout(L, ap->n_stout, ap->stout_recompute));
     double2* top;
-    TRY(smear_to(L, ap->n_stout, ap->rho, rc, &top));
+    TRY(smear_to(L, stout_plan(ap->n_stout, ap->stout_recompute), ap->rho, &top));
     CK(gauge_make12(L->stout_top12, top, L->g, L->st));
     *out = Links{top, L->stout_top12};
     return LGT_OK;
@@ -682,9 +1062,16 @@ static int pf_action_on(lgt_lattice* L, const Links& lk, const lgt_action_params
     TRY(ensure_solver(L));
     const bool eo = ap->even_odd != 0;
     const int n = eo ? L->g.Vh : 2 * L->g.Vh;
-    TRY(cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats));
-    if (eo) TRY(dhat(L, lk, true, false, L->X, L->Y, L->t, ap->kappa));
-    else TRY(dfull(L, lk, true, false, L->X, L->Y, ap->kappa));
+    L->cap_X = L->X;
+    L->cap_Y = L->Y;
+    const int rc = cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats);
+    L->cap_X = L->cap_Y = nullptr;
+    TRY(rc);
+    // eta = M chi: left in Y by the solver's final residual, else computed here
+    if (!L->cap_valid) {
+        if (eo) TRY(dhat(L, lk, true, false, L->X, L->Y, L->t, ap->kappa));
+        else TRY(dfull(L, lk, true, false, L->X, L->Y, ap->kappa));
+    }
     CK(blas_action_parts(phi, L->X, L->Y, n, L->g.Vh, red(L), L->st));
     TRY(sync_scalars(L));
     *S_f = 2.0 * L->hs->slot[0] - L->hs->slot[1];
@@ -728,7 +1115,11 @@ extern "C" int lgt_kinetic_energy(lgt_lattice_t L, const double* mom, double* K)
 static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_params* ap, const double2* phi,
                          const lgt_solver_params* sp, lgt_solve_stats* stats, bool fp32) {
     const bool eo = ap->even_odd != 0;
-    TRY(cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats));
+    L->cap_X = L->X;
+    L->cap_Y = L->Y;
+    const int rc = cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats);
+    L->cap_X = L->cap_Y = nullptr;
+    TRY(rc);
     if (fp32) {
         if (eo) {
             float4* Xo = (float4*)half(L->X32, L, false, 1);
@@ -743,6 +1134,7 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
         }
         return LGT_OK;
     }
+    if (L->cap_valid) return LGT_OK;   // built by the solver's final FP64 residual
     if (eo) {
         double2* Xo = (double2*)half(L->X, L, true, 1);
         double2* Yo = (double2*)half(L->Y, L, true, 1);
@@ -757,13 +1149,17 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
 }
 
 // out = keep*out + coef * (dS_G + dS_f) in Lie (form 0) or G (form 1) layout, on the
-// links the actions see (no smearing here).  With the mixed solver and force_fp32 the
-// Lie form is computed in FP32 arithmetic (X, Y, staples, outer products) and
-// accumulated in FP64; otherwise every force kernel is FP64.
+// links the actions see (no smearing here).  With the mixed solver, Lie-form forces
+// use the arithmetic ap->force_arith: FP64 kernels, FP32 arithmetic on the FP32 links
+// and FP32 X, Y, or double-float arithmetic on double-float copies of the FP64 links
+// and FP64 X, Y; every variant accumulates into FP64.  FP64 solves, and the G form,
+// always use the FP64 kernels.
 static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk, const lgt_action_params* ap,
                     const double2* phi, const lgt_solver_params* sp, double coef, int keep, int form, double2* out,
                     lgt_solve_stats* stats) {
-    const bool fp32 = form == 0 && sp && sp->precision == LGT_MIXED && ap->force_fp32;
+    const int arith = (form == 0 && sp && sp->precision == LGT_MIXED) ? ap->force_arith : LGT_ARITH_FP64;
+    const bool fp32 = arith == LGT_ARITH_FP32, dfa = arith == LGT_ARITH_DF64;
+    if (dfa) TRY(ensure_df(L));
     if (ap->fermions) {
         if (!phi) return fail(LGT_EINVAL, "null phi");
         TRY(ensure_solver(L));
@@ -771,31 +1167,74 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
     }
     if (ap->beta != 0.0) {
         if (fp32) CK(gauge_force_fp32(gauge_lk.U12, L->g, ap->beta, coef, keep, out, L->st));
-        else CK(gauge_force(gauge_lk.U, L->g, ap->beta, coef, keep, form, out, L->st));
+        else if (dfa) {
+            CK(links_to_df(L->Udf, gauge_lk.U, L->g, L->st));
+            CK(gauge_force_df(L->Udf, L->g, ap->beta, coef, keep, out, L->st));
+        } else CK(gauge_force(gauge_lk.U, L->g, ap->beta, coef, keep, form, out, L->st));
         keep = 1;
     }
     if (ap->fermions) {
         if (fp32) CK(fermion_force_fp32(ferm_lk.U12, L->X32, L->Y32, L->g, ap->kappa, coef, keep, out, L->st));
-        else CK(fermion_force(ferm_lk.U, L->X, L->Y, L->g, ap->kappa, coef, keep, form, out, L->st));
+        else if (dfa) {
+            if (ap->beta == 0.0 || ferm_lk.U != gauge_lk.U) CK(links_to_df(L->Udf, ferm_lk.U, L->g, L->st));
+            CK(spinor_to_df(L->Xdf, L->X, L->g, L->st));
+            CK(spinor_to_df(L->Ydf, L->Y, L->g, L->st));
+            CK(fermion_force_df(L->Udf, L->Xdf, L->Ydf, L->g, ap->kappa, coef, keep, out, L->st));
+        } else CK(fermion_force(ferm_lk.U, L->X, L->Y, L->g, ap->kappa, coef, keep, form, out, L->st));
         keep = 1;
     }
     if (!keep) CK(cudaMemsetAsync(out, 0, form == 0 ? mom_bytes(L) : links64(L), L->st));
     return LGT_OK;
 }
 
-// Adjoint of the smearing levels n..1: sgrad[0] holds the gradient w.r.t. the top
-// level on entry; the gradient w.r.t. the thin links is written to G.
+// Adjoint of the smearing levels n..1 (after smear_to with the same plan): sgrad[0]
+// holds the gradient w.r.t. the top level on entry; the gradient w.r.t. the thin
+// links is written to G.  The input U_{k-1} of level k is read from where the plan
+// keeps it, or recomputed (mode 1: from the thin links; checkpoint mode: each
+// segment below the top one from its checkpoint, once).
 static int stout_chain(lgt_lattice* L, const lgt_action_params* ap, double2* G) {
+    const StoutPlan P = stout_plan(ap->n_stout, ap->stout_recompute);
     double2* ga = L->sgrad[0];
     double2* gb = L->sgrad[1];
-    const bool rc = ap->stout_recompute != 0;
-    for (int k = ap->n_stout; k >= 1; --k) {
-        const double2* Uin;
-        if (rc) TRY(recompute_level(L, k - 1, ap->rho, &Uin));
-        else Uin = L->smeared[k - 1];
+    const double rho = ap->rho;
+    auto step = [&](int k, const double2* Uin) -> int {
         double2* dst = (k == 1) ? G : gb;
-        CK(stout_backward(Uin, ga, dst, L->sgrad[2], L->g, ap->rho, L->st));
+        CK(stout_backward(Uin, ga, dst, L->sgrad[2], L->g, rho, L->st));
         std::swap(ga, gb);
+        return LGT_OK;
+    };
+    if (P.m == 0) {
+        for (int k = P.n; k >= 1; --k) TRY(step(k, k == 1 ? L->thin.U : L->sbuf[P.slot(k - 1)]));
+    } else if (P.m == 1) {
+        // U_{k-1} recomputed from the thin links into the field the top level does not use
+        // (the top level itself is no longer needed once its gradient exists)
+        for (int k = P.n; k >= 1; --k) {
+            const double2* src = L->thin.U;
+            for (int j = 1; j <= k - 1; ++j) {
+                double2* dst = L->sbuf[((k - 1 - j) % 2 == 0) ? 1 : 0];
+                CK(stout_forward(src, dst, L->g, rho, L->st));
+                src = dst;
+            }
+            TRY(step(k, src));
+        }
+    } else {
+        const int c = P.c;
+        for (int s0 = ((P.n - 1) / c) * c; s0 >= 0; s0 -= c) {
+            const int e = std::min(s0 + c, P.n);
+            const double2* base = (s0 == 0) ? L->thin.U : L->sbuf[P.slot(s0)];
+            // levels s0+1 .. e-1 into the segment fields (the top segment's are still
+            // there from the forward pass)
+            if (e != P.n || s0 + c < P.n) {
+                const double2* src = base;
+                for (int k = s0 + 1; k <= e - 1; ++k) {
+                    double2* dst = L->sbuf[P.nck + (k - s0)];
+                    CK(stout_forward(src, dst, L->g, rho, L->st));
+                    src = dst;
+                }
+            }
+            for (int k = e; k >= s0 + 1; --k)
+                TRY(step(k, (k - 1 == s0) ? base : L->sbuf[P.nck + (k - 1 - s0)]));
+        }
     }
     return LGT_OK;
 }
@@ -991,6 +1430,7 @@ extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, 
     TRY(ensure_solver(L));
     memset(res, 0, sizeof *res);
     const bool eo = ap->even_odd != 0;
+    L->ch.n = L->ch.head = 0;   // a new pseudofermion source: earlier solutions do not apply
     CK(cudaMemcpyAsync(L->Ubak, L->thin.U, links64(L), cudaMemcpyDeviceToDevice, L->st));
     CK(gauge_momenta_heatbath(L->mom, L->g, seed, traj, L->st));
     TRY(lgt_kinetic_energy(L, (const double*)L->mom, &res->K_old));

@@ -128,6 +128,22 @@ cudaError_t launch_p_update_batch(const BatchAxpy* d, int n, int total_blocks, b
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void __launch_bounds__(NT) p_update_multi_kernel(PUpdateM P, long ne) {
+    const int k = blockIdx.y;
+    if (k >= P.nrhs) return;
+    p_update_body<T>((T*)P.p[k], (const T*)P.r[k], ne, P.red[k], blockIdx.x, gridDim.x);
+}
+cudaError_t blas_cg_p_update_multi(const PUpdateM& P, int n, bool fp64, cudaStream_t st) {
+    if (P.nrhs < 1 || P.nrhs > KMAX_RHS) return cudaErrorInvalidValue;
+    const long ne = (long)n * (fp64 ? 12 : 6);
+    const dim3 grid(grid_for(ne), P.nrhs);
+    if (fp64) p_update_multi_kernel<double2><<<grid, NT, 0, st>>>(P, ne);
+    else p_update_multi_kernel<float4><<<grid, NT, 0, st>>>(P, ne);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t blas_cg_p_update(void* p, const void* r, int n, int Vh, bool fp64, const RedArgs& R,
                              cudaStream_t st) {
     (void)Vh;

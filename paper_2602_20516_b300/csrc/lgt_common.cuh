@@ -357,8 +357,15 @@ __device__ __forceinline__ void grid_reduce(double block_partial, double* partia
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < nblk; k += NT) acc += __ldcg(partials + k);
+    // eight independent loads in flight per thread (a fixed summation order, so the
+    // result is the same on every run)
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < nblk; k += 8 * NT) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (k + j * NT < nblk) a[j] += __ldcg(partials + k + j * NT);
+    }
+    double acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     acc = block_sum(acc);
     if (threadIdx.x == 0) {
         *counter = 0u;

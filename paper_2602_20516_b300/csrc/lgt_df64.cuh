@@ -1,0 +1,154 @@
+// lgt_df64.cuh -- double-float arithmetic: a value is the unevaluated sum hi + lo of
+// two FP32 numbers (|lo| <= ulp(hi)/2), about 48 significant bits.  On this part an
+// FP64 FMA issues at 1/64 of the FP32 rate, so FP64-accurate products of link
+// matrices are cheaper as FP32 pairs.  Built from the error-free transformations
+// TwoSum (Knuth) and TwoProduct with a fused multiply-add (Dekker's product without
+// splitting); a dot product keeps one running FP32 sum with its rounding errors
+// collected in a second FP32 word, as in the compensated dot product Dot2 of Ogita,
+// Rump and Oishi (SIAM J. Sci. Comput. 26 (2005) 1955), with the low words of the
+// operands entering through the error word.
+//
+// Every addition and product whose rounding error is captured uses the _rn
+// intrinsics, which the compiler never contracts into an FMA.
+#pragma once
+#include "lgt_common.cuh"
+
+namespace lgt {
+
+struct df { float h, l; };
+struct dfc { df r, i; };
+struct dfmat { dfc e[3][3]; };
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ df df_from(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(df a) { return (double)a.h + (double)a.l; }
+
+// s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// h + l = s + c with |l| <= ulp(h)/2 (needs |s| >= |c| or s = 0)
+__device__ __forceinline__ df fast_renorm(float s, float c) {
+    const float h = __fadd_rn(s, c);
+    return {h, __fsub_rn(c, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    return fast_renorm(s, e);
+}
+
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfc operator+(const dfc& a, const dfc& b) { return {df_add(a.r, b.r), df_add(a.i, b.i)}; }
+__device__ __forceinline__ dfc operator-(const dfc& a, const dfc& b) { return {df_sub(a.r, b.r), df_sub(a.i, b.i)}; }
+__device__ __forceinline__ dfc operator-(const dfc& a) { return {df_neg(a.r), df_neg(a.i)}; }
+__device__ __forceinline__ dfc times_i(const dfc& a) { return {df_neg(a.i), a.r}; }
+
+// compensated accumulator: value s + c
+struct dacc {
+    float s, c;
+};
+__device__ __forceinline__ dacc dacc0() { return {0.f, 0.f}; }
+// A += a * b  (a, b double-floats; the lo*lo term is below the format's precision)
+__device__ __forceinline__ void dacc_mul(dacc& A, df a, df b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);   // exact rounding error of the product
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    float s, t;
+    two_sum(A.s, p, s, t);
+    A.s = s;
+    A.c = __fadd_rn(A.c, __fadd_rn(t, e));
+}
+// A += a (a double-float)
+__device__ __forceinline__ void dacc_add(dacc& A, df a) {
+    float s, t;
+    two_sum(A.s, a.h, s, t);
+    A.s = s;
+    A.c = __fadd_rn(A.c, __fadd_rn(t, a.l));
+}
+__device__ __forceinline__ df dacc_get(const dacc& A) {
+    // s carries the leading part; renormalise with TwoSum (no magnitude assumption)
+    float h, l;
+    two_sum(A.s, A.c, h, l);
+    return {h, l};
+}
+
+// complex multiply-accumulate into a pair of accumulators (re, im):
+//   conj flags select a, b or their conjugates
+template <bool CA, bool CB>
+__device__ __forceinline__ void cacc_mul(dacc& re, dacc& im, const dfc& a, const dfc& b) {
+    const df ai = CA ? df_neg(a.i) : a.i;
+    const df bi = CB ? df_neg(b.i) : b.i;
+    dacc_mul(re, a.r, b.r);
+    dacc_mul(re, df_neg(ai), bi);
+    dacc_mul(im, a.r, bi);
+    dacc_mul(im, ai, b.r);
+}
+
+// C = op(A) op(B) with op = identity or Hermitian conjugate
+template <bool DA, bool DB>
+__device__ __forceinline__ dfmat df_mul(const dfmat& A, const dfmat& B) {
+    dfmat C;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dacc re = dacc0(), im = dacc0();
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const dfc& a = DA ? A.e[k][i] : A.e[i][k];
+                const dfc& b = DB ? B.e[j][k] : B.e[k][j];
+                cacc_mul<DA, DB>(re, im, a, b);
+            }
+            C.e[i][j] = {dacc_get(re), dacc_get(im)};
+        }
+    return C;
+}
+__device__ __forceinline__ void df_add_to(dfmat& A, const dfmat& B) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            A.e[i][j].r = df_add(A.e[i][j].r, B.e[i][j].r);
+            A.e[i][j].i = df_add(A.e[i][j].i, B.e[i][j].i);
+        }
+}
+__device__ __forceinline__ dfmat df_zero3() {
+    dfmat C;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) C.e[i][j] = {{0.f, 0.f}, {0.f, 0.f}};
+    return C;
+}
+
+// double-float links: float4 [parity][4][9][Vh], entry k = (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ dfmat load_link_df(const float4* __restrict__ U, int Vh, int p, int mu, int i) {
+    const float4* b = U + (size_t)((p * 4 + mu) * 9) * Vh + i;
+    dfmat m;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float4 v = __ldg(b + (size_t)k * Vh);
+        m.e[k / 3][k % 3] = {{v.x, v.y}, {v.z, v.w}};
+    }
+    return m;
+}
+__device__ __forceinline__ void store_link_df(float4* __restrict__ U, int Vh, int p, int mu, int i, const dmat& m) {
+    float4* b = U + (size_t)((p * 4 + mu) * 9) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const df r = df_from(m.e[k / 3][k % 3].r), im = df_from(m.e[k / 3][k % 3].i);
+        b[(size_t)k * Vh] = make_float4(r.h, r.l, im.h, im.l);
+    }
+}
+
+}  // namespace lgt

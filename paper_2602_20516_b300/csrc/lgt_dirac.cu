@@ -94,87 +94,92 @@ template <typename R> __device__ __forceinline__ double sq(const cx<R> (&v)[4][3
     return (double)acc;
 }
 
+// The work of one output site t (t < n): accumulate the 8 hops, apply the epilogue
+// and return this site's contribution to the epilogue's reduction.
 template <typename R, bool DAG, int EPI>
-__device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk) {
+__device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
     using P = Prec<R>;
     using T = typename P::T;
-    if (A.skip && A.s->done >= 1) return;
-    const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
-    const int t = blk * NT + threadIdx.x;
-    const bool valid = t < n;
     double red = 0.0;
-    if (valid) {
-        int p, i;
-        if (A.parity == 2) { p = t >= A.g.Vh; i = t - p * A.g.Vh; }
-        else { p = A.parity; i = t; }
-        int x[4];
-        int lex = eo_coords(A.g, p, i, x);
-        cx<R> out[4][3];
+    int p, i;
+    if (A.parity == 2) { p = t >= A.g.Vh; i = t - p * A.g.Vh; }
+    else { p = A.parity; i = t; }
+    int x[4];
+    int lex = eo_coords(A.g, p, i, x);
+    cx<R> out[4][3];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) out[a][c] = {0, 0};
-        constexpr int SF = DAG ? +1 : -1;
-        constexpr int SB = -SF;
-        hop_dir<0, SF, SB, R>(A, p, lex, x, i, out);
-        hop_dir<1, SF, SB, R>(A, p, lex, x, i, out);
-        hop_dir<2, SF, SB, R>(A, p, lex, x, i, out);
-        hop_dir<3, SF, SB, R>(A, p, lex, x, i, out);
-        const R a = (R)A.a;
-        const int Vh = A.g.Vh;
-        if (EPI == EPI_HOP) {
+        for (int c = 0; c < 3; ++c) out[a][c] = {0, 0};
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    hop_dir<0, SF, SB, R>(A, p, lex, x, i, out);
+    hop_dir<1, SF, SB, R>(A, p, lex, x, i, out);
+    hop_dir<2, SF, SB, R>(A, p, lex, x, i, out);
+    hop_dir<3, SF, SB, R>(A, p, lex, x, i, out);
+    const R a = (R)A.a;
+    const int Vh = A.g.Vh;
+    if (EPI == EPI_HOP) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
+        for (int s = 0; s < 4; ++s)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) out[s][c] = a * out[s][c];
-            typename P::S o;
+            for (int c = 0; c < 3; ++c) out[s][c] = a * out[s][c];
+        typename P::S o;
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
+        for (int s = 0; s < 4; ++s)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) o.c[s][c] = out[s][c];
+            for (int c = 0; c < 3; ++c) o.c[s][c] = out[s][c];
+        store_spinor((T*)A.out[p], Vh, i, o);
+    } else {
+        typename P::S yv = load_spinor((const T*)A.y[p], Vh, i);
+        typename P::S o;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o.c[s][c].r = fma(a, out[s][c].r, yv.c[s][c].r);
+                o.c[s][c].i = fma(a, out[s][c].i, yv.c[s][c].i);
+            }
+        if (EPI == EPI_XPAY || EPI == EPI_XPAY_NORM) {
             store_spinor((T*)A.out[p], Vh, i, o);
-        } else {
-            typename P::S yv = load_spinor((const T*)A.y[p], Vh, i);
-            typename P::S o;
+            if (EPI == EPI_XPAY_NORM) red = sq<R>(o.c);
+        } else if (EPI == EPI_CG) {
+            // o = A p at this site: x += alpha p, r -= alpha A p, red = |r|^2
+            const R alpha = (R)A.s->alpha;
+            typename P::S xv = load_spinor((const T*)A.x[p], Vh, i);
+            typename P::S rv = load_spinor((const T*)A.r[p], Vh, i);
+            typename P::S pv = load_spinor((const T*)A.pv[p], Vh, i);
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    o.c[s][c].r = fma(a, out[s][c].r, yv.c[s][c].r);
-                    o.c[s][c].i = fma(a, out[s][c].i, yv.c[s][c].i);
+                    xv.c[s][c].r = fma(alpha, pv.c[s][c].r, xv.c[s][c].r);
+                    xv.c[s][c].i = fma(alpha, pv.c[s][c].i, xv.c[s][c].i);
+                    rv.c[s][c].r = fma(-alpha, o.c[s][c].r, rv.c[s][c].r);
+                    rv.c[s][c].i = fma(-alpha, o.c[s][c].i, rv.c[s][c].i);
                 }
-            if (EPI == EPI_XPAY || EPI == EPI_XPAY_NORM) {
-                store_spinor((T*)A.out[p], Vh, i, o);
-                if (EPI == EPI_XPAY_NORM) red = sq<R>(o.c);
-            } else if (EPI == EPI_CG) {
-                // o = A p at this site: x += alpha p, r -= alpha A p, red = |r|^2
-                const R alpha = (R)A.s->alpha;
-                typename P::S xv = load_spinor((const T*)A.x[p], Vh, i);
-                typename P::S rv = load_spinor((const T*)A.r[p], Vh, i);
-                typename P::S pv = load_spinor((const T*)A.pv[p], Vh, i);
+            store_spinor((T*)A.x[p], Vh, i, xv);
+            store_spinor((T*)A.r[p], Vh, i, rv);
+            red = sq<R>(rv.c);
+        } else {  // EPI_RESID: out = b - A x, b in pv
+            typename P::S bv = load_spinor((const T*)A.pv[p], Vh, i);
 #pragma unroll
-                for (int s = 0; s < 4; ++s)
+            for (int s = 0; s < 4; ++s)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        xv.c[s][c].r = fma(alpha, pv.c[s][c].r, xv.c[s][c].r);
-                        xv.c[s][c].i = fma(alpha, pv.c[s][c].i, xv.c[s][c].i);
-                        rv.c[s][c].r = fma(-alpha, o.c[s][c].r, rv.c[s][c].r);
-                        rv.c[s][c].i = fma(-alpha, o.c[s][c].i, rv.c[s][c].i);
-                    }
-                store_spinor((T*)A.x[p], Vh, i, xv);
-                store_spinor((T*)A.r[p], Vh, i, rv);
-                red = sq<R>(rv.c);
-            } else {  // EPI_RESID: out = b - A x, b in pv
-                typename P::S bv = load_spinor((const T*)A.pv[p], Vh, i);
-#pragma unroll
-                for (int s = 0; s < 4; ++s)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) o.c[s][c] = bv.c[s][c] - o.c[s][c];
-                store_spinor((T*)A.out[p], Vh, i, o);
-                red = sq<R>(o.c);
-            }
+                for (int c = 0; c < 3; ++c) o.c[s][c] = bv.c[s][c] - o.c[s][c];
+            store_spinor((T*)A.out[p], Vh, i, o);
+            red = sq<R>(o.c);
         }
     }
+    return red;
+}
+
+template <typename R, bool DAG, int EPI>
+__device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk) {
+    if (A.skip && A.s->done >= 1) return;
+    const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
+    const int t = blk * NT + threadIdx.x;
+    const double red = (t < n) ? hop_site<R, DAG, EPI>(A, t) : 0.0;
     if (EPI == EPI_XPAY_NORM || EPI == EPI_CG || EPI == EPI_RESID) {
         double b = block_sum(red);
         grid_reduce(b, A.partials, A.counter, A.s, A.red_op, A.red_slot, blk, nblk);
@@ -187,7 +192,7 @@ __device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk) {
 #define LGT_HOP32_MIN_BLOCKS 4
 #endif
 #ifndef LGT_HOP32_EPI_MIN_BLOCKS
-#define LGT_HOP32_EPI_MIN_BLOCKS 6
+#define LGT_HOP32_EPI_MIN_BLOCKS 4
 #endif
 template <typename R, int EPI> constexpr int hop_min_blocks() {
     return sizeof(R) == 4 ? (EPI == EPI_HOP ? LGT_HOP32_MIN_BLOCKS : LGT_HOP32_EPI_MIN_BLOCKS) : 1;
@@ -257,6 +262,178 @@ static cudaError_t launch_epi(const HopArgs& A, int epi, cudaStream_t st) {
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st) {
     if (fp64) return dagger ? launch_epi<double, true>(A, epi, st) : launch_epi<double, false>(A, epi, st);
     return dagger ? launch_epi<float, true>(A, epi, st) : launch_epi<float, false>(A, epi, st);
+}
+
+// ---------------------------------------------------------------- several right-hand sides
+// One thread per output site for K systems: each link is loaded once per site and
+// direction and applied to the K input spinors, so a launch moves 8 links + K (in +
+// out) spinors per site instead of K times 8 links + 1 pair.  The K slots are
+// computed in straight-line code (the host packs only running systems, so every
+// slot holds valid fields) and the loads of all directions and systems can be in
+// flight together; a system whose scalars say done is masked at its stores and its
+// reduction.  Per system the arithmetic is that of hop_site (same direction order,
+// same epilogue) and the reduction is block_sum / grid_reduce over the same 128
+// sites per block, so a system's result does not depend on the others in the launch.
+template <int MU, int SF, int SB, typename R, int K>
+__device__ __forceinline__ void hop_dir_multi(const HopArgsM& A, int p, int lex, const int (&x)[4], int i,
+                                              cx<R> (&out)[K][4][3]) {
+    using P = Prec<R>;
+    const int Vh = A.g.Vh;
+    {
+        const int j = nb_lex(A.g, lex, x, MU, +1) >> 1;
+        const mat3<R> M = P::link(A.U, Vh, p, MU, i);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            typename P::S s = load_spinor((const typename P::T*)A.in[k], Vh, j);
+            cx<R> h[2][3], uh[2][3];
+            project<MU, SF>(s.c, h);
+            if (MU == 3 && x[3] == A.g.L[3] - 1) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) { h[0][c] = -h[0][c]; h[1][c] = -h[1][c]; }
+            }
+            mult<false>(M, h, uh);
+            accumulate<MU, SF>(out[k], uh);
+        }
+    }
+    {
+        const int j = nb_lex(A.g, lex, x, MU, -1) >> 1;
+        const mat3<R> M = P::link(A.U, Vh, 1 - p, MU, j);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            typename P::S s = load_spinor((const typename P::T*)A.in[k], Vh, j);
+            cx<R> h[2][3], uh[2][3];
+            project<MU, SB>(s.c, h);
+            if (MU == 3 && x[3] == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) { h[0][c] = -h[0][c]; h[1][c] = -h[1][c]; }
+            }
+            mult<true>(M, h, uh);
+            accumulate<MU, SB>(out[k], uh);
+        }
+    }
+}
+
+template <typename R, bool DAG, int EPI, int K>
+__global__ void __launch_bounds__(NT, (K == 1 ? 4 : (K == 2 ? 3 : 2))) hop_multi_kernel(HopArgsM A) {
+    using P = Prec<R>;
+    using T = typename P::T;
+    bool act[K];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        act[k] = !(A.skip && A.s[k]->done >= 1);
+        any = any || act[k];
+    }
+    if (!any) return;
+    const int t = blockIdx.x * NT + threadIdx.x;
+    double red[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[k] = 0.0;
+    if (t < A.g.Vh) {
+        const int p = A.parity, i = t;
+        int x[4];
+        const int lex = eo_coords(A.g, p, i, x);
+        cx<R> out[K][4][3];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[k][a][c] = {0, 0};
+        constexpr int SF = DAG ? +1 : -1;
+        constexpr int SB = -SF;
+        hop_dir_multi<0, SF, SB, R, K>(A, p, lex, x, i, out);
+        hop_dir_multi<1, SF, SB, R, K>(A, p, lex, x, i, out);
+        hop_dir_multi<2, SF, SB, R, K>(A, p, lex, x, i, out);
+        hop_dir_multi<3, SF, SB, R, K>(A, p, lex, x, i, out);
+        const int Vh = A.g.Vh;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!act[k]) continue;
+            const R a = (R)A.a[k];
+            if (EPI == EPI_HOP) {
+                typename P::S o;
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) o.c[s][c] = a * out[k][s][c];
+                store_spinor((T*)A.out[k], Vh, i, o);
+            } else {
+                const typename P::S yv = load_spinor((const T*)A.y[k], Vh, i);
+                typename P::S o;
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        o.c[s][c].r = fma(a, out[k][s][c].r, yv.c[s][c].r);
+                        o.c[s][c].i = fma(a, out[k][s][c].i, yv.c[s][c].i);
+                    }
+                if (EPI == EPI_XPAY || EPI == EPI_XPAY_NORM) {
+                    store_spinor((T*)A.out[k], Vh, i, o);
+                    if (EPI == EPI_XPAY_NORM) red[k] = sq<R>(o.c);
+                } else {  // EPI_CG
+                    const R alpha = (R)A.s[k]->alpha;
+                    typename P::S xv = load_spinor((const T*)A.x[k], Vh, i);
+                    typename P::S rv = load_spinor((const T*)A.r[k], Vh, i);
+                    const typename P::S pv = load_spinor((const T*)A.pv[k], Vh, i);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            xv.c[s][c].r = fma(alpha, pv.c[s][c].r, xv.c[s][c].r);
+                            xv.c[s][c].i = fma(alpha, pv.c[s][c].i, xv.c[s][c].i);
+                            rv.c[s][c].r = fma(-alpha, o.c[s][c].r, rv.c[s][c].r);
+                            rv.c[s][c].i = fma(-alpha, o.c[s][c].i, rv.c[s][c].i);
+                        }
+                    store_spinor((T*)A.x[k], Vh, i, xv);
+                    store_spinor((T*)A.r[k], Vh, i, rv);
+                    red[k] = sq<R>(rv.c);
+                }
+            }
+        }
+    }
+    if (EPI == EPI_XPAY_NORM || EPI == EPI_CG) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!act[k]) continue;   // the same for every block of the launch
+            const double b = block_sum(red[k]);
+            grid_reduce(b, A.partials[k], A.counter[k], A.s[k], A.red_op, 0, blockIdx.x, gridDim.x);
+        }
+    }
+}
+
+template <bool DAG, int K>
+static cudaError_t launch_multi_epi(const HopArgsM& A, int epi, cudaStream_t st) {
+    const int grid = (A.g.Vh + NT - 1) / NT;
+    switch (epi) {
+    case EPI_HOP: hop_multi_kernel<float, DAG, EPI_HOP, K><<<grid, NT, 0, st>>>(A); break;
+    case EPI_XPAY: hop_multi_kernel<float, DAG, EPI_XPAY, K><<<grid, NT, 0, st>>>(A); break;
+    case EPI_XPAY_NORM: hop_multi_kernel<float, DAG, EPI_XPAY_NORM, K><<<grid, NT, 0, st>>>(A); break;
+    case EPI_CG: hop_multi_kernel<float, DAG, EPI_CG, K><<<grid, NT, 0, st>>>(A); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+template <bool DAG>
+static cudaError_t launch_multi_k(const HopArgsM& A, int epi, cudaStream_t st) {
+    switch (A.nrhs) {
+    case 1: return launch_multi_epi<DAG, 1>(A, epi, st);
+    case 2: return launch_multi_epi<DAG, 2>(A, epi, st);
+    case 3: return launch_multi_epi<DAG, 3>(A, epi, st);
+    default: return launch_multi_epi<DAG, 4>(A, epi, st);
+    }
+}
+
+// FP32 only: the FP64 hop is bound by FP64 arithmetic, which sharing link loads
+// does not reduce (and K FP64 accumulators exceed the register file)
+cudaError_t launch_hop_multi(const HopArgsM& A, bool fp64, bool dagger, int epi, cudaStream_t st) {
+    if (fp64 || A.nrhs < 1 || A.nrhs > KMAX_RHS || (A.parity != 0 && A.parity != 1)) return cudaErrorInvalidValue;
+    for (int k = 0; k < A.nrhs; ++k)
+        if (!A.in[k]) return cudaErrorInvalidValue;
+    const bool reduces = epi == EPI_XPAY_NORM || epi == EPI_CG;
+    if (reduces && (A.g.Vh + NT - 1) / NT > A.red_capacity) return cudaErrorInvalidValue;
+    return dagger ? launch_multi_k<true>(A, epi, st) : launch_multi_k<false>(A, epi, st);
 }
 
 int hop_grid(const Geom& g, int parity) {

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(NT) random_links_kernel(double2* U, float4* U1
     double h[8];
     for (int j = 0; j < 4; ++j) gauss_pair(seed, (uint32_t)(4 * lex + mu), j, 0, FIELD_LINKS, h[2 * j], h[2 * j + 1]);
     for (int a = 0; a < 8; ++a) h[a] *= alpha;
-    dmat m = expiQ(herm_from_lie(h));
+    dmat m = expiQ_h(herm_parts_lie(h));
     store_link(U, g.Vh, p, mu, i, m);
     store_link12(U12, g.Vh, p, mu, i, m);
 }
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(NT) update_links_kernel(double2* U, float4* U1
     double pi[8];
     load_mom(mom, g.Vh, p, mu, i, pi);
     for (int a = 0; a < 8; ++a) pi[a] *= eps;
-    dmat E = expiQ(herm_from_lie(pi));
+    dmat E = expiQ_h(herm_parts_lie(pi));
     dmat m = mul(E, load_link(U, g.Vh, p, mu, i));
     store_link(U, g.Vh, p, mu, i, m);
     store_link12(U12, g.Vh, p, mu, i, m);

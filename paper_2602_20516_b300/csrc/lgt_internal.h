@@ -35,6 +35,33 @@ struct HopArgs {
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st);
 int hop_grid(const Geom& g, int parity);
 
+// Several right-hand sides (1..KMAX_RHS, every slot a valid system) on the same FP32
+// links and output parity in one launch: each link is loaded once per site and
+// direction for all of them.  System k is masked (skip = 1) once its scalars say
+// done; its epilogue and its reduction (own scalars, partials and counter) are
+// those of the single-system hop.
+constexpr int KMAX_RHS = 4;
+struct HopArgsM {
+    const void* U;
+    Geom g;
+    int parity;           // output parity, 0 or 1
+    int nrhs;
+    int skip;
+    int red_op;
+    int red_capacity;
+    const void* in[KMAX_RHS];   // half fields of parity 1 - parity
+    void* out[KMAX_RHS];
+    const void* y[KMAX_RHS];
+    void* x[KMAX_RHS];
+    void* r[KMAX_RHS];
+    const void* pv[KMAX_RHS];
+    double a[KMAX_RHS];
+    Scalars* s[KMAX_RHS];
+    double* partials[KMAX_RHS];
+    unsigned* counter[KMAX_RHS];
+};
+cudaError_t launch_hop_multi(const HopArgsM& A, bool fp64, bool dagger, int epi, cudaStream_t st);
+
 // One entry of a batched launch: the hop arguments of one problem and its block
 // range [first, first + nblk) in the combined grid (entries sorted by first).
 struct BatchHop {
@@ -76,6 +103,15 @@ struct BatchAxpy {
     int first, nblk;
 };
 cudaError_t launch_p_update_batch(const BatchAxpy* d_desc, int n, int total_blocks, bool fp64, cudaStream_t st);
+// p_k = r_k + beta_k p_k for nrhs systems of n sites each (one launch, blockIdx.y = k),
+// each with its own scalars and counter, as blas_cg_p_update
+struct PUpdateM {
+    void* p[KMAX_RHS];
+    const void* r[KMAX_RHS];
+    RedArgs red[KMAX_RHS];
+    int nrhs;
+};
+cudaError_t blas_cg_p_update_multi(const PUpdateM& P, int n, bool fp64, cudaStream_t st);
 // y = x (FP64 -> FP32 rounding) / y64 += x32 / y = x
 cudaError_t blas_d2f(float4* y, const double2* x, int n, int Vh, cudaStream_t st);
 cudaError_t blas_add_f2d(double2* y, const float4* x, int n, int Vh, cudaStream_t st);
@@ -126,6 +162,36 @@ cudaError_t fermion_force(const double2* U, const double2* X, const double2* Y, 
 // Lie form with FP32 arithmetic: X, Y float4 [2][6][Vh], two-row FP32 links; FP64 output
 cudaError_t fermion_force_fp32(const float4* U12, const float4* X, const float4* Y, const Geom& g, double kappa,
                                double coef, int keep, double2* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- chronological guess (lgt_chrono.cu)
+constexpr int CHRONO_MAX = KMAX_RHS;               // solutions kept
+constexpr int CDOT_MAX = CHRONO_MAX * CHRONO_MAX;  // inner products per launch
+// out[m] = <a_m, b_m> (complex, conj(a) b) over even-odd half fields of Vh sites:
+// a_m FP64 (double2 [12][Vh]), b_m FP64 or FP32 (float4 [6][Vh]); m < M <= CDOT_MAX.
+struct CdotArgs {
+    const void* a[CDOT_MAX];
+    const void* b[CDOT_MAX];
+    double2* out;        // [M]
+    double2* partials;   // [M][blocks]
+    unsigned* counter;   // [M], zero between launches
+    int Vh;
+    long capacity;       // double2 entries of partials
+};
+cudaError_t cdot_many(const CdotArgs& D, int M, bool b_fp32, cudaStream_t st);
+// G c = g for the N x N Hermitian G (row-major), dependent vectors dropped (c = 0)
+cudaError_t chrono_solve(const double2* G, const double2* g, double2* c, int N, int* used, cudaStream_t st);
+// x = sum_i c_i v_i (FP64 half fields)
+cudaError_t chrono_combine(double2* x, const double2* const* v, const double2* c, int N, int Vh, cudaStream_t st);
+
+// ---------------------------------------------------------------- double-float forces (lgt_force_df.cu)
+// FP64 links / full spinor field -> double-float copies (float4 per complex entry)
+cudaError_t links_to_df(float4* Udf, const double2* U, const Geom& g, cudaStream_t st);
+cudaError_t spinor_to_df(float4* y, const double2* x, const Geom& g, cudaStream_t st);
+// Lie form, out = keep*out + coef*F, double-float arithmetic, FP64 accumulation
+cudaError_t gauge_force_df(const float4* Udf, const Geom& g, double beta, double coef, int keep, double2* out,
+                           cudaStream_t st);
+cudaError_t fermion_force_df(const float4* Udf, const float4* Xdf, const float4* Ydf, const Geom& g, double kappa,
+                             double coef, int keep, double2* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- stout (lgt_stout.cu)
 cudaError_t stout_forward(const double2* Uin, double2* Uout, const Geom& g, double rho, cudaStream_t st);

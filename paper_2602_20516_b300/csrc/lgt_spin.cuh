@@ -7,9 +7,10 @@
 
 namespace lgt {
 
-// (1 + S g_MU) psi = (h0, h1, recon): h_j are two colour vectors
-template <int MU, int S, typename R>
-__device__ __forceinline__ void project(const cx<R> (&psi)[4][3], cx<R> (&h)[2][3]) {
+// (1 + S g_MU) psi = (h0, h1, recon): h_j are two colour vectors.  C is a complex
+// type with +, - and times_i (cx<float>, cx<double> or the double-float dfc).
+template <int MU, int S, typename C>
+__device__ __forceinline__ void project(const C (&psi)[4][3], C (&h)[2][3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if (MU == 0) {

@@ -35,7 +35,7 @@ class LGTError(RuntimeError):
 
 class SolverParams(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
-                ("delta", C.c_double), ("check_every", C.c_int)]
+                ("delta", C.c_double), ("check_every", C.c_int), ("chrono", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -49,7 +49,7 @@ class SolveStats(C.Structure):
 class ActionParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("fermions", C.c_int),
                 ("even_odd", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double),
-                ("stout_recompute", C.c_int), ("force_fp32", C.c_int)]
+                ("stout_recompute", C.c_int), ("force_arith", C.c_int)]
 
 
 class HMCParams(C.Structure):
@@ -121,6 +121,10 @@ SIGNATURES = [
     ("lgt_unpack_links_field", _I, [_P, _P, _P]),
     ("lgt_dslash", _I, [_P, _P, _P, _I, _I, _I, _D, _I]),
     ("lgt_cg_solve", _I, [_P, _P, _P, _D, _I, C.POINTER(SolverParams), C.POINTER(SolveStats)]),
+    ("lgt_cg_solve_multi", _I, [_P, _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D), C.POINTER(SolverParams),
+                                C.POINTER(SolveStats)]),
+    ("lgt_hop_multi", _I, [_P, _I, C.POINTER(_P), C.POINTER(_P), _I, _I]),
+    ("lgt_chrono_reset", _I, [_P]),
     ("lgt_action", _I, [_P, C.POINTER(ActionParams), _P, C.POINTER(SolverParams), C.POINTER(_D),
                         C.POINTER(_D), C.POINTER(SolveStats)]),
     ("lgt_kinetic_energy", _I, [_P, _P, C.POINTER(_D)]),
@@ -176,15 +180,22 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def solver(precision="fp64", tol=1e-10, max_iter=10000, delta=1e-3, check_every=16):
+def solver(precision="fp64", tol=1e-10, max_iter=10000, delta=1e-3, check_every=16, chrono=0):
+    """chrono = N > 0: even-odd solves start from the best combination of the handle's
+    last N solutions of the same operator (chronological initial guess)."""
     prec = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else precision
-    return SolverParams(prec, tol, max_iter, delta, check_every)
+    return SolverParams(prec, tol, max_iter, delta, check_every, chrono)
+
+
+ARITH = {"fp64": 0, "fp32": 1, "df64": 2}
 
 
 def action_params(beta=0.0, kappa=0.0, fermions=True, even_odd=False, n_stout=0, rho=0.0,
-                  stout_recompute=False, force_fp32=False):
+                  stout_recompute=False, force_arith="fp64"):
+    """force_arith: arithmetic of Lie-form forces with the mixed solver ("fp64",
+    "fp32" or "df64", the double-float FP32-pair format)."""
     return ActionParams(beta, kappa, int(fermions), int(even_odd), n_stout, rho, int(stout_recompute),
-                        int(force_fp32))
+                        ARITH[force_arith] if isinstance(force_arith, str) else int(force_arith))
 
 
 SEXTON_WEINGARTEN = 2
@@ -384,6 +395,30 @@ class Lattice:
         st = SolveStats()
         check(lib().lgt_cg_solve(self.h, _ptr(b), _ptr(x), kappa, int(even_odd), C.byref(sp), C.byref(st)))
         return x, st.as_dict()
+
+    def cg_solve_multi(self, bs, kappas, sp=None, xs=None):
+        """Solve Dhat_k^+ Dhat_k x_k = b_k (even half fields) for several sources at once."""
+        sp = sp or solver()
+        n = len(bs)
+        if xs is None:
+            xs = [torch.zeros_like(b) for b in bs]
+        st = (SolveStats * n)()
+        check(lib().lgt_cg_solve_multi(self.h, n, (C.c_void_p * n)(*[b.data_ptr() for b in bs]),
+                                       (C.c_void_p * n)(*[x.data_ptr() for x in xs]),
+                                       (C.c_double * n)(*kappas), C.byref(sp), st))
+        return xs, [s.as_dict() for s in st]
+
+    def chrono_reset(self):
+        check(lib().lgt_chrono_reset(self.h))
+
+    def hop_multi(self, ins, out_parity, dagger=False, outs=None):
+        """out_k = H_{p,1-p} in_k for FP32 half fields, one link load for all of them."""
+        n = len(ins)
+        if outs is None:
+            outs = [self.spinor_field(out_parity, FP32) for _ in ins]
+        check(lib().lgt_hop_multi(self.h, n, (C.c_void_p * n)(*[t.data_ptr() for t in ins]),
+                                  (C.c_void_p * n)(*[t.data_ptr() for t in outs]), out_parity, int(dagger)))
+        return outs
 
     # ------------------------------------------------------------ actions and forces
     def action(self, ap, phi=None, sp=None):

@@ -54,3 +54,5 @@ def test_invalid_arguments_rejected_on_host(liblgt):
     assert liblgt.lgt_cg_solve(None, None, None, 0.1, 1, None, None) == 1
     st = lgt.SolveStats()
     assert liblgt.lgt_force(None, None, None, None, None, 0, C.byref(st)) == 1
+    assert liblgt.lgt_cg_solve_multi(None, 2, None, None, None, None, None) == 1
+    assert liblgt.lgt_hop_multi(None, 2, None, None, 0, 0) == 1

@@ -225,21 +225,22 @@ def test_total_force_link_level_error_cdf(lgt, ora):
 
 
 @pytest.mark.parametrize("eo", [False, True])
-@pytest.mark.parametrize("force_fp32", [False, True])
-def test_mixed_total_force(lgt, ora, eo, force_fp32):
-    """Mixed path: FP32 CG with FP64 reliable updates; FP64 force arithmetic (default)
-    or FP32 force arithmetic accumulated in FP64 (force_fp32).  Within 1e-6 of the
-    FP64 oracle (whole field and per link); the FP64-force path within 1e-7."""
+@pytest.mark.parametrize("arith", ["fp64", "fp32", "df64"])
+def test_mixed_total_force(lgt, ora, eo, arith):
+    """Mixed path: FP32 CG with FP64 reliable updates; force arithmetic FP64 (default),
+    FP32 accumulated in FP64, or double-float (FP32 pairs) accumulated in FP64.  Within
+    1e-6 of the FP64 oracle (whole field and per link); FP64 and double-float forces
+    within 1e-7, where the solver tolerance (1e-10) sets the error."""
     dims = (8, 6, 4, 10)
     U = synth.random_links(dims, 0.5, 27)
     phi = synth.gaussian_spinor(dims, 28, parity_mask=1 if eo else 3)
     lat = _lat(lgt, dims, U)
-    ap = lgt.action_params(beta=5.8, kappa=0.156, even_odd=eo, force_fp32=force_fp32)
+    ap = lgt.action_params(beta=5.8, kappa=0.156, even_odd=eo, force_arith=arith)
     pf = lat.pack_spinor(phi, lgt.EVEN if eo else lgt.FULL, lgt.FP64)
     F, st = lat.force(ap, pf, lgt.solver("mixed", tol=1e-10, delta=1e-4))
     Fo = ora.gauge_force(dims, U, 5.8) + ora.pf_force(dims, U, 0.156, phi, eo=eo, tol=1e-13)[0]
     Fg = _np(lat.unpack_momenta(F))
-    assert H.rel(Fg, Fo) < (1e-6 if force_fp32 else 1e-7)
+    assert H.rel(Fg, Fo) < (1e-6 if arith == "fp32" else 1e-7)
     eps = np.linalg.norm(Fg - Fo, axis=-1) / np.linalg.norm(Fo, axis=-1)
     assert np.quantile(eps, 0.999) < 1e-5
     # the kick applies exactly this force: mom - eps F
@@ -247,6 +248,40 @@ def test_mixed_total_force(lgt, ora, eo, force_fp32):
     m = lat.pack_momenta(mom)
     lat.md_update(m, 0.05, lgt.UPDATE_P, ap, pf, lgt.solver("mixed", tol=1e-10, delta=1e-4))
     assert H.rel(_np(lat.unpack_momenta(m)), mom - 0.05 * Fo) < 1e-6
+
+
+def test_double_float_gauge_force(lgt, ora):
+    """Double-float staple force (pure gauge, mixed solver selects the arithmetic):
+    about 48-bit products, within 1e-13 of the FP64 oracle, per link within 1e-12."""
+    dims = (8, 6, 4, 10)
+    U = synth.random_links(dims, 0.5, 31)
+    lat = _lat(lgt, dims, U)
+    ap = lgt.action_params(beta=5.8, fermions=False, force_arith="df64")
+    F, _ = lat.force(ap, None, lgt.solver("mixed", tol=1e-10))
+    Fo = ora.gauge_force(dims, U, 5.8)
+    Fg = _np(lat.unpack_momenta(F))
+    assert H.rel(Fg, Fo) < 1e-13
+    eps = np.linalg.norm(Fg - Fo, axis=-1) / np.linalg.norm(Fo, axis=-1)
+    assert eps.max() < 1e-12
+
+
+@pytest.mark.parametrize("eo", [False, True])
+def test_double_float_fermion_force(lgt, ora, eo):
+    """Double-float fermion force on the same mixed solve as the FP64 kernel: the two
+    differ only by the force arithmetic (within 1e-12); against the oracle the solver
+    tolerance (1e-12) sets the error."""
+    dims = (8, 6, 4, 10)
+    U = synth.random_links(dims, 0.5, 32)
+    phi = synth.gaussian_spinor(dims, 33, parity_mask=1 if eo else 3)
+    lat = _lat(lgt, dims, U)
+    pf = lat.pack_spinor(phi, lgt.EVEN if eo else lgt.FULL, lgt.FP64)
+    sp = lgt.solver("mixed", tol=1e-12, delta=1e-4)
+    F64, s64 = lat.force(lgt.action_params(kappa=0.156, even_odd=eo, force_arith="fp64"), pf, sp)
+    Fdf, sdf = lat.force(lgt.action_params(kappa=0.156, even_odd=eo, force_arith="df64"), pf, sp)
+    assert s64["iters"] == sdf["iters"]
+    assert H.rel(_np(lat.unpack_momenta(Fdf)), _np(lat.unpack_momenta(F64))) < 1e-12
+    Fo = ora.pf_force(dims, U, 0.156, phi, eo=eo, tol=1e-13)[0]
+    assert H.rel(_np(lat.unpack_momenta(Fdf)), Fo) < 1e-9
 
 
 # ------------------------------------------------------------------ molecular dynamics
@@ -308,20 +343,23 @@ def test_hmc_trajectory_matches_oracle(lgt, ora, integrator, eo):
 
 
 def test_hmc_mixed_vs_fp64_delta_h(lgt):
-    """Same start, same seeds: the mixed path (FP32 CG, FP64 reliable updates, FP64
-    forces) reproduces the FP64 path's Delta H within 1e-6 relative; FP32 force
-    arithmetic moves it by O(1e-4) and is only asked to stay within 1e-2."""
+    """Same start, same seeds: the mixed path (FP32 CG, FP64 reliable updates) with
+    FP64 or double-float force arithmetic reproduces the FP64 path's Delta H within
+    1e-6 relative; FP32 force arithmetic moves it by O(1e-4) and is only asked to
+    stay within 1e-2."""
     dims = (8, 8, 8, 8)
     lat = lgt.Lattice(dims)
     lat.random_links(4, 0.5)
     U0 = lat.get_links()
     dH = {}
-    for name, prec, f32 in (("fp64", "fp64", False), ("mixed", "mixed", False), ("mixed_f32", "mixed", True)):
+    for name, prec, arith in (("fp64", "fp64", "fp64"), ("mixed", "mixed", "fp64"),
+                              ("mixed_df64", "mixed", "df64"), ("mixed_f32", "mixed", "fp32")):
         lat.set_links(U0)
         sp = lgt.solver(prec, tol=1e-10, delta=1e-4)
-        ap = lgt.action_params(beta=5.8, kappa=0.156, even_odd=True, force_fp32=f32)
+        ap = lgt.action_params(beta=5.8, kappa=0.156, even_odd=True, force_arith=arith)
         dH[name] = lat.hmc_trajectory(ap, lgt.hmc_params("omelyan", 20, 1.0, sp, sp), 4, 0)["dH"]
     assert abs(dH["mixed"] - dH["fp64"]) <= 1e-6 * abs(dH["fp64"]) + 1e-9
+    assert abs(dH["mixed_df64"] - dH["fp64"]) <= 1e-6 * abs(dH["fp64"]) + 1e-9
     assert abs(dH["mixed_f32"] - dH["fp64"]) <= 1e-2 * abs(dH["fp64"]) + 1e-6
 
 

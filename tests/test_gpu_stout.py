@@ -149,3 +149,54 @@ def test_config3_16x4_finite_differences_and_memory(lgt, ora):
             assert abs(fd - F[s, mu, a]) < bound + 1e-7 * abs(F[s, mu, a]), (eps, s, mu, a, fd, F[s, mu, a])
     print(f"\n16^4 stout stack: stored {res[False][2] / 1e6:.0f} MB {res[False][3]:.3f} s; "
           f"recomputed {res[True][2] / 1e6:.0f} MB {res[True][3]:.3f} s")
+
+
+@pytest.mark.parametrize("n", [5, 7])
+def test_deep_chain_checkpoint_modes_bitwise(lgt, ora, n):
+    """Deep chains: every storage of the levels (all stored, recomputed from the thin
+    links, checkpoints every 2 / 3 / n levels) gives the same smeared links and the
+    same adjoint, bit for bit; the adjoint agrees with the oracle's."""
+    U = synth.random_links(DIMS, 0.5, 45)
+    G = synth.random_links(DIMS, 1.0, 46) + 0.5 * synth.random_links(DIMS, 1.0, 47)
+    lat = lgt.Lattice(DIMS)
+    lat.set_links(U)
+    top = {m: lat.stout_smear(0.1, n, recompute=m) for m in (0, 1, 2, 3, n)}
+    grad = {m: lat.stout_backward(0.1, n, G, recompute=m) for m in (0, 1, 2, 3, n)}
+    for m in (1, 2, 3, n):
+        assert torch.equal(top[m], top[0]), m
+        assert torch.equal(grad[m], grad[0]), m
+    levels = [U]
+    for _ in range(n):
+        levels.append(ora.stout_forward(DIMS, levels[-1], 0.1))
+    Gr = G
+    for k in range(n, 0, -1):
+        Gr = ora.stout_backward(DIMS, levels[k - 1], 0.1, Gr)
+    assert H.rel(_np(top[0]), levels[-1]) < 1e-13
+    assert H.rel(_np(grad[0]), Gr) < 1e-12
+
+
+def test_deep_chain_memory_and_force(lgt):
+    """Level fields held for a 12-level chain: all stored 12, checkpoints every 3 levels
+    3 + top + 2 segment fields, recomputed from the thin links 2 (measured against a
+    1-level chain, which holds one); the force through the chain is the same in every
+    mode, bit for bit."""
+    n = 12
+    U = synth.random_links(DIMS, 0.5, 48)
+    phi = synth.gaussian_spinor(DIMS, 49)
+    sp = lgt.solver("fp64", tol=1e-12)
+
+    def run(n_levels, m):
+        lat = lgt.Lattice(DIMS)
+        lat.set_links(U)
+        ap = lgt.action_params(beta=6.0, kappa=0.12, n_stout=n_levels, rho=0.05, stout_recompute=m)
+        F, _ = lat.force(ap, lat.pack_spinor(phi, lgt.FULL, lgt.FP64), sp)
+        return F, lat.info()[1]
+
+    _, ref = run(1, 0)
+    link_field = 4 * int(np.prod(DIMS)) * 9 * 16
+    forces, fields = {}, {}
+    for m in (0, 3, 1):
+        forces[m], b = run(n, m)
+        fields[m] = (b - ref) / link_field + 1
+    assert fields == {0: 12, 3: 6, 1: 2}
+    assert torch.equal(forces[3], forces[0]) and torch.equal(forces[1], forces[0])
