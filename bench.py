@@ -12,7 +12,7 @@ runs the CG in FP32 with FP64 reliable updates and the forces in double-float
 (FP32-pair) arithmetic accumulated in FP64; the FP64 path is FP64 throughout.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --kernel hop32|hop64 [--reps R]   # a few hop launches, for ncu
+    python bench.py --kernel hop32|hop64|force_df [--reps R]   # a few launches, for ncu
 
 Prints one JSON line (rank 0).  With torchrun each rank runs an independent
 replica (no collective in the data path; weak scaling).
@@ -60,8 +60,8 @@ HOP_FLOPS = 1320
 HOP_MIN_MS = 0.010
 # ncu DRAM traffic (read + write) of one FP32 hop launch at 32^3 x 64, and the hash of
 # the kernel sources it was taken from (traffic is reported as null once they change)
-NCU_TRAFFIC = {"bytes": 594124544,
-               "sources_sha256": "536d9e3e5c675235ac377096557add97b640d649c97d784a4a95517511f14c6f"}
+NCU_TRAFFIC = {"bytes": 593333504,
+               "sources_sha256": "48794f32001d51140ab466607ef3c791e19e36b88dd6813be7191e879aa9f9f6"}
 HOP_SOURCES = ["paper_2602_20516_b300/csrc/lgt_dirac.cu", "paper_2602_20516_b300/csrc/lgt_spin.cuh",
                "paper_2602_20516_b300/csrc/lgt_common.cuh"]
 
@@ -519,6 +519,15 @@ def run_kernel(args):
     from paper_2602_20516_b300 import lgt
     lat = lgt.Lattice(DIMS)
     lat.random_links(SEED, ALPHA)
+    if args.kernel == "force_df":
+        # one mixed-precision force evaluation with double-float force arithmetic
+        phi = lat.gaussian_spinor(SEED, 0, lgt.FIELD_SOURCE, lgt.EVEN)
+        ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith="df64")
+        for _ in range(args.reps):
+            lat.force(ap, phi, lgt.solver("mixed", tol=TOL, delta=DELTA))
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": args.kernel, "force_evals": args.reps, "lattice": list(DIMS)}))
+        return
     prec = lgt.FP32 if args.kernel == "hop32" else lgt.FP64
     src = lat.pack_spinor(lat.unpack_spinor(lat.gaussian_spinor(SEED, 0, lgt.FIELD_SOURCE, lgt.ODD),
                                             lgt.ODD, lgt.FP64), lgt.ODD, prec)
@@ -546,7 +555,7 @@ def main():
     ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")
     ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
     ap.add_argument("--hmc-fp64", type=int, default=2, help="trajectories replayed on the FP64 path")
-    ap.add_argument("--kernel", choices=["hop32", "hop64"])
+    ap.add_argument("--kernel", choices=["hop32", "hop64", "force_df"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "ours" and not args.kernel:
