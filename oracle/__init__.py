@@ -35,7 +35,8 @@ class HMCParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("eo", C.c_int),
                 ("fermions", C.c_int), ("integrator", C.c_int), ("n_steps", C.c_int),
                 ("tau", C.c_double), ("tol_md", C.c_double), ("tol_action", C.c_double),
-                ("max_iter", C.c_int), ("n_inner", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double)]
+                ("max_iter", C.c_int), ("n_inner", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double),
+                ("c1", C.c_double)]
 
 
 class HMCResult(C.Structure):
@@ -70,6 +71,10 @@ def lib():
             "ora_cg": (C.c_int, [_ip, _cp, C.c_double, C.c_int, _cp, _cp, C.c_double, C.c_int, C.POINTER(C.c_double)]),
             "ora_plaquette_sum": (C.c_double, [_ip, _cp]),
             "ora_gauge_action": (C.c_double, [_ip, _cp, C.c_double]),
+            "ora_gauge_action_imp": (C.c_double, [_ip, _cp, C.c_double, C.c_double]),
+            "ora_rectangle_sum": (C.c_double, [_ip, _cp]),
+            "ora_gauge_force_imp": (None, [_ip, _cp, C.c_double, C.c_double, C.c_double, _dp]),
+            "ora_gauge_action_grad_imp": (None, [_ip, _cp, C.c_double, C.c_double, _cp]),
             "ora_pf_action": (C.c_double, [_ip, _cp, C.c_double, C.c_int, _cp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
             "ora_momentum_energy": (C.c_double, [_ip, _dp]),
             "ora_gauge_force": (None, [_ip, _cp, C.c_double, C.c_double, _dp]),
@@ -212,8 +217,16 @@ def plaquette(dims, U):
     return plaquette_sum(dims, U) / (6.0 * volume(dims))
 
 
-def gauge_action(dims, U, beta):
-    return lib().ora_gauge_action(_dims(dims), _c(U), beta)
+def gauge_action(dims, U, beta, c1=0.0):
+    """beta sum [c0 (1 - Re tr P / 3) + c1 (1 - Re tr R / 3)], c0 = 1 - 8 c1 (c1 = 0: Wilson)."""
+    if c1 == 0.0:
+        return lib().ora_gauge_action(_dims(dims), _c(U), beta)
+    return lib().ora_gauge_action_imp(_dims(dims), _c(U), beta, c1)
+
+
+def rectangle_sum(dims, U):
+    """sum over x and ordered mu != nu of Re tr R_munu(x) / 3 (2 x 1 loops, long side mu)."""
+    return lib().ora_rectangle_sum(_dims(dims), _c(U))
 
 
 def pf_action(dims, U, kappa, phi, eo=False, tol=1e-12, max_iter=10000):
@@ -227,10 +240,13 @@ def momentum_energy(dims, mom):
 
 
 # ---------------------------------------------------------------- forces
-def gauge_force(dims, U, beta):
+def gauge_force(dims, U, beta, c1=0.0):
     d = _dims(dims)
     F = np.zeros((volume(d), 4, 8))
-    lib().ora_gauge_force(d, _c(U), beta, 1.0, F)
+    if c1 == 0.0:
+        lib().ora_gauge_force(d, _c(U), beta, 1.0, F)
+    else:
+        lib().ora_gauge_force_imp(d, _c(U), beta, c1, 1.0, F)
     return F
 
 
@@ -255,10 +271,13 @@ def grad_to_force(dims, U, G):
     return F
 
 
-def gauge_action_grad(dims, U, beta):
+def gauge_action_grad(dims, U, beta, c1=0.0):
     d = _dims(dims)
     G = np.zeros((volume(d), 4, 3, 3), np.complex128)
-    lib().ora_gauge_action_grad(d, _c(U), beta, G)
+    if c1 == 0.0:
+        lib().ora_gauge_action_grad(d, _c(U), beta, G)
+    else:
+        lib().ora_gauge_action_grad_imp(d, _c(U), beta, c1, G)
     return G
 
 
@@ -301,9 +320,9 @@ INTEGRATORS = {"leapfrog": 0, "omelyan": 1, "sexton_weingarten": 2}
 
 
 def hmc_params(beta, kappa, eo=False, fermions=True, integrator="leapfrog", n_steps=10,
-               tau=1.0, tol_md=1e-12, tol_action=1e-12, max_iter=10000, n_inner=1, n_stout=0, rho=0.0):
+               tau=1.0, tol_md=1e-12, tol_action=1e-12, max_iter=10000, n_inner=1, n_stout=0, rho=0.0, c1=0.0):
     return HMCParams(beta, kappa, int(eo), int(fermions), INTEGRATORS[integrator], n_steps, tau, tol_md,
-                     tol_action, max_iter, n_inner, n_stout, rho)
+                     tol_action, max_iter, n_inner, n_stout, rho, c1)
 
 
 def md_force(dims, U, params, phi, part=0):

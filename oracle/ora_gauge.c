@@ -122,6 +122,122 @@ void ora_gauge_action_grad(const int d[4], const ocplx *U, double beta, ocplx *G
         }
 }
 
+/* ---------------- rectangle-improved gauge action ----------------
+ * S_G = beta sum_x [ c0 sum_{mu<nu} (1 - Re tr P_munu(x)/3) + c1 sum_{mu!=nu} (1 - Re tr R_munu(x)/3) ],
+ * c0 = 1 - 8 c1, R_munu the 2 x 1 loop with the long side along mu.  Loops are
+ * written as step lists: +(mu+1) steps forward along mu with U_mu(y), -(mu+1) steps
+ * back with U_mu(y-mu)^+.  The force on U_mu(x) uses every loop through that link
+ * rotated to start with it: Re tr(U_mu(x) S), S the product along the rest. */
+static void path_product(const int d[4], const ocplx *U, long y, const int *steps, int n, ocplx out[9])
+{
+    ocplx acc[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, t[9], m[9];
+    for (int k = 0; k < n; ++k) {
+        const int mu = abs(steps[k]) - 1;
+        if (steps[k] > 0) {
+            su3_mul(acc, link_at(U, y, mu), t);
+            y = ora_neighbour(d, y, mu, +1);
+        } else {
+            y = ora_neighbour(d, y, mu, -1);
+            su3_dag(link_at(U, y, mu), m);
+            su3_mul(acc, m, t);
+        }
+        memcpy(acc, t, sizeof acc);
+    }
+    memcpy(out, acc, sizeof acc);
+}
+
+double ora_rectangle_sum(const int d[4], const ocplx *U)
+{
+    long V = ora_volume(d);
+    double *site = malloc(V * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < V; ++x) {
+        double acc = 0;
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = 0; nu < 4; ++nu) {
+                if (nu == mu) continue;
+                const int m = mu + 1, n = nu + 1;
+                const int loop[6] = {m, m, n, -m, -m, -n};
+                ocplx R[9];
+                path_product(d, U, x, loop, 6, R);
+                acc += retrace(R) / 3.0;
+            }
+        site[x] = acc;
+    }
+    double sum = 0;
+    for (long x = 0; x < V; ++x) sum += site[x];
+    free(site);
+    return sum;
+}
+
+double ora_gauge_action_imp(const int d[4], const ocplx *U, double beta, double c1)
+{
+    if (c1 == 0.0) return ora_gauge_action(d, U, beta);
+    const double V = (double)ora_volume(d);
+    return beta * ((1.0 - 8.0 * c1) * (6.0 * V - ora_plaquette_sum(d, U)) +
+                   c1 * (12.0 * V - ora_rectangle_sum(d, U)));
+}
+
+/* c0 (plaquette staples) + c1 (rectangle staples) through U_mu(x) */
+static void staple_imp(const int d[4], const ocplx *U, long x, int mu, double c1, ocplx Vs[9])
+{
+    staple(d, U, x, mu, Vs);
+    if (c1 == 0.0) return;
+    const double c0 = 1.0 - 8.0 * c1;
+    for (int i = 0; i < 9; ++i) Vs[i] *= c0;
+    const long xp = ora_neighbour(d, x, mu, +1);
+    const int m = mu + 1;
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        const int n = nu + 1;
+        /* the six rectangles through U_mu(x), each starting with the step +mu from x */
+        const int loops[6][6] = {
+            {m, m, n, -m, -m, -n},  {m, n, -m, -m, -n, m},   /* long side mu, above */
+            {m, m, -n, -m, -m, n},  {m, -n, -m, -m, n, m},   /* long side mu, below */
+            {m, n, n, -m, -n, -n},  {m, -n, -n, -m, n, n},   /* long side nu */
+        };
+        for (int k = 0; k < 6; ++k) {
+            ocplx S[9];
+            path_product(d, U, xp, loops[k] + 1, 5, S);
+            for (int i = 0; i < 9; ++i) Vs[i] += c1 * S[i];
+        }
+    }
+}
+
+void ora_gauge_force_imp(const int d[4], const ocplx *U, double beta, double c1, double coef, double *F)
+{
+    if (c1 == 0.0) { ora_gauge_force(d, U, beta, coef, F); return; }
+    long V = ora_volume(d);
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < V; ++x)
+        for (int mu = 0; mu < 4; ++mu) {
+            ocplx Vs[9], UV[9], T[9];
+            staple_imp(d, U, x, mu, c1, Vs);
+            su3_mul(link_at(U, x, mu), Vs, UV);
+            for (int a = 0; a < 8; ++a) {
+                ora_gellmann_T(a, T);
+                ocplx tr = 0;
+                for (int i = 0; i < 3; ++i)
+                    for (int k = 0; k < 3; ++k) tr += T[i * 3 + k] * UV[k * 3 + i];
+                F[(x * 4 + mu) * 8 + a] += coef * (beta / 3.0) * cimag(tr);
+            }
+        }
+}
+
+void ora_gauge_action_grad_imp(const int d[4], const ocplx *U, double beta, double c1, ocplx *G)
+{
+    if (c1 == 0.0) { ora_gauge_action_grad(d, U, beta, G); return; }
+    long V = ora_volume(d);
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < V; ++x)
+        for (int mu = 0; mu < 4; ++mu) {
+            ocplx Vs[9], Vd[9];
+            staple_imp(d, U, x, mu, c1, Vs);
+            su3_dag(Vs, Vd);
+            for (int i = 0; i < 9; ++i) G[(x * 4 + mu) * 9 + i] = -(beta / 3.0) * Vd[i];
+        }
+}
+
 void ora_update_links(const int d[4], ocplx *U, const double *mom, double eps)
 {
     long V = ora_volume(d);

@@ -37,7 +37,7 @@ int ora_md_force_part(const int d[4], const ocplx *U, const ora_hmc_params *p, c
 {
     long V = ora_volume(d);
     memset(F, 0, V * 32 * sizeof(double));
-    if (part != 2 && p->beta != 0.0) ora_gauge_force(d, U, p->beta, 1.0, F);
+    if (part != 2 && p->beta != 0.0) ora_gauge_force_imp(d, U, p->beta, p->c1, 1.0, F);
     if (part == 1 || !p->fermions) return 0;
     int it;
     if (p->n_stout == 0) {
@@ -80,7 +80,7 @@ double ora_hamiltonian(const int d[4], const ocplx *U, const double *mom, const 
                        const ora_hmc_params *p)
 {
     int it;
-    double H = ora_momentum_energy(d, mom) + ora_gauge_action(d, U, p->beta);
+    double H = ora_momentum_energy(d, mom) + ora_gauge_action_imp(d, U, p->beta, p->c1);
     if (p->fermions) H += pf_action_smeared(d, U, p, phi, &it);
     return H;
 }
@@ -156,7 +156,7 @@ int ora_hmc_trajectory(const int d[4], ocplx *U, const ora_hmc_params *p, uint64
 
     ora_gaussian_momenta(d, seed, traj, mom);
     res->K_old = ora_momentum_energy(d, mom);
-    res->Sg_old = ora_gauge_action(d, U, p->beta);
+    res->Sg_old = ora_gauge_action_imp(d, U, p->beta, p->c1);
     if (p->fermions) {
         int mask = p->eo ? 1 : 3;
         ora_gaussian_spinor(d, seed, traj, ORA_FIELD_XI, mask, xi);
@@ -171,7 +171,7 @@ int ora_hmc_trajectory(const int d[4], ocplx *U, const ora_hmc_params *p, uint64
     res->cg_iters = integrate(d, U, mom, phi, p, &evals);
     res->force_evals = evals;
     res->K_new = ora_momentum_energy(d, mom);
-    res->Sg_new = ora_gauge_action(d, U, p->beta);
+    res->Sg_new = ora_gauge_action_imp(d, U, p->beta, p->c1);
     if (p->fermions) {
         int it = 0;
         res->Sf_new = pf_action_smeared(d, U, p, phi, &it);

@@ -108,6 +108,13 @@ void ora_gauge_action_grad(const int d[4], const ocplx *U, double beta, ocplx *G
 int ora_pf_action_grad(const int d[4], const ocplx *U, double kappa, int eo,
                        const ocplx *phi, double tol, int max_iter, ocplx *G);
 
+/* rectangle-improved gauge action (c0 = 1 - 8 c1; c1 = 0 is the Wilson action):
+ * S_G = beta sum_x [c0 sum_{mu<nu}(1 - Re tr P/3) + c1 sum_{mu!=nu}(1 - Re tr R/3)] */
+double ora_rectangle_sum(const int d[4], const ocplx *U);   /* sum_{x,mu!=nu} Re tr R_munu / 3 */
+double ora_gauge_action_imp(const int d[4], const ocplx *U, double beta, double c1);
+void ora_gauge_force_imp(const int d[4], const ocplx *U, double beta, double c1, double coef, double *F);
+void ora_gauge_action_grad_imp(const int d[4], const ocplx *U, double beta, double c1, ocplx *G);
+
 /* ---------------- link update ---------------- */
 /* U <- exp(i eps Pi) U for every link (Eq. S2.1), Pi = sum_a mom_a T^a */
 void ora_update_links(const int d[4], ocplx *U, const double *mom, double eps);
@@ -137,6 +144,7 @@ typedef struct {
     int n_inner;         /* Sexton-Weingarten: gauge-force steps per outer step */
     int n_stout;         /* stout levels in front of the Wilson operator (S_G: thin links) */
     double rho;
+    double c1;           /* rectangle coefficient of the gauge action (0: Wilson) */
 } ora_hmc_params;
 
 /* parts of the MD force: 0 all, 1 gauge only, 2 fermion only */

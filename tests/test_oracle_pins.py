@@ -366,3 +366,70 @@ def test_stout_backward_finite_difference(ora):
                 Um = U.copy(); Um[s, mu, i, j] -= h * unit
                 fd = (L(Up) - L(Um)) / (2 * h)
                 assert abs(fd - part(G[s, mu, i, j])) < 2e-8 * max(1, abs(fd))
+
+
+# ------------------------------------------------------------------ rectangle-improved gauge action
+IWASAKI = -0.331
+
+
+def test_improved_action_closed_form_abelian_field(ora):
+    """U_1(x) = exp(i phi x_0 H), H = diag(1, -1, 0), phi = 2 pi / L_0, other links 1:
+    every (0,1) plaquette is exp(i phi H) and both (0,1) rectangles exp(+-2 i phi H),
+    all other loops are 1, so sum Re tr P / 3 = V (5 + (1 + 2 cos phi) / 3) and
+    sum Re tr R / 3 = V (10 + 2 (1 + 2 cos 2 phi) / 3)."""
+    d = (6, 4, 4, 4)
+    V = int(np.prod(d))
+    phi = 2 * np.pi / d[0]
+    x0 = synth.coords(d)[:, 0]
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (V, 4, 3, 3)).copy()
+    for s in range(V):
+        U[s, 1] = np.diag(np.exp(1j * phi * x0[s] * np.array([1.0, -1.0, 0.0])))
+    P = V * (5 + (1 + 2 * np.cos(phi)) / 3)
+    R = V * (10 + 2 * (1 + 2 * np.cos(2 * phi)) / 3)
+    assert abs(ora.plaquette_sum(d, U) - P) < 1e-11 * P
+    assert abs(ora.rectangle_sum(d, U) - R) < 1e-11 * R
+    beta = 2.5
+    for c1 in (-1.0 / 12, IWASAKI, -1.4088):
+        want = beta * ((1 - 8 * c1) * (6 * V - P) + c1 * (12 * V - R))
+        assert abs(ora.gauge_action(d, U, beta, c1) - want) < 1e-10 * abs(want)
+
+
+def test_improved_action_invariance_and_unit_field(ora):
+    d = (4, 4, 4, 6)
+    V = int(np.prod(d))
+    U = synth.random_links(d, 0.5, 81)
+    g = synth.random_su3(V, 82)
+    Ug = H.gauge_transform_links(d, U, g)
+    S = ora.gauge_action(d, U, 2.5, IWASAKI)
+    assert abs(S - ora.gauge_action(d, Ug, 2.5, IWASAKI)) < 1e-12 * abs(S)
+    one = np.broadcast_to(np.eye(3), (V, 4, 3, 3)).copy()
+    assert ora.gauge_action(d, one, 2.5, IWASAKI) == 0.0
+    # the rectangle term is not the plaquette term: the two sums differ on a random field
+    assert abs(ora.rectangle_sum(d, U) / (12 * V) - ora.plaquette_sum(d, U) / (6 * V)) > 1e-2
+
+
+def test_improved_force_and_gradient_finite_difference(ora):
+    """Lie force (central differences in Lie directions) and real-component gradient
+    (central differences on matrix entries) of the Iwasaki action, including links
+    whose rectangles wrap around the lattice."""
+    d = (4, 4, 4, 6)
+    U = synth.random_links(d, 0.5, 83)
+    beta = 2.5
+    F = ora.gauge_force(d, U, beta, IWASAKI)
+    G = ora.gauge_action_grad(d, U, beta, IWASAKI)
+    h = 1e-5
+    for (s, mu) in [(0, 0), (37, 1), (100, 2), (383, 3), (3, 3)]:
+        for a in (0, 4, 7):
+            Sp = ora.gauge_action(d, H.lie_perturb(U, s, mu, a, h), beta, IWASAKI)
+            Sm = ora.gauge_action(d, H.lie_perturb(U, s, mu, a, -h), beta, IWASAKI)
+            fd = (Sp - Sm) / (2 * h)
+            assert abs(fd - F[s, mu, a]) < 2e-6 * max(1.0, abs(F[s, mu, a]))
+    for (s, mu) in [(5, 1), (200, 3)]:
+        for (i, j) in ((0, 0), (1, 2)):
+            for unit, part in ((1.0, "re"), (1j, "im")):
+                Up = U.copy(); Up[s, mu, i, j] += h * unit
+                Um = U.copy(); Um[s, mu, i, j] -= h * unit
+                fd = (ora.gauge_action(d, Up, beta, IWASAKI) - ora.gauge_action(d, Um, beta, IWASAKI)) / (2 * h)
+                ga = G[s, mu, i, j].real if part == "re" else G[s, mu, i, j].imag
+                assert abs(fd - ga) < 2e-6 * max(1.0, abs(ga))
+    assert H.rel(ora.grad_to_force(d, U, G), F) < 1e-13
