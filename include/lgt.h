@@ -19,7 +19,8 @@
  *     b = -1 on hops that wrap in time (antiperiodic fermions), chiral gammas
  *     g_k = [[0,-i s_k],[i s_k,0]] (mu = k-1 < 3), g_4 = [[0,1],[1,0]] (mu = 3).
  *   - Even-odd: Dhat = 1 - kappa^2 H_eo H_oe on even sites, Dhat^+ = g5 Dhat g5.
- *   - S_G = beta sum_{x, mu<nu} (1 - Re tr U_munu(x) / 3).
+ *   - S_G = beta sum_{x, mu<nu} (1 - Re tr U_munu(x) / 3), plus the rectangle term of
+ *     the improved actions when lgt_action_params.c1 != 0.
  *   - a real-component gradient ("G form", Eq. S2.11) is dS/dReU + i dS/dImU.
  *
  * Device layouts (all buffers below are DEVICE pointers owned by the caller;
@@ -112,6 +113,12 @@ typedef struct {
                               moves an MD trajectory's Delta H by ~1e-4);
                             LGT_ARITH_DF64 double-float: products carried as pairs of FP32
                               numbers (about 48 bits, ~1e-13 relative), accumulated in FP64 */
+    double c1;           /* rectangle weight of the gauge action (not printed in the paper; an
+                            improved discretisation of Sec. IV): S_G = beta sum_x [c0 sum_{mu<nu}
+                            (1 - Re tr P/3) + c1 sum_{mu!=nu} (1 - Re tr R/3)], c0 = 1 - 8 c1,
+                            R the 2 x 1 loop with its long side along mu.  0: Wilson action;
+                            -1/12 tree-level Symanzik, -0.331 Iwasaki, -1.4088 DBW2.  With
+                            c1 != 0 the LGT_ARITH_DF64 gauge force uses FP64 arithmetic. */
 } lgt_action_params;
 
 typedef struct {
@@ -187,6 +194,9 @@ int lgt_random_links(lgt_lattice_t lat, uint64_t seed, double alpha);
 int lgt_reunitarise(lgt_lattice_t lat);
 /* <P> = sum_{x,mu<nu} Re tr U_munu / (3 * 6 V) (host result). */
 int lgt_plaquette(lgt_lattice_t lat, double *plaq);
+/* <R> = sum_{x,mu!=nu} Re tr R_munu / (3 * 12 V), R the 2 x 1 rectangle with its long
+ * side along mu (host result). */
+int lgt_rectangle(lgt_lattice_t lat, double *rect);
 
 /* Mean plaquette, as lgt_plaquette, of a canonical link field (device,
  * complex128 [V][4][3][3], extents dims[0..3], all even) without allocating any

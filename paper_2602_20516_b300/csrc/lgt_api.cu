@@ -436,6 +436,33 @@ static int plaquette_sum(lgt_lattice* L, const double2* U, double* out) {
     *out = L->hs->slot[0];
     return LGT_OK;
 }
+static int rectangle_sum(lgt_lattice* L, const double2* U, double* out) {
+    CK(gauge_rectangles(U, L->g, red(L), 0, L->st));
+    TRY(sync_scalars(L));
+    *out = L->hs->slot[0];
+    return LGT_OK;
+}
+// S_G = beta [c0 (6V - sum Re tr P / 3) + c1 (12V - sum Re tr R / 3)], c0 = 1 - 8 c1
+static int gauge_action_value(lgt_lattice* L, const lgt_action_params* ap, double* S) {
+    double ps;
+    TRY(plaquette_sum(L, L->thin.U, &ps));
+    if (ap->c1 == 0.0) {
+        *S = ap->beta * (6.0 * L->g.V - ps);
+        return LGT_OK;
+    }
+    double rs;
+    TRY(rectangle_sum(L, L->thin.U, &rs));
+    *S = ap->beta * ((1.0 - 8.0 * ap->c1) * (6.0 * L->g.V - ps) + ap->c1 * (12.0 * L->g.V - rs));
+    return LGT_OK;
+}
+extern "C" int lgt_rectangle(lgt_lattice_t L, double* rect) {
+    if (!L || !rect) return fail(LGT_EINVAL, "null argument");
+    double s;
+    TRY(rectangle_sum(L, L->thin.U, &s));
+    *rect = s / (12.0 * L->g.V);
+    return LGT_OK;
+}
+
 extern "C" int lgt_plaquette(lgt_lattice_t L, double* plaq) {
     if (!L || !plaq) return fail(LGT_EINVAL, "null argument");
     double s;
@@ -1085,8 +1112,8 @@ extern "C" int lgt_action(lgt_lattice_t L, const lgt_action_params* ap, const do
     if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
     if (S_g) {
         double s;
-        TRY(plaquette_sum(L, L->thin.U, &s));
-        *S_g = ap->beta * (6.0 * L->g.V - s);
+        TRY(gauge_action_value(L, ap, &s));
+        *S_g = s;
     }
     if (S_f) {
         *S_f = 0.0;
@@ -1166,17 +1193,18 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
         TRY(force_vectors(L, ferm_lk, ap, phi, sp, stats, fp32));
     }
     if (ap->beta != 0.0) {
-        if (fp32) CK(gauge_force_fp32(gauge_lk.U12, L->g, ap->beta, coef, keep, out, L->st));
-        else if (dfa) {
+        if (fp32) CK(gauge_force_fp32(gauge_lk.U12, L->g, ap->beta, ap->c1, coef, keep, out, L->st));
+        else if (dfa && ap->c1 == 0.0) {
             CK(links_to_df(L->Udf, gauge_lk.U, L->g, L->st));
             CK(gauge_force_df(L->Udf, L->g, ap->beta, coef, keep, out, L->st));
-        } else CK(gauge_force(gauge_lk.U, L->g, ap->beta, coef, keep, form, out, L->st));
+        } else CK(gauge_force(gauge_lk.U, L->g, ap->beta, ap->c1, coef, keep, form, out, L->st));
         keep = 1;
     }
     if (ap->fermions) {
         if (fp32) CK(fermion_force_fp32(ferm_lk.U12, L->X32, L->Y32, L->g, ap->kappa, coef, keep, out, L->st));
         else if (dfa) {
-            if (ap->beta == 0.0 || ferm_lk.U != gauge_lk.U) CK(links_to_df(L->Udf, ferm_lk.U, L->g, L->st));
+            if (ap->beta == 0.0 || ap->c1 != 0.0 || ferm_lk.U != gauge_lk.U)
+                CK(links_to_df(L->Udf, ferm_lk.U, L->g, L->st));
             CK(spinor_to_df(L->Xdf, L->X, L->g, L->st));
             CK(spinor_to_df(L->Ydf, L->Y, L->g, L->st));
             CK(fermion_force_df(L->Udf, L->Xdf, L->Ydf, L->g, ap->kappa, coef, keep, out, L->st));
@@ -1254,7 +1282,7 @@ static int force_grad_stout(lgt_lattice* L, const lgt_action_params* ap, const d
         CK(cudaMemsetAsync(ga, 0, links64(L), L->st));
     }
     TRY(stout_chain(L, ap, G));
-    if (ap->beta != 0.0) CK(gauge_force(L->thin.U, L->g, ap->beta, 1.0, 1, 1, G, L->st));
+    if (ap->beta != 0.0) CK(gauge_force(L->thin.U, L->g, ap->beta, ap->c1, 1.0, 1, 1, G, L->st));
     return LGT_OK;
 }
 
@@ -1435,8 +1463,7 @@ extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, 
     CK(gauge_momenta_heatbath(L->mom, L->g, seed, traj, L->st));
     TRY(lgt_kinetic_energy(L, (const double*)L->mom, &res->K_old));
     double ps;
-    TRY(plaquette_sum(L, L->thin.U, &ps));
-    res->Sg_old = ap->beta * (6.0 * L->g.V - ps);
+    TRY(gauge_action_value(L, ap, &res->Sg_old));
     if (ap->fermions) {
         // phi = M^+ xi on the (smeared) links, S_f(old) = xi^+ xi
         CK(cudaMemsetAsync(L->xi, 0, spinor64_full(L), L->st));
@@ -1453,8 +1480,7 @@ extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, 
     TRY(integrate(L, ap, hp, L->phi, &res->total, &evals));
     res->force_evals = evals;
     TRY(lgt_kinetic_energy(L, (const double*)L->mom, &res->K_new));
-    TRY(plaquette_sum(L, L->thin.U, &ps));
-    res->Sg_new = ap->beta * (6.0 * L->g.V - ps);
+    TRY(gauge_action_value(L, ap, &res->Sg_new));
     if (ap->fermions) {
         Links lk;
         TRY(fermion_links(L, ap, &lk));

@@ -3,6 +3,8 @@
 // plaquette action, the staple force (Eq. 9 applied to S_G), the left link
 // update of Eq. S2.1 and the momentum heatbath / kinetic energy.
 //
+// The staple force and action also take the rectangle term of the improved
+// gauge actions (weight c1, plaquette weight c0 = 1 - 8 c1).
 // Link kernels run one thread per link with the site index fastest, so the
 // SoA loads of a warp are contiguous.  The FP64 staple force and the exponential
 // are FP64-ALU bound on this part; they are written for FMA throughput.
@@ -185,16 +187,73 @@ __device__ __forceinline__ mat3<R> staple_sum(const void* U, const Geom& g, cons
     return V;
 }
 
+// ---------------------------------------------------------------- rectangle staples
+// The rectangle-improved action adds c1 sum_{x, mu != nu} (1 - Re tr R_munu(x) / 3),
+// R_munu the 2 x 1 loop with its long side along mu (plaquette weight c0 = 1 - 8 c1).
+// The six rectangles per nu through U_mu(x), each walked from x + mu after the step
+// along U_mu(x): a step +d moves along U_d(y), a step -d moves back with U_d(y-d)^+.
+__constant__ signed char RECT_WALKS[6][5] = {
+    {'m', 'n', 'M', 'M', 'N'},   // long side mu above, U_mu(x) first
+    {'n', 'M', 'M', 'N', 'm'},   // long side mu above, U_mu(x) second
+    {'m', 'N', 'M', 'M', 'n'},   // long side mu below, U_mu(x) first
+    {'N', 'M', 'M', 'n', 'm'},   // long side mu below, U_mu(x) second
+    {'n', 'n', 'M', 'N', 'N'},   // long side nu, above
+    {'N', 'N', 'M', 'n', 'n'},   // long side nu, below
+};
+template <typename R>
+__device__ __forceinline__ mat3<R> walk5(const void* U, const Geom& g, const int x0[4], int mu, int nu,
+                                         const signed char* w) {
+    int y[4] = {x0[0], x0[1], x0[2], x0[3]};
+    shift(g, y, mu, +1);
+    mat3<R> acc;
+#pragma unroll 1
+    for (int k = 0; k < 5; ++k) {
+        const char c = w[k];
+        const int d = (c == 'm' || c == 'M') ? mu : nu;
+        mat3<R> L;
+        if (c == 'm' || c == 'n') {
+            L = GLink<R>::at(U, g, y, d);
+            shift(g, y, d, +1);
+            acc = (k == 0) ? L : mul(acc, L);
+        } else {
+            shift(g, y, d, -1);
+            L = GLink<R>::at(U, g, y, d);
+            acc = (k == 0) ? dag(L) : mul_nd(acc, L);
+        }
+    }
+    return acc;
+}
+// V_mu(x) = c0 (plaquette staples) + c1 (rectangle staples)
+template <typename R>
+__device__ __forceinline__ mat3<R> staple_sum_imp(const void* U, const Geom& g, const int x[4], int mu, double c1) {
+    mat3<R> V = staple_sum<R>(U, g, x, mu);
+    if (c1 == 0.0) return V;
+    const R c0 = (R)(1.0 - 8.0 * c1), r1 = (R)c1;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) V.e[a][b] = c0 * V.e[a][b];
+#pragma unroll 1
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+#pragma unroll 1
+        for (int k = 0; k < 6; ++k) {
+            const mat3<R> S = walk5<R>(U, g, x, mu, nu, RECT_WALKS[k]);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) V.e[a][b] = V.e[a][b] + r1 * S.e[a][b];
+        }
+    }
+    return V;
+}
+
 // Lie form: out = keep*out + coef*(beta/6) Im tr(lambda^a U V), accumulated in FP64
 // whatever the arithmetic precision R of the staples.
 template <typename R>
-__global__ void __launch_bounds__(NT) gauge_force_lie_kernel(const void* U, Geom g, double beta, double coef,
-                                                             int keep, double2* out) {
+__global__ void __launch_bounds__(NT) gauge_force_lie_kernel(const void* U, Geom g, double beta, double c1,
+                                                             double coef, int keep, double2* out) {
     int mu, p, i;
     if (!link_index(g, mu, p, i)) return;
     int x[4];
     eo_coords(g, p, i, x);
-    mat3<R> V = staple_sum<R>(U, g, x, mu);
+    mat3<R> V = staple_sum_imp<R>(U, g, x, mu, c1);
     mat3<R> M = mul(GLink<R>::at(U, g, x, mu), V);
     R c[8];
     lie_im_tr(M, c);
@@ -206,13 +265,13 @@ __global__ void __launch_bounds__(NT) gauge_force_lie_kernel(const void* U, Geom
 }
 
 template <int FORM>
-__global__ void __launch_bounds__(NT) gauge_force_kernel(const double2* U, Geom g, double beta, double coef,
-                                                         int keep, double2* out) {
+__global__ void __launch_bounds__(NT) gauge_force_kernel(const double2* U, Geom g, double beta, double c1,
+                                                         double coef, int keep, double2* out) {
     int mu, p, i;
     if (!link_index(g, mu, p, i)) return;
     int x[4];
     eo_coords(g, p, i, x);
-    dmat V = staple_sum<double>(U, g, x, mu);
+    dmat V = staple_sum_imp<double>(U, g, x, mu, c1);
     if (FORM == 0) {
         dmat M = mul(load_link(U, g.Vh, p, mu, i), V);
         double c[8];
@@ -234,16 +293,52 @@ __global__ void __launch_bounds__(NT) gauge_force_kernel(const double2* U, Geom 
         store_link(out, g.Vh, p, mu, i, G);
     }
 }
-cudaError_t gauge_force(const double2* U, const Geom& g, double beta, double coef, int keep, int form,
+cudaError_t gauge_force(const double2* U, const Geom& g, double beta, double c1, double coef, int keep, int form,
                         double2* out, cudaStream_t st) {
-    if (form == 0) gauge_force_kernel<0><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, g, beta, coef, keep, out);
-    else gauge_force_kernel<1><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, g, beta, coef, keep, out);
+    if (form == 0) gauge_force_kernel<0><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, g, beta, c1, coef, keep, out);
+    else gauge_force_kernel<1><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, g, beta, c1, coef, keep, out);
     count_launch();
     return cudaGetLastError();
 }
-cudaError_t gauge_force_fp32(const float4* U12, const Geom& g, double beta, double coef, int keep, double2* out,
-                             cudaStream_t st) {
-    gauge_force_lie_kernel<float><<<grid_for(8L * g.Vh), NT, 0, st>>>(U12, g, beta, coef, keep, out);
+cudaError_t gauge_force_fp32(const float4* U12, const Geom& g, double beta, double c1, double coef, int keep,
+                             double2* out, cudaStream_t st) {
+    gauge_force_lie_kernel<float><<<grid_for(8L * g.Vh), NT, 0, st>>>(U12, g, beta, c1, coef, keep, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// sum over x and ordered mu != nu of Re tr R_munu(x) / 3: the loop from x is the link
+// U_mu(x) followed by the walk of the first rectangle (long side mu, above)
+__global__ void __launch_bounds__(NT) rectangle_kernel(const double2* U, Geom g, RedArgs R, int slot) {
+    const int t = blockIdx.x * NT + threadIdx.x;
+    double acc = 0.0;
+    if (t < 2 * g.Vh) {
+        const int p = t >= g.Vh, i = t - p * g.Vh;
+        int x[4];
+        eo_coords(g, p, i, x);
+#pragma unroll 1
+        for (int mu = 0; mu < 4; ++mu) {
+            const dmat Umu = load_link(U, g.Vh, p, mu, i);
+#pragma unroll 1
+            for (int nu = 0; nu < 4; ++nu) {
+                if (nu == mu) continue;
+                const dmat S = walk5<double>(U, g, x, mu, nu, RECT_WALKS[0]);
+                // Re tr(U S) from the diagonal of the product
+                double tr = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        tr = fma(Umu.e[a][b].r, S.e[b][a].r, fma(-Umu.e[a][b].i, S.e[b][a].i, tr));
+                acc += tr;
+            }
+        }
+        acc *= (1.0 / 3.0);
+    }
+    double bs = block_sum(acc);
+    grid_reduce(bs, R.partials, R.counter, R.s, RED_STORE, slot);
+}
+cudaError_t gauge_rectangles(const double2* U, const Geom& g, const RedArgs& R, int slot, cudaStream_t st) {
+    if (grid_for(2L * g.Vh) > R.capacity) return cudaErrorInvalidValue;
+    rectangle_kernel<<<grid_for(2L * g.Vh), NT, 0, st>>>(U, g, R, slot);
     count_launch();
     return cudaGetLastError();
 }

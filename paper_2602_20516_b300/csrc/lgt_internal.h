@@ -132,13 +132,16 @@ cudaError_t gauge_random(double2* U, float4* U12, const Geom& g, uint64_t seed, 
 cudaError_t gauge_make12(float4* U12, const double2* U, const Geom& g, cudaStream_t st);
 cudaError_t gauge_reunitarise(double2* U, float4* U12, const Geom& g, cudaStream_t st);
 cudaError_t gauge_plaquette(const double2* U, const Geom& g, const RedArgs& R, int slot, cudaStream_t st);
-// mom (or F) update from the gauge force: F_G -> out = keep*out + coef*F (Lie or G form)
-cudaError_t gauge_force(const double2* U, const Geom& g, double beta, double coef, int keep, int form,
+// mom (or F) update from the gauge force: F_G -> out = keep*out + coef*F (Lie or G form);
+// c1 = rectangle weight of the improved action (0: Wilson plaquette action)
+cudaError_t gauge_force(const double2* U, const Geom& g, double beta, double c1, double coef, int keep, int form,
                         double2* out, cudaStream_t st);
 // Lie-form gauge force with FP32 staple arithmetic on the two-row links,
 // accumulated into FP64 (the mixed-precision MD path)
-cudaError_t gauge_force_fp32(const float4* U12, const Geom& g, double beta, double coef, int keep, double2* out,
-                             cudaStream_t st);
+cudaError_t gauge_force_fp32(const float4* U12, const Geom& g, double beta, double c1, double coef, int keep,
+                             double2* out, cudaStream_t st);
+// sum_{x, mu != nu} Re tr R_munu(x) / 3 (2 x 1 rectangles) -> slot
+cudaError_t gauge_rectangles(const double2* U, const Geom& g, const RedArgs& R, int slot, cudaStream_t st);
 // U <- exp(i eps P) U, refresh FP32 copy
 cudaError_t gauge_update_links(double2* U, float4* U12, const double2* mom, double eps, const Geom& g,
                                cudaStream_t st);

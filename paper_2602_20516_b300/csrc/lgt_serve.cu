@@ -265,7 +265,7 @@ int finish(lgt_server* S, Req* R) {
         STRY(rhop(S, R, true, true, 1, R->Y, Yo, kappa));
         int keep = 0;
         if (R->q.beta != 0.0) {
-            SCK(gauge_force(G.U, g, R->q.beta, 1.0, 0, 0, R->out, S->st));
+            SCK(gauge_force(G.U, g, R->q.beta, 0.0, 1.0, 0, 0, R->out, S->st));
             keep = 1;
         }
         SCK(fermion_force(G.U, R->X, R->Y, g, kappa, 1.0, keep, 0, R->out, S->st));

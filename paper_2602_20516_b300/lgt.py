@@ -49,7 +49,7 @@ class SolveStats(C.Structure):
 class ActionParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("fermions", C.c_int),
                 ("even_odd", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double),
-                ("stout_recompute", C.c_int), ("force_arith", C.c_int)]
+                ("stout_recompute", C.c_int), ("force_arith", C.c_int), ("c1", C.c_double)]
 
 
 class HMCParams(C.Structure):
@@ -112,6 +112,7 @@ SIGNATURES = [
     ("lgt_random_links", _I, [_P, _U64, _D]),
     ("lgt_reunitarise", _I, [_P]),
     ("lgt_plaquette", _I, [_P, C.POINTER(_D)]),
+    ("lgt_rectangle", _I, [_P, C.POINTER(_D)]),
     ("lgt_plaquette_noalloc", _I, [_P, C.POINTER(C.c_int), _P, _P]),
     ("lgt_pack_spinor", _I, [_P, _P, _P, _I, _I]),
     ("lgt_unpack_spinor", _I, [_P, _P, _P, _I, _I]),
@@ -191,11 +192,12 @@ ARITH = {"fp64": 0, "fp32": 1, "df64": 2}
 
 
 def action_params(beta=0.0, kappa=0.0, fermions=True, even_odd=False, n_stout=0, rho=0.0,
-                  stout_recompute=False, force_arith="fp64"):
+                  stout_recompute=False, force_arith="fp64", c1=0.0):
     """force_arith: arithmetic of Lie-form forces with the mixed solver ("fp64",
-    "fp32" or "df64", the double-float FP32-pair format)."""
+    "fp32" or "df64", the double-float FP32-pair format); c1: rectangle weight of the
+    gauge action (0 Wilson, -1/12 Symanzik, -0.331 Iwasaki, -1.4088 DBW2)."""
     return ActionParams(beta, kappa, int(fermions), int(even_odd), n_stout, rho, int(stout_recompute),
-                        ARITH[force_arith] if isinstance(force_arith, str) else int(force_arith))
+                        ARITH[force_arith] if isinstance(force_arith, str) else int(force_arith), c1)
 
 
 SEXTON_WEINGARTEN = 2
@@ -327,6 +329,11 @@ class Lattice:
 
     def reunitarise(self):
         check(lib().lgt_reunitarise(self.h))
+
+    def rectangle(self):
+        r = C.c_double()
+        check(lib().lgt_rectangle(self.h, C.byref(r)))
+        return r.value
 
     def plaquette(self):
         v = C.c_double()

@@ -424,3 +424,47 @@ def test_full_size_hop_sampled(lgt, ora):
         got = _np(lat.unpack_spinor(h, lgt.EVEN, prec))
         assert H.rel(got[sample], want[sample]) < tol
         assert H.rel(got[ev], want[ev]) < tol
+
+
+# ------------------------------------------------------------------ rectangle-improved gauge action
+@pytest.mark.parametrize("c1", [-1.0 / 12, -0.331])
+def test_improved_gauge_action_and_force(lgt, ora, c1):
+    """Symanzik and Iwasaki actions: S_G, the mean rectangle, the Lie force (FP64 and
+    FP32 arithmetic; double-float falls back to FP64 for c1 != 0) and the G-form
+    gradient against the oracle."""
+    dims = (8, 6, 4, 10)
+    V = int(np.prod(dims))
+    U = synth.random_links(dims, 0.5, 91)
+    lat = _lat(lgt, dims, U)
+    beta = 2.5
+    ap = lgt.action_params(beta=beta, fermions=False, c1=c1)
+    Sg, _, _ = lat.action(ap)
+    assert abs(Sg - ora.gauge_action(dims, U, beta, c1)) < 1e-12 * abs(Sg)
+    assert abs(lat.rectangle() - ora.rectangle_sum(dims, U) / (12 * V)) < 1e-13
+    Fo = ora.gauge_force(dims, U, beta, c1)
+    F, _ = lat.force(ap, None, lgt.solver("fp64"))
+    assert H.rel(_np(lat.unpack_momenta(F)), Fo) < 1e-12
+    G, _ = lat.force(ap, None, lgt.solver("fp64"), form=lgt.GRAD_G)
+    assert H.rel(_np(lat.unpack_grad(G)), ora.gauge_action_grad(dims, U, beta, c1)) < 1e-12
+    for arith, bar in (("fp32", 1e-6), ("df64", 1e-12)):
+        a2 = lgt.action_params(beta=beta, fermions=False, c1=c1, force_arith=arith)
+        F2, _ = lat.force(a2, None, lgt.solver("mixed"))
+        assert H.rel(_np(lat.unpack_momenta(F2)), Fo) < bar, arith
+
+
+def test_improved_hmc_trajectory_matches_oracle(lgt, ora):
+    """Iwasaki gauge action + Nf=2 Wilson fermions, leapfrog: energies and Delta H of
+    one trajectory against the oracle."""
+    dims = (4, 4, 4, 4)
+    U = synth.random_links(dims, 0.3, 92)
+    lat = _lat(lgt, dims, U)
+    c1 = -0.331
+    ap = lgt.action_params(beta=2.3, kappa=0.14, c1=c1)
+    sp = lgt.solver("fp64", tol=1e-13)
+    r = lat.hmc_trajectory(ap, lgt.hmc_params("leapfrog", 10, 1.0, sp, sp), 3, 0)
+    Uo, ro = ora.hmc_trajectory(dims, U, ora.hmc_params(2.3, 0.14, integrator="leapfrog", n_steps=10, tau=1.0,
+                                                        tol_md=1e-13, tol_action=1e-13, c1=c1), 3, 0)
+    for k in ("K_old", "Sg_old", "Sf_old", "K_new", "Sg_new", "Sf_new"):
+        assert abs(r[k] - ro[k]) / abs(ro[k]) < 1e-10, k
+    assert abs(r["dH"] - ro["dH"]) < 1e-8 * max(1.0, abs(ro["dH"]))
+    assert r["accepted"] == ro["accepted"]
