@@ -457,11 +457,11 @@ def run_hmc(args):
     import torch
     from paper_2602_20516_b300 import lgt
     torch.cuda.set_device(0)
-    ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True)
-    mixed = lgt.solver("mixed", tol=TOL, delta=DELTA)
-    fp64 = lgt.solver("fp64", tol=TOL)
-    hp_m = lgt.hmc_params("omelyan", 20, 1.0, mixed, mixed)
-    hp_d = lgt.hmc_params("omelyan", 20, 1.0, fp64, fp64)
+    ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith=FORCE_ARITH)
+    mixed = lgt.solver("mixed", tol=TOL, delta=DELTA, chrono=args.chrono)
+    fp64 = lgt.solver("fp64", tol=TOL, chrono=args.chrono)
+    hp_m = lgt.hmc_params("omelyan", 20, 1.0, mixed, lgt.solver("mixed", tol=TOL, delta=DELTA))
+    hp_d = lgt.hmc_params("omelyan", 20, 1.0, fp64, lgt.solver("fp64", tol=TOL))
     lat = lgt.Lattice(DIMS)
     lat.random_links(SEED, ALPHA)
     ref = lgt.Lattice(DIMS) if args.hmc_fp64 > 0 else None
@@ -490,7 +490,8 @@ def run_hmc(args):
            "seconds_per_trajectory_fp64": statistics.mean(t["fp64_seconds"] for t in trajs if "fp64_seconds" in t)
            if args.hmc_fp64 else None,
            "config": {"lattice": list(DIMS), "beta": BETA, "kappa": KAPPA, "alpha_start": ALPHA, "seed": SEED,
-                      "tol": TOL, "delta": DELTA, "integrator": "omelyan2mn", "n_steps": 20, "tau": 1.0},
+                      "tol": TOL, "delta": DELTA, "integrator": "omelyan2mn", "n_steps": 20, "tau": 1.0,
+                      "force_arith": FORCE_ARITH, "chrono": args.chrono},
            "per_trajectory": trajs}
     print(json.dumps(out), flush=True)
 
@@ -555,6 +556,8 @@ def main():
     ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")
     ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
     ap.add_argument("--hmc-fp64", type=int, default=2, help="trajectories replayed on the FP64 path")
+    ap.add_argument("--chrono", type=int, default=0,
+                    help="HMC mode: MD solves start from the last N solutions (chronological guess)")
     ap.add_argument("--kernel", choices=["hop32", "hop64", "force_df"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()

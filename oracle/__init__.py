@@ -36,7 +36,7 @@ class HMCParams(C.Structure):
                 ("fermions", C.c_int), ("integrator", C.c_int), ("n_steps", C.c_int),
                 ("tau", C.c_double), ("tol_md", C.c_double), ("tol_action", C.c_double),
                 ("max_iter", C.c_int), ("n_inner", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double),
-                ("c1", C.c_double)]
+                ("c1", C.c_double), ("csw", C.c_double)]
 
 
 class HMCResult(C.Structure):
@@ -73,6 +73,16 @@ def lib():
             "ora_gauge_action": (C.c_double, [_ip, _cp, C.c_double]),
             "ora_gauge_action_imp": (C.c_double, [_ip, _cp, C.c_double, C.c_double]),
             "ora_rectangle_sum": (C.c_double, [_ip, _cp]),
+            "ora_clover_field_strength": (None, [_ip, _cp, C.c_int, C.c_int, _cp]),
+            "ora_clover_term": (None, [_ip, _cp, C.c_double, C.c_double, _cp]),
+            "ora_dirac_sw": (None, [_ip, _cp, C.c_double, C.c_double, _cp, _cp, C.c_int]),
+            "ora_cg_sw": (C.c_int, [_ip, _cp, C.c_double, C.c_double, _cp, _cp, C.c_double, C.c_int,
+                                    C.POINTER(C.c_double)]),
+            "ora_pf_action_sw": (C.c_double, [_ip, _cp, C.c_double, C.c_double, _cp, C.c_double, C.c_int,
+                                              C.POINTER(C.c_int)]),
+            "ora_pf_action_grad_sw": (C.c_int, [_ip, _cp, C.c_double, C.c_double, _cp, C.c_double, C.c_int, _cp]),
+            "ora_pf_force_sw": (C.c_int, [_ip, _cp, C.c_double, C.c_double, _cp, C.c_double, C.c_int,
+                                          C.c_double, _dp]),
             "ora_gauge_force_imp": (None, [_ip, _cp, C.c_double, C.c_double, C.c_double, _dp]),
             "ora_gauge_action_grad_imp": (None, [_ip, _cp, C.c_double, C.c_double, _cp]),
             "ora_pf_action": (C.c_double, [_ip, _cp, C.c_double, C.c_int, _cp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
@@ -224,6 +234,58 @@ def gauge_action(dims, U, beta, c1=0.0):
     return lib().ora_gauge_action_imp(_dims(dims), _c(U), beta, c1)
 
 
+# ---------------------------------------------------------------- clover term (full lattice)
+def clover_field_strength(dims, U, mu, nu):
+    """F_munu(x) = (Q - Q^+)/(8i), Q the four leaves of the mu-nu plane at x: (V, 3, 3)."""
+    d = _dims(dims)
+    F = np.zeros((volume(d), 3, 3), np.complex128)
+    lib().ora_clover_field_strength(d, _c(U), mu, nu, F)
+    return F
+
+
+def clover_term(dims, U, kappa, csw):
+    """A(x) = -kappa c_sw sum_{mu<nu} sigma_munu F_munu(x) as (V, 12, 12), index 3 spin + colour."""
+    d = _dims(dims)
+    A = np.zeros((volume(d), 12, 12), np.complex128)
+    lib().ora_clover_term(d, _c(U), kappa, csw, A)
+    return A
+
+
+def dirac_sw(dims, U, kappa, csw, psi, dagger=False):
+    d = _dims(dims)
+    out = np.zeros_like(_c(psi))
+    lib().ora_dirac_sw(d, _c(U), kappa, csw, _c(psi), out, int(dagger))
+    return out
+
+
+def cg_sw(dims, U, kappa, csw, b, tol=1e-12, max_iter=10000):
+    d = _dims(dims)
+    x = np.zeros_like(_c(b))
+    res = C.c_double()
+    it = lib().ora_cg_sw(d, _c(U), kappa, csw, _c(b), x, tol, max_iter, C.byref(res))
+    return x, it, res.value
+
+
+def pf_action_sw(dims, U, kappa, csw, phi, tol=1e-12, max_iter=10000):
+    it = C.c_int()
+    S = lib().ora_pf_action_sw(_dims(dims), _c(U), kappa, csw, _c(phi), tol, max_iter, C.byref(it))
+    return S, it.value
+
+
+def pf_action_grad_sw(dims, U, kappa, csw, phi, tol=1e-12, max_iter=10000):
+    d = _dims(dims)
+    G = np.zeros((volume(d), 4, 3, 3), np.complex128)
+    it = lib().ora_pf_action_grad_sw(d, _c(U), kappa, csw, _c(phi), tol, max_iter, G)
+    return G, it
+
+
+def pf_force_sw(dims, U, kappa, csw, phi, tol=1e-12, max_iter=10000):
+    d = _dims(dims)
+    F = np.zeros((volume(d), 4, 8))
+    it = lib().ora_pf_force_sw(d, _c(U), kappa, csw, _c(phi), tol, max_iter, 1.0, F)
+    return F, it
+
+
 def rectangle_sum(dims, U):
     """sum over x and ordered mu != nu of Re tr R_munu(x) / 3 (2 x 1 loops, long side mu)."""
     return lib().ora_rectangle_sum(_dims(dims), _c(U))
@@ -320,9 +382,12 @@ INTEGRATORS = {"leapfrog": 0, "omelyan": 1, "sexton_weingarten": 2}
 
 
 def hmc_params(beta, kappa, eo=False, fermions=True, integrator="leapfrog", n_steps=10,
-               tau=1.0, tol_md=1e-12, tol_action=1e-12, max_iter=10000, n_inner=1, n_stout=0, rho=0.0, c1=0.0):
+               tau=1.0, tol_md=1e-12, tol_action=1e-12, max_iter=10000, n_inner=1, n_stout=0, rho=0.0, c1=0.0,
+               csw=0.0):
+    if csw != 0.0 and eo:
+        raise ValueError("the clover term is implemented for the full-lattice action only")
     return HMCParams(beta, kappa, int(eo), int(fermions), INTEGRATORS[integrator], n_steps, tau, tol_md,
-                     tol_action, max_iter, n_inner, n_stout, rho, c1)
+                     tol_action, max_iter, n_inner, n_stout, rho, c1, csw)
 
 
 def md_force(dims, U, params, phi, part=0):

@@ -7,7 +7,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["ora_core.c", "ora_dirac.c", "ora_gauge.c", "ora_hmc.c"]
+SOURCES = ["ora_core.c", "ora_dirac.c", "ora_gauge.c", "ora_hmc.c", "ora_clover.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -62,12 +62,28 @@ void ora_hop(const int d[4], const ocplx *U, const ocplx *in, ocplx *out, int ou
     }
 }
 
-void ora_dirac(const int d[4], const ocplx *U, double kappa, const ocplx *in, ocplx *out,
-               int dagger)
+/* D = 1 - kappa H (+ A when a clover term A, [V][12][12], is given; A is Hermitian,
+ * so D^+ = 1 - kappa H^+ + A) */
+void ora_dirac_c(const int d[4], const ocplx *U, double kappa, const ocplx *A, const ocplx *in,
+                 ocplx *out, int dagger)
 {
     long V = ora_volume(d);
     ora_hop(d, U, in, out, 3, dagger);
     for (long i = 0; i < V * 12; ++i) out[i] = in[i] - kappa * out[i];
+    if (!A) return;
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < V; ++x)
+        for (int i = 0; i < 12; ++i) {
+            ocplx acc = 0;
+            for (int j = 0; j < 12; ++j) acc += A[(x * 12 + i) * 12 + j] * in[x * 12 + j];
+            out[x * 12 + i] += acc;
+        }
+}
+
+void ora_dirac(const int d[4], const ocplx *U, double kappa, const ocplx *in, ocplx *out,
+               int dagger)
+{
+    ora_dirac_c(d, U, kappa, NULL, in, out, dagger);
 }
 
 void ora_dhat(const int d[4], const ocplx *U, double kappa, const ocplx *in, ocplx *out,
@@ -103,16 +119,16 @@ double ora_norm2(const int d[4], const ocplx *a, int mask)
     return creal(ora_dot(d, a, a, mask));
 }
 
-/* A = M^+ M with M = D (full) or Dhat (even sites) */
-static void apply_A(const int d[4], const ocplx *U, double kappa, int eo, const ocplx *in,
+/* A = M^+ M with M = D (full, with clover term C if given) or Dhat (even sites) */
+static void apply_A(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo, const ocplx *in,
                     ocplx *out, ocplx *tmp)
 {
     if (eo) {
         ora_dhat(d, U, kappa, in, tmp, 0);
         ora_dhat(d, U, kappa, tmp, out, 1);
     } else {
-        ora_dirac(d, U, kappa, in, tmp, 0);
-        ora_dirac(d, U, kappa, tmp, out, 1);
+        ora_dirac_c(d, U, kappa, C, in, tmp, 0);
+        ora_dirac_c(d, U, kappa, C, tmp, out, 1);
     }
 }
 
@@ -122,8 +138,8 @@ static void apply_A(const int d[4], const ocplx *U, double kappa, int eo, const 
  * When the recursive residual passes tol the true residual is formed; if it is
  * still above tol the recursion restarts from it.
  * ------------------------------------------------------------------------- */
-int ora_cg(const int d[4], const ocplx *U, double kappa, int eo, const ocplx *b, ocplx *x,
-           double tol, int max_iter, double *true_res)
+int ora_cg_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo, const ocplx *b, ocplx *x,
+             double tol, int max_iter, double *true_res)
 {
     long n = ora_volume(d) * 12;
     int mask = eo ? 1 : 3;
@@ -138,14 +154,14 @@ int ora_cg(const int d[4], const ocplx *U, double kappa, int eo, const ocplx *b,
     double res = (bb > 0) ? 1.0 : 0.0;
     if (bb == 0) converged = 1;
     while (!converged && k < max_iter) {
-        apply_A(d, U, kappa, eo, p, Ap, tmp);
+        apply_A(d, U, kappa, C, eo, p, Ap, tmp);
         double pAp = creal(ora_dot(d, p, Ap, mask));
         double alpha = rr / pAp;
         for (long i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * Ap[i]; }
         double rr_new = ora_norm2(d, r, mask);
         ++k;
         if (rr_new <= tol * tol * bb) {
-            apply_A(d, U, kappa, eo, x, Ap, tmp);
+            apply_A(d, U, kappa, C, eo, x, Ap, tmp);
             for (long i = 0; i < n; ++i) r[i] = b[i] - Ap[i];
             rr_new = ora_norm2(d, r, mask);
             res = sqrt(rr_new / bb);
@@ -156,7 +172,7 @@ int ora_cg(const int d[4], const ocplx *U, double kappa, int eo, const ocplx *b,
         rr = rr_new;
     }
     if (!converged) {
-        apply_A(d, U, kappa, eo, x, Ap, tmp);
+        apply_A(d, U, kappa, C, eo, x, Ap, tmp);
         for (long i = 0; i < n; ++i) r[i] = b[i] - Ap[i];
         res = sqrt(ora_norm2(d, r, mask) / bb);
     }
@@ -165,24 +181,36 @@ int ora_cg(const int d[4], const ocplx *U, double kappa, int eo, const ocplx *b,
     return converged ? k : -k;
 }
 
+int ora_cg(const int d[4], const ocplx *U, double kappa, int eo, const ocplx *b, ocplx *x,
+           double tol, int max_iter, double *true_res)
+{
+    return ora_cg_c(d, U, kappa, NULL, eo, b, x, tol, max_iter, true_res);
+}
+
 /* S_f = phi^+ A^{-1} phi evaluated as 2 Re(phi^+ chi) - |M chi|^2, which equals it
  * at the exact chi and deviates only quadratically in the solver error. */
-double ora_pf_action(const int d[4], const ocplx *U, double kappa, int eo, const ocplx *phi,
-                     double tol, int max_iter, int *iters)
+double ora_pf_action_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo, const ocplx *phi,
+                       double tol, int max_iter, int *iters)
 {
     long n = ora_volume(d) * 12;
     int mask = eo ? 1 : 3;
     ocplx *chi = malloc(n * sizeof(ocplx));
     ocplx *eta = malloc(n * sizeof(ocplx));
     double res;
-    int it = ora_cg(d, U, kappa, eo, phi, chi, tol, max_iter, &res);
+    int it = ora_cg_c(d, U, kappa, C, eo, phi, chi, tol, max_iter, &res);
     if (iters) *iters = it;
     if (eo) ora_dhat(d, U, kappa, chi, eta, 0);
-    else ora_dirac(d, U, kappa, chi, eta, 0);
+    else ora_dirac_c(d, U, kappa, C, chi, eta, 0);
     double S = 2 * creal(ora_dot(d, phi, chi, mask)) - ora_norm2(d, eta, mask);
     free(chi);
     free(eta);
     return S;
+}
+
+double ora_pf_action(const int d[4], const ocplx *U, double kappa, int eo, const ocplx *phi,
+                     double tol, int max_iter, int *iters)
+{
+    return ora_pf_action_c(d, U, kappa, NULL, eo, phi, tol, max_iter, iters);
 }
 
 /* ---------------------------------------------------------------------------
@@ -247,8 +275,7 @@ void ora_fermion_force_xy(const int d[4], const ocplx *U, double kappa, const oc
         }
 }
 
-static void fermion_grad_xy(const int d[4], double kappa, const ocplx *X, const ocplx *Y,
-                            ocplx *G)
+void ora_fermion_grad_xy(const int d[4], double kappa, const ocplx *X, const ocplx *Y, ocplx *G)
 {
     ocplx gam[4][16];
     for (int mu = 0; mu < 4; ++mu) ora_gamma(mu, gam[mu]);
@@ -266,14 +293,14 @@ static void fermion_grad_xy(const int d[4], double kappa, const ocplx *X, const 
 /* X and Y of the force: full lattice X = chi, Y = D chi; even-odd
  * X = (chi_e, kappa H_oe chi_e), Y = (eta_e, kappa (H^+)_oe eta_e), eta_e = Dhat chi_e,
  * from eta_e^+ (delta Dhat) chi_e = Y^+ (-kappa delta H) X. */
-static int force_vectors(const int d[4], const ocplx *U, double kappa, int eo,
-                         const ocplx *phi, double tol, int max_iter, ocplx *X, ocplx *Y)
+int ora_force_vectors_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo,
+                        const ocplx *phi, double tol, int max_iter, ocplx *X, ocplx *Y)
 {
     long n = ora_volume(d) * 12;
     double res;
-    int it = ora_cg(d, U, kappa, eo, phi, X, tol, max_iter, &res);
+    int it = ora_cg_c(d, U, kappa, C, eo, phi, X, tol, max_iter, &res);
     if (!eo) {
-        ora_dirac(d, U, kappa, X, Y, 0);
+        ora_dirac_c(d, U, kappa, C, X, Y, 0);
         return it;
     }
     ora_dhat(d, U, kappa, X, Y, 0);            /* eta_e on even sites, 0 on odd */
@@ -297,7 +324,7 @@ int ora_pf_force(const int d[4], const ocplx *U, double kappa, int eo, const ocp
     long n = ora_volume(d) * 12;
     ocplx *X = calloc(n, sizeof(ocplx));
     ocplx *Y = calloc(n, sizeof(ocplx));
-    int it = force_vectors(d, U, kappa, eo, phi, tol, max_iter, X, Y);
+    int it = ora_force_vectors_c(d, U, kappa, NULL, eo, phi, tol, max_iter, X, Y);
     ora_fermion_force_xy(d, U, kappa, X, Y, coef, F);
     free(X);
     free(Y);
@@ -310,8 +337,8 @@ int ora_pf_action_grad(const int d[4], const ocplx *U, double kappa, int eo,
     long n = ora_volume(d) * 12;
     ocplx *X = calloc(n, sizeof(ocplx));
     ocplx *Y = calloc(n, sizeof(ocplx));
-    int it = force_vectors(d, U, kappa, eo, phi, tol, max_iter, X, Y);
-    fermion_grad_xy(d, kappa, X, Y, G);
+    int it = ora_force_vectors_c(d, U, kappa, NULL, eo, phi, tol, max_iter, X, Y);
+    ora_fermion_grad_xy(d, kappa, X, Y, G);
     free(X);
     free(Y);
     return it;

@@ -2,6 +2,7 @@
  * ora_hmc.c -- molecular dynamics and one HMC trajectory with the left update
  * of Eq. S2.1 / S2.2: leapfrog (PQP), Omelyan 2MN, or a Sexton-Weingarten
  * nested leapfrog (gauge force on the inner time scale), Metropolis on Delta H.
+ * The pseudofermion operator may carry the clover term (full lattice, csw).
  * With stout smearing the pseudofermion action sees the smeared links and its
  * force is taken back through every level (the reverse recursion of Eq. 3);
  * the gauge action sees the thin links.
@@ -40,14 +41,19 @@ int ora_md_force_part(const int d[4], const ocplx *U, const ora_hmc_params *p, c
     if (part != 2 && p->beta != 0.0) ora_gauge_force_imp(d, U, p->beta, p->c1, 1.0, F);
     if (part == 1 || !p->fermions) return 0;
     int it;
-    if (p->n_stout == 0) {
+    if (p->n_stout == 0 && p->csw == 0.0) {
         it = ora_pf_force(d, U, p->kappa, p->eo, phi, p->tol_md, p->max_iter, 1.0, F);
+    } else if (p->n_stout == 0) {
+        it = ora_pf_force_sw(d, U, p->kappa, p->csw, phi, p->tol_md, p->max_iter, 1.0, F);
     } else {
         ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
         ocplx *G = malloc(sizeof(ocplx) * 36 * V);
         ocplx *G2 = malloc(sizeof(ocplx) * 36 * V);
         double *Ff = malloc(sizeof(double) * 32 * V);
-        it = ora_pf_action_grad(d, lv[p->n_stout], p->kappa, p->eo, phi, p->tol_md, p->max_iter, G);
+        if (p->csw == 0.0)
+            it = ora_pf_action_grad(d, lv[p->n_stout], p->kappa, p->eo, phi, p->tol_md, p->max_iter, G);
+        else
+            it = ora_pf_action_grad_sw(d, lv[p->n_stout], p->kappa, p->csw, phi, p->tol_md, p->max_iter, G);
         for (int k = p->n_stout; k >= 1; --k) {
             ora_stout_backward(d, lv[k - 1], p->rho, G, G2);
             ocplx *t = G; G = G2; G2 = t;
@@ -69,9 +75,10 @@ int ora_md_force(const int d[4], const ocplx *U, const ora_hmc_params *p, const 
 static double pf_action_smeared(const int d[4], const ocplx *U, const ora_hmc_params *p,
                                 const ocplx *phi, int *it)
 {
-    if (p->n_stout == 0) return ora_pf_action(d, U, p->kappa, p->eo, phi, p->tol_action, p->max_iter, it);
     ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
-    double S = ora_pf_action(d, lv[p->n_stout], p->kappa, p->eo, phi, p->tol_action, p->max_iter, it);
+    double S = (p->csw == 0.0)
+                   ? ora_pf_action(d, lv[p->n_stout], p->kappa, p->eo, phi, p->tol_action, p->max_iter, it)
+                   : ora_pf_action_sw(d, lv[p->n_stout], p->kappa, p->csw, phi, p->tol_action, p->max_iter, it);
     free_levels(lv, p->n_stout);
     return S;
 }
@@ -163,7 +170,7 @@ int ora_hmc_trajectory(const int d[4], ocplx *U, const ora_hmc_params *p, uint64
         /* phi = M^+ xi on the links the pseudofermion action sees: S_f(old) = xi^+ xi */
         ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
         if (p->eo) ora_dhat(d, lv[p->n_stout], p->kappa, xi, phi, 1);
-        else ora_dirac(d, lv[p->n_stout], p->kappa, xi, phi, 1);
+        else ora_dirac_sw(d, lv[p->n_stout], p->kappa, p->csw, xi, phi, 1);
         free_levels(lv, p->n_stout);
         res->Sf_old = ora_norm2(d, xi, mask);
     }

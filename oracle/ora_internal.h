@@ -17,6 +17,19 @@ void su3_dag(const ocplx *A, ocplx *B);
 void su3_from_coeffs(const double *h, ocplx *H);
 void su3_expi(const ocplx *H, double eps, ocplx *out);
 
+/* Dirac operator, CG, action and force vectors with an optional clover term C
+ * ([V][12][12], NULL: Wilson); the public entry points pass NULL */
+void ora_dirac_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, const ocplx *in,
+                 ocplx *out, int dagger);
+int ora_cg_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo, const ocplx *b, ocplx *x,
+             double tol, int max_iter, double *true_res);
+double ora_pf_action_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo, const ocplx *phi,
+                       double tol, int max_iter, int *iters);
+int ora_force_vectors_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo,
+                        const ocplx *phi, double tol, int max_iter, ocplx *X, ocplx *Y);
+/* real-component gradient of the hopping part of S_f from X, Y (written to G) */
+void ora_fermion_grad_xy(const int d[4], double kappa, const ocplx *X, const ocplx *Y, ocplx *G);
+
 /* inner products over sites whose parity bit is in mask */
 ocplx ora_dot(const int d[4], const ocplx *a, const ocplx *b, int mask);
 double ora_norm2(const int d[4], const ocplx *a, int mask);

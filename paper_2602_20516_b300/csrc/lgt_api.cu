@@ -775,10 +775,14 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
         TRY(sync_scalars(L));
         rr0 = hs->slot[0];
         st.reliable_updates += 1;
-        if (!std::isfinite(rr0)) return fail(LGT_ENAN, "non-finite residual of the initial guess");
-    } else {
-        CK(cudaMemcpyAsync(L->r, b, b64, cudaMemcpyDeviceToDevice, L->st));
+        // a guess no better than zero (e.g. from a history of another source) is dropped
+        if (!(rr0 < bb)) {
+            guess = false;
+            rr0 = bb;
+            CK(cudaMemsetAsync(x, 0, b64, L->st));
+        }
     }
+    if (!guess) CK(cudaMemcpyAsync(L->r, b, b64, cudaMemcpyDeviceToDevice, L->st));
     memset(hs, 0, sizeof(Scalars));
     hs->rr = rr0;
     hs->rr_max = rr0;

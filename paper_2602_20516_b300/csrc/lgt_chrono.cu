@@ -88,9 +88,12 @@ cudaError_t cdot_many(const CdotArgs& D, int M, bool b_fp32, cudaStream_t st) {
 }
 
 // G (N x N, row-major, G[i*N+j] = <v_i, A v_j>) and g (N) -> c with G c = g.  G is
-// Hermitian positive definite for independent v; the Hermitian part is used, and a
-// vector whose Cholesky pivot is not positive beyond roundoff (dependent on the ones
-// before it) gets c = 0 and is left out.  Result in c[0..N), count kept in *used.
+// Hermitian positive definite for independent v; the Hermitian part is used.  The
+// products A v are FP32 (relative error ~1e-7), and successive MD solutions are close
+// to parallel: a vector whose Cholesky pivot (the squared A-norm of its part not
+// spanned by the vectors before it) is below 1e-6 of the largest diagonal entry is
+// at the FP32 noise level of G, gets c = 0 and is left out.  Result in c[0..N),
+// count kept in *used.
 __global__ void chrono_solve_kernel(const double2* G, const double2* g, double2* c, int N, int* used) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double Lr[CHRONO_MAX][CHRONO_MAX], Li[CHRONO_MAX][CHRONO_MAX];
@@ -103,7 +106,7 @@ __global__ void chrono_solve_kernel(const double2* G, const double2* g, double2*
         double d = G[j * N + j].x;
         for (int k = 0; k < j; ++k)
             if (keep[k]) d -= Lr[j][k] * Lr[j][k] + Li[j][k] * Li[j][k];
-        keep[j] = d > 1e-12 * dmax;
+        keep[j] = d > 1e-6 * dmax;
         for (int i = 0; i < N; ++i) { Lr[i][j] = 0.0; Li[i][j] = 0.0; }
         if (!keep[j]) continue;
         ++n_used;

@@ -93,3 +93,15 @@ def test_hmc_trajectory_with_guess(lgt):
     assert abs(res[4]["dH"] - res[0]["dH"]) < 1e-6 * max(1.0, abs(res[0]["dH"]))
     # measured: 1933 against 2270 iterations (10 Omelyan steps, eps = 0.1)
     assert res[4]["total"]["iters"] < 0.9 * res[0]["total"]["iters"]
+
+
+def test_guess_with_nearly_parallel_history(lgt):
+    """Small MD steps make the kept solutions nearly parallel (the Gram matrix close to
+    singular at the FP32 level of its entries): the guess must still help, never hurt."""
+    zero = _md_sequence(lgt, lgt.solver("mixed", tol=1e-10, delta=1e-4), steps=9, eps=0.002)
+    chrono = _md_sequence(lgt, lgt.solver("mixed", tol=1e-10, delta=1e-4, chrono=4), steps=9, eps=0.002)
+    for (xc, sc), (xz, sz) in zip(chrono, zero):
+        assert sc["true_rel_residual"] <= 1e-10
+        assert sc["iters"] <= sz["iters"]
+        assert H.rel(xc.cpu().numpy(), xz.cpu().numpy()) < 1e-7
+    assert sum(s["iters"] for _, s in chrono[4:]) < 0.5 * sum(s["iters"] for _, s in zero[4:])

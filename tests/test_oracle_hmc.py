@@ -159,3 +159,27 @@ def test_improved_gauge_energy_conservation(ora):
     p2 = ora.hmc_params(2.5, 0.0, fermions=False, n_steps=40, tau=1.0, c1=-0.331)
     d1, d2 = abs(_dH(U, mom, phi, p1)), abs(_dH(U, mom, phi, p2))
     assert 3.2 < d1 / d2 < 4.8
+
+
+def test_clover_hmc_reversible_and_dt_squared(ora):
+    """Wilson-clover fermions (c_sw = 1.5, full lattice): the integrator is reversible
+    and Delta H falls by ~4 when the leapfrog step halves."""
+    global ORA
+    ORA = ora
+    U, mom = _setup(seed=9)
+    phi = synth.gaussian_spinor(D4, 10)
+    p = ora.hmc_params(5.7, 0.13, integrator="leapfrog", n_steps=5, tau=0.5, tol_md=1e-14, csw=1.5)
+    U1, m1, _ = ora.md_integrate(D4, U, mom, phi, p)
+    U2, m2, _ = ora.md_integrate(D4, U1, -m1, phi, p)
+    assert H.rel(U2, U) < 1e-11 and H.rel(-m2, mom) < 1e-10
+
+    def energy(Ux, mx, pp):
+        return (ora.gauge_action(D4, Ux, pp.beta) + ora.momentum_energy(D4, mx)
+                + ora.pf_action_sw(D4, Ux, pp.kappa, pp.csw, phi, tol=1e-14)[0])
+
+    dh = []
+    for n in (10, 20):
+        pp = ora.hmc_params(5.7, 0.13, integrator="leapfrog", n_steps=n, tau=1.0, tol_md=1e-14, csw=1.5)
+        Ux, mx, _ = ora.md_integrate(D4, U, mom, phi, pp)
+        dh.append(abs(energy(Ux, mx, pp) - energy(U, mom, pp)))
+    assert 3.2 < dh[0] / dh[1] < 4.8, dh

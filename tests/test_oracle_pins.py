@@ -433,3 +433,99 @@ def test_improved_force_and_gradient_finite_difference(ora):
                 ga = G[s, mu, i, j].real if part == "re" else G[s, mu, i, j].imag
                 assert abs(fd - ga) < 2e-6 * max(1.0, abs(ga))
     assert H.rel(ora.grad_to_force(d, U, G), F) < 1e-13
+
+
+# ------------------------------------------------------------------ clover (Sheikholeslami-Wohlert) term
+def _chiral_gammas():
+    """g_k = [[0, -i s_k], [i s_k, 0]] (mu = k - 1), g_4 = [[0, 1], [1, 0]], built here
+    from the Pauli matrices, independently of the oracle."""
+    s = [np.array([[0, 1], [1, 0]], complex), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]], complex)]
+    z = np.zeros((2, 2))
+    g = [np.block([[z, -1j * sk], [1j * sk, z]]) for sk in s]
+    g.append(np.block([[z, np.eye(2)], [np.eye(2), z]]))
+    return g
+
+
+def _abelian_field(d, n=1):
+    V = int(np.prod(d))
+    phi = 2 * np.pi * n / d[0]
+    x0 = synth.coords(d)[:, 0]
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (V, 4, 3, 3)).copy()
+    for s_ in range(V):
+        U[s_, 1] = np.diag(np.exp(1j * phi * x0[s_] * np.array([1.0, -1.0, 0.0])))
+    return U, phi
+
+
+def test_clover_abelian_field_closed_form(ora):
+    """U_1(x) = exp(i phi x_0 H): all four leaves of the (0,1) plane are exp(i phi H),
+    so F_01 = sin(phi H) = diag(sin phi, -sin phi, 0) at every site and the other
+    planes vanish; D_sw - D = -kappa c_sw sigma_01 (x) F_01."""
+    d = (6, 4, 4, 4)
+    V = int(np.prod(d))
+    U, phi = _abelian_field(d)
+    F01 = ora.clover_field_strength(d, U, 0, 1)
+    want = np.diag([np.sin(phi), -np.sin(phi), 0.0])
+    assert np.abs(F01 - want).max() < 1e-14
+    for (mu, nu) in ((0, 2), (1, 3), (2, 3)):
+        assert np.abs(ora.clover_field_strength(d, U, mu, nu)).max() < 1e-14
+    g = _chiral_gammas()
+    sig01 = 0.5j * (g[0] @ g[1] - g[1] @ g[0])
+    kappa, csw = 0.13, 1.7
+    psi = synth.gaussian_spinor(d, 84)
+    diff = ora.dirac_sw(d, U, kappa, csw, psi) - ora.dirac(d, U, kappa, psi)
+    expect = -kappa * csw * np.einsum("st,ab,xtb->xsa", sig01, want, psi)
+    assert np.abs(diff - expect).max() < 1e-13
+
+
+def test_clover_hermiticity_covariance_and_unit_field(ora):
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 85)
+    kappa, csw = 0.13, 1.5
+    phi, psi = synth.gaussian_spinor(d, 86), synth.gaussian_spinor(d, 87)
+    Dpsi = ora.dirac_sw(d, U, kappa, csw, psi)
+    Ddphi = ora.dirac_sw(d, U, kappa, csw, phi, dagger=True)
+    assert abs(np.vdot(phi, Dpsi) - np.vdot(Ddphi, psi)) < 1e-12 * abs(np.vdot(phi, Dpsi))
+    g5 = np.diag([1, 1, -1, -1])
+    g5D = np.einsum("st,xtc->xsc", g5, ora.dirac_sw(d, U, kappa, csw, np.einsum("st,xtc->xsc", g5, psi)))
+    assert H.rel(g5D, ora.dirac_sw(d, U, kappa, csw, psi, dagger=True)) < 1e-14
+    gt = synth.random_su3(256, 88)
+    Ug = H.gauge_transform_links(d, U, gt)
+    lhs = ora.dirac_sw(d, Ug, kappa, csw, H.gauge_transform_spinor(psi, gt))
+    assert H.rel(lhs, H.gauge_transform_spinor(Dpsi, gt)) < 1e-13
+    one = np.broadcast_to(np.eye(3), (256, 4, 3, 3)).copy()
+    assert H.rel(ora.dirac_sw(d, one, kappa, csw, psi), ora.dirac(d, one, kappa, psi)) < 1e-15
+    # the clover term is Hermitian and traceless in spin at every site
+    A = ora.clover_term(d, U, kappa, csw)
+    assert np.abs(A - np.conj(np.swapaxes(A, 1, 2))).max() < 1e-15
+    assert np.abs(np.einsum("xii->x", A)).max() < 1e-13
+
+
+def test_clover_force_and_gradient_finite_difference(ora):
+    """S_f = phi^+ (D_sw^+ D_sw)^{-1} phi: the Lie force against central differences in
+    Lie directions, and the real-component gradient against differences on entries."""
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 89)
+    kappa, csw = 0.13, 1.5
+    phi = synth.gaussian_spinor(d, 90)
+    F, _ = ora.pf_force_sw(d, U, kappa, csw, phi, tol=1e-14)
+    h = 1e-5
+    for (s, mu) in LINKS:
+        for a in (1, 4, 7):
+            Sp, _ = ora.pf_action_sw(d, H.lie_perturb(U, s, mu, a, h), kappa, csw, phi, tol=1e-14)
+            Sm, _ = ora.pf_action_sw(d, H.lie_perturb(U, s, mu, a, -h), kappa, csw, phi, tol=1e-14)
+            fd = (Sp - Sm) / (2 * h)
+            assert abs(fd - F[s, mu, a]) < 2e-6 * max(1.0, abs(F[s, mu, a]))
+    G, _ = ora.pf_action_grad_sw(d, U, kappa, csw, phi, tol=1e-14)
+    h = 3e-5
+    for (s, mu) in LINKS[:2]:
+        for (i, j) in ((0, 1), (2, 2)):
+            for unit, part in ((1.0, "re"), (1j, "im")):
+                Up = U.copy(); Up[s, mu, i, j] += h * unit
+                Um = U.copy(); Um[s, mu, i, j] -= h * unit
+                fd = (ora.pf_action_sw(d, Up, kappa, csw, phi, tol=1e-14)[0]
+                      - ora.pf_action_sw(d, Um, kappa, csw, phi, tol=1e-14)[0]) / (2 * h)
+                ga = G[s, mu, i, j].real if part == "re" else G[s, mu, i, j].imag
+                assert abs(fd - ga) < 3e-6 * max(1.0, abs(ga))
+    # c_sw = 0 is the Wilson force
+    F0, _ = ora.pf_force_sw(d, U, kappa, 0.0, phi, tol=1e-14)
+    assert H.rel(F0, ora.pf_force(d, U, kappa, phi, tol=1e-14)[0]) < 1e-10
