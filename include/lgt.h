@@ -119,6 +119,12 @@ typedef struct {
                             R the 2 x 1 loop with its long side along mu.  0: Wilson action;
                             -1/12 tree-level Symanzik, -0.331 Iwasaki, -1.4088 DBW2.  With
                             c1 != 0 the LGT_ARITH_DF64 gauge force uses FP64 arithmetic. */
+    double csw;          /* clover coefficient (not printed in the paper; a further discretisation
+                            of Sec. IV): D = 1 - kappa H + A, A(x) = -kappa csw sum_{mu<nu}
+                            sigma_munu F_munu(x), sigma_munu = (i/2)[g_mu, g_nu], F_munu =
+                            (Q_munu - Q_munu^+)/(8i) with Q_munu the four plaquettes (leaves) of
+                            the mu-nu plane at x.  Full-lattice action only (even_odd = 1 with
+                            csw != 0 is LGT_EINVAL); the clover force is FP64 arithmetic. */
 } lgt_action_params;
 
 typedef struct {
@@ -229,6 +235,14 @@ int lgt_pack_links_field(lgt_lattice_t lat, const double *canonical, double *fie
 int lgt_unpack_links_field(lgt_lattice_t lat, const double *field, double *canonical);
 
 /* ------------------------------------------------------------------ operators */
+/* Attach the clover term with coefficient csw (see lgt_action_params.csw) for hopping
+ * parameter kappa, built from the handle's current links, to the operators that act
+ * on them directly: lgt_dslash with LGT_OP_D and the full-lattice lgt_cg_solve (use the
+ * same kappa there).  csw = 0 detaches it.  It is not refreshed when the links change.
+ * lgt_action, lgt_force, lgt_md_update and lgt_hmc_trajectory take the clover term
+ * from lgt_action_params.csw instead.  Synchronous. */
+int lgt_set_clover(lgt_lattice_t lat, double csw, double kappa);
+
 /* Apply a Wilson-Dirac operator (Sec. III: "Wilson-Dirac operator"; D of
  * Eq. S3.1) to `in`, writing `out` (distinct buffers, device layout of
  * `precision`, LGT_FP64 or LGT_FP32).  op/out_parity as in the LGT_OP_* enum;

@@ -4,6 +4,7 @@
 // kernels of the other translation units; this file only sequences launches on
 // the handle's stream and reads back the few scalars the control flow needs.
 #include <chrono>
+#include <complex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -96,6 +97,9 @@ constexpr int MAX_STOUT = LGT_MAX_STOUT;   // stout levels in front of D
 struct Links {
     double2* U;
     float4* U12;
+    // clover term 1 + A of these links (null: Wilson operator)
+    const double2* C64 = nullptr;
+    const float4* C32 = nullptr;
 };
 
 struct lgt_lattice {
@@ -120,6 +124,13 @@ struct lgt_lattice {
     bool have_solver;
     // double-float copies for LGT_ARITH_DF64 forces: links, X, Y
     float4 *Udf, *Xdf, *Ydf;
+    // clover term: fields of the thin links (lgt_set_clover) and of the links of a
+    // force/action call (fermion_links), full spinor temporaries for (1 + A) y, and
+    // the insertion field of the clover force
+    double2 *thin_c64, *call_c64, *cins;
+    float4 *thin_c32, *call_c32;
+    double2* ct64;
+    float4* ct32;
     // several right-hand sides (lgt_cg_solve_multi): per system FP32 even/odd half
     // fields, an FP64 residual, scalars, reduction partials and counter
     struct {
@@ -224,6 +235,48 @@ static int ensure_multi(lgt_lattice* L) {
     CK(cudaMemsetAsync(L->mw.counter, 0, 64 * KMAX_RHS, L->st));
     L->mw.ready = true;
     return LGT_OK;
+}
+
+static int ensure_clover(lgt_lattice* L, bool thin) {
+    const size_t c64 = (size_t)2 * 72 * L->g.Vh * sizeof(double2), c32 = (size_t)2 * 36 * L->g.Vh * sizeof(float4);
+    if (thin && !L->thin_c64) { TRY(A(L, c64, &L->thin_c64)); TRY(A(L, c32, &L->thin_c32)); }
+    if (!thin && !L->call_c64) {
+        TRY(A(L, c64, &L->call_c64));
+        TRY(A(L, c32, &L->call_c32));
+        TRY(A(L, (size_t)2 * 54 * L->g.Vh * sizeof(double2), &L->cins));
+    }
+    if (!L->ct64) { TRY(A(L, spinor64_full(L), &L->ct64)); TRY(A(L, spinor32_full(L), &L->ct32)); }
+    return LGT_OK;
+}
+
+// sigma_munu = (i/2)[g_mu, g_nu] in the chiral basis of the hop kernels
+// (g_k = [[0, -i s_k], [i s_k, 0]] for mu = k - 1, g_4 = [[0, 1], [1, 0]]), as its two
+// 2 x 2 chiral blocks; the off-diagonal blocks vanish because sigma commutes with g5
+static CloverSigma clover_sigma() {
+    typedef std::complex<double> C;
+    const C I(0, 1);
+    C pauli[3][2][2] = {{{0, 1}, {1, 0}}, {{0, -I}, {I, 0}}, {{1, 0}, {0, -1}}};
+    C gam[4][4][4] = {};
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                gam[k][a][2 + b] = -I * pauli[k][a][b];
+                gam[k][2 + a][b] = I * pauli[k][a][b];
+            }
+    for (int a = 0; a < 2; ++a) { gam[3][a][2 + a] = 1; gam[3][2 + a][a] = 1; }
+    CloverSigma S;
+    memset(&S, 0, sizeof S);
+    const int pm[6] = {0, 0, 0, 1, 1, 2}, pn[6] = {1, 2, 3, 2, 3, 3};
+    for (int pl = 0; pl < 6; ++pl)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                C acc = 0;
+                for (int c = 0; c < 4; ++c)
+                    acc += gam[pm[pl]][a][c] * gam[pn[pl]][c][b] - gam[pn[pl]][a][c] * gam[pm[pl]][c][b];
+                acc *= 0.5 * I;
+                if (a / 2 == b / 2) S.s[pl][a / 2][a % 2][b % 2] = make_double2(acc.real(), acc.imag());
+            }
+    return S;
 }
 
 static int ensure_chrono(lgt_lattice* L) {
@@ -543,14 +596,25 @@ static int hop1(lgt_lattice* L, const Links& lk, bool fp64, bool dag, int q, con
     CK(timed_hop(A, fp64, dag, epi, L->st));
     return LGT_OK;
 }
-// full-lattice D or D^+: out = in - kappa H in
+// (1 + A) in into the clover temporary of the precision (full fields), or in itself
+static const void* clover_y(lgt_lattice* L, const Links& lk, bool fp64, const void* in) {
+    if (!lk.C64) return in;
+    void* t = fp64 ? (void*)L->ct64 : (void*)L->ct32;
+    if (clover_apply(fp64 ? (const void*)lk.C64 : (const void*)lk.C32, in, t, L->g, 2, fp64, L->st) != cudaSuccess)
+        return nullptr;
+    return t;
+}
+
+// full-lattice D or D^+: out = (1 + A) in - kappa H in (A = 0 without clover term)
 static int dfull(lgt_lattice* L, const Links& lk, bool fp64, bool dag, const void* in, void* out, double kappa) {
+    const void* yin = clover_y(L, lk, fp64, in);
+    if (!yin) return fail(LGT_ECUDA, "clover apply failed");
     HopArgs A = hop_base(L, lk, fp64);
     A.parity = 2;
     for (int q = 0; q < 2; ++q) {
         A.in[q] = half(in, L, fp64, q);
         A.out[q] = half(out, L, fp64, q);
-        A.y[q] = half(in, L, fp64, q);
+        A.y[q] = half(yin, L, fp64, q);
     }
     A.a = -kappa;
     CK(timed_hop(A, fp64, dag, EPI_XPAY, L->st));
@@ -564,9 +628,26 @@ static int dhat(lgt_lattice* L, const Links& lk, bool fp64, bool dag, const void
     return LGT_OK;
 }
 
+extern "C" int lgt_set_clover(lgt_lattice_t L, double csw, double kappa) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    if (csw == 0.0) {
+        L->thin.C64 = nullptr;
+        L->thin.C32 = nullptr;
+        return LGT_OK;
+    }
+    TRY(ensure_clover(L, true));
+    CK(clover_field(L->thin.U, L->g, clover_sigma(), kappa, csw, L->thin_c64, L->thin_c32, L->st));
+    CK(cudaStreamSynchronize(L->st));
+    L->thin.C64 = L->thin_c64;
+    L->thin.C32 = L->thin_c32;
+    return LGT_OK;
+}
+
 extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, int out_parity, int dagger,
                           double kappa, int precision) {
     if (!L || !in || !out) return fail(LGT_EINVAL, "null argument");
+    if (L->thin.C64 && (op == LGT_OP_DHAT || op == LGT_OP_DHAT_NORMAL))
+        return fail(LGT_EINVAL, "the clover term is attached: even-odd operators are not available");
     if (in == out) return fail(LGT_EINVAL, "in and out must be distinct buffers");
     if (precision != LGT_FP64 && precision != LGT_FP32) return fail(LGT_EINVAL, "precision %d", precision);
     const bool fp64 = precision == LGT_FP64;
@@ -616,19 +697,23 @@ static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, dou
         CK(timed_hop(A, fp64, true, EPI_CG, L->st));
         CK(blas_cg_p_update(p, r, L->g.Vh, L->g.Vh, fp64, red(L), L->st));
     } else {
+        const void* yp = clover_y(L, lk, fp64, p);
+        if (!yp) return fail(LGT_ECUDA, "clover apply failed");
         HopArgs A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 2;
         for (int q = 0; q < 2; ++q) {
-            A.in[q] = half(p, L, fp64, q); A.out[q] = half(u, L, fp64, q); A.y[q] = half(p, L, fp64, q);
+            A.in[q] = half(p, L, fp64, q); A.out[q] = half(u, L, fp64, q); A.y[q] = half(yp, L, fp64, q);
         }
         A.a = -kappa; A.red_op = RED_PAP;
         CK(timed_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
+        const void* yu = clover_y(L, lk, fp64, u);
+        if (!yu) return fail(LGT_ECUDA, "clover apply failed");
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 2;
         for (int q = 0; q < 2; ++q) {
-            A.in[q] = half(u, L, fp64, q); A.y[q] = half(u, L, fp64, q);
+            A.in[q] = half(u, L, fp64, q); A.y[q] = half(yu, L, fp64, q);
             A.x[q] = half(x, L, fp64, q); A.r[q] = half(r, L, fp64, q); A.pv[q] = half(p, L, fp64, q);
         }
         A.a = -kappa; A.red_op = RED_RR;
@@ -661,10 +746,12 @@ static int true_residual(lgt_lattice* L, const Links& lk, bool eo, double kappa,
     } else {
         double2* Yf = cap ? L->cap_Y : L->u;
         TRY(dfull(L, lk, true, false, x, Yf, kappa));
+        const void* yY = clover_y(L, lk, true, Yf);
+        if (!yY) return fail(LGT_ECUDA, "clover apply failed");
         HopArgs A = hop_base(L, lk, true);
         A.parity = 2;
         for (int q = 0; q < 2; ++q) {
-            A.in[q] = half(Yf, L, true, q); A.y[q] = half(Yf, L, true, q);
+            A.in[q] = half(Yf, L, true, q); A.y[q] = half(yY, L, true, q);
             A.out[q] = half(res, L, true, q); A.pv[q] = half(b, L, true, q);
         }
         A.a = -kappa; A.red_op = RED_STORE; A.red_slot = 0;
@@ -856,6 +943,7 @@ static void add_stats(lgt_solve_stats* acc, const lgt_solve_stats& s) {
 extern "C" int lgt_cg_solve(lgt_lattice_t L, const double* b, double* x, double kappa, int even_odd,
                             const lgt_solver_params* sp, lgt_solve_stats* stats) {
     if (!L || !b || !x) return fail(LGT_EINVAL, "null argument");
+    if (L->thin.C64 && even_odd) return fail(LGT_EINVAL, "the clover term is attached: even-odd solve not available");
     if (b == x) return fail(LGT_EINVAL, "b and x must be distinct");
     return cg_core(L, L->thin, (const double2*)b, (double2*)x, kappa, even_odd != 0, sp, stats);
 }
@@ -1019,6 +1107,7 @@ extern "C" int lgt_cg_solve_multi(lgt_lattice_t L, int nrhs, const double* const
                                   const double* kappa, const lgt_solver_params* sp, lgt_solve_stats* stats) {
     if (!L || !b || !x || !kappa || !sp) return fail(LGT_EINVAL, "null argument");
     if (nrhs < 1 || nrhs > KMAX_RHS) return fail(LGT_EINVAL, "nrhs = %d outside 1..%d", nrhs, KMAX_RHS);
+    if (L->thin.C64) return fail(LGT_EINVAL, "the clover term is attached: even-odd solves are not available");
     if (sp->precision != LGT_FP64 && sp->precision != LGT_MIXED) return fail(LGT_EINVAL, "solver precision %d", sp->precision);
     if (!(sp->tol > 0) || sp->max_iter <= 0) return fail(LGT_EINVAL, "tol and max_iter must be positive");
     for (int k = 0; k < nrhs; ++k) {
@@ -1060,6 +1149,8 @@ static int check_action(const lgt_action_params* ap) {
     if (ap->n_stout < 0 || ap->n_stout > MAX_STOUT)
         return fail(LGT_EINVAL, "n_stout = %d outside 0..%d", ap->n_stout, MAX_STOUT);
     if (ap->stout_recompute < 0) return fail(LGT_EINVAL, "stout_recompute = %d", ap->stout_recompute);
+    if (ap->csw != 0.0 && ap->even_odd && ap->fermions)
+        return fail(LGT_EINVAL, "the clover term needs the full-lattice action (even_odd = 0)");
     if (ap->force_arith < LGT_ARITH_FP64 || ap->force_arith > LGT_ARITH_DF64)
         return fail(LGT_EINVAL, "force_arith = %d", ap->force_arith);
     return LGT_OK;
@@ -1076,15 +1167,27 @@ static int smear_to(lgt_lattice* L, const StoutPlan& P, double rho, double2** le
     return LGT_OK;
 }
 // links seen by the Dirac operator: thin, or the top stout level (+ its FP32 copy)
+// (+ the clover term of ap->csw built from them; lgt_set_clover's field is not used here)
 static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out) {
-    if (ap->n_stout == 0) { *out = L->thin; return LGT_OK; }
-    TRY(ensure_stout(L, ap->n_stout, ap->stout_recompute));
-    double2* top;
-    TRY(smear_to(L, stout_plan(ap->n_stout, ap->stout_recompute), ap->rho, &top));
-    CK(gauge_make12(L->stout_top12, top, L->g, L->st));
-    *out = Links{top, L->stout_top12};
+    Links lk{L->thin.U, L->thin.U12};
+    if (ap->n_stout > 0) {
+        TRY(ensure_stout(L, ap->n_stout, ap->stout_recompute));
+        double2* top;
+        TRY(smear_to(L, stout_plan(ap->n_stout, ap->stout_recompute), ap->rho, &top));
+        CK(gauge_make12(L->stout_top12, top, L->g, L->st));
+        lk = Links{top, L->stout_top12};
+    }
+    if (ap->fermions && ap->csw != 0.0) {
+        TRY(ensure_clover(L, false));
+        CK(clover_field(lk.U, L->g, clover_sigma(), ap->kappa, ap->csw, L->call_c64, L->call_c32, L->st));
+        lk.C64 = L->call_c64;
+        lk.C32 = L->call_c32;
+    }
+    *out = lk;
     return LGT_OK;
 }
+// the thin links without any clover term (what the gauge action and force see)
+static Links gauge_links(lgt_lattice* L) { return Links{L->thin.U, L->thin.U12}; }
 
 // ---------------------------------------------------------------- actions
 // S_f pieces after a solve chi = X (even half or full): eta = M chi into Y
@@ -1214,6 +1317,11 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
             CK(fermion_force_df(L->Udf, L->Xdf, L->Ydf, L->g, ap->kappa, coef, keep, out, L->st));
         } else CK(fermion_force(ferm_lk.U, L->X, L->Y, L->g, ap->kappa, coef, keep, form, out, L->st));
         keep = 1;
+        if (ferm_lk.C64) {   // clover part, FP64 from X = chi, Y = D chi (full lattice)
+            if (fp32 && !L->cap_valid) TRY(dfull(L, ferm_lk, true, false, L->X, L->Y, ap->kappa));
+            CK(clover_insertion(L->X, L->Y, L->g, clover_sigma(), ap->kappa, ap->csw, L->cins, L->st));
+            CK(clover_force(ferm_lk.U, L->cins, L->g, coef, 1, form, out, L->st));
+        }
     }
     if (!keep) CK(cudaMemsetAsync(out, 0, form == 0 ? mom_bytes(L) : links64(L), L->st));
     return LGT_OK;
@@ -1337,7 +1445,9 @@ extern "C" int lgt_force(lgt_lattice_t L, const lgt_action_params* ap, const dou
     if (form != LGT_FORCE_LIE && form != LGT_GRAD_G) return fail(LGT_EINVAL, "form %d", form);
     if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
     if (ap->n_stout == 0) {
-        TRY(force_on(L, L->thin, L->thin, ap, (const double2*)phi, sp, 1.0, 0, form, (double2*)F_out, stats));
+        Links fl;
+        TRY(fermion_links(L, ap, &fl));
+        TRY(force_on(L, gauge_links(L), fl, ap, (const double2*)phi, sp, 1.0, 0, form, (double2*)F_out, stats));
     } else {
         TRY(ensure_solver(L));
         TRY(ensure_md(L));
@@ -1353,7 +1463,11 @@ extern "C" int lgt_force(lgt_lattice_t L, const lgt_action_params* ap, const dou
 static int kick(lgt_lattice* L, double2* mom, double eps, const lgt_action_params* ap, const double2* phi,
                 const lgt_solver_params* sp, lgt_solve_stats* stats) {
     // the gauge action always sees thin links: only a fermion part goes through smearing
-    if (ap->n_stout == 0 || !ap->fermions) return force_on(L, L->thin, L->thin, ap, phi, sp, -eps, 1, 0, mom, stats);
+    if (ap->n_stout == 0 || !ap->fermions) {
+        Links fl;
+        TRY(fermion_links(L, ap, &fl));
+        return force_on(L, gauge_links(L), fl, ap, phi, sp, -eps, 1, 0, mom, stats);
+    }
     TRY(ensure_md(L));
     TRY(force_grad_stout(L, ap, phi, sp, L->G, stats));
     CK(grad_to_lie(L->F, L->G, L->thin.U, L->g, L->st));

@@ -1,0 +1,311 @@
+// lgt_clover.cu -- the clover (Sheikholeslami-Wohlert) term of the Wilson-Dirac
+// operator for the full-lattice pseudofermion action (a further discretisation the
+// paper names in Sec. IV without a formula):
+//   D_sw = 1 - kappa H + A,  A(x) = -kappa c_sw sum_{mu<nu} sigma_munu F_munu(x),
+//   sigma_munu = (i/2)[g_mu, g_nu],  F_munu = (Q_munu - Q_munu^+) / (8i),
+// Q_munu(x) the four plaquettes of the mu-nu plane at x, each traversed mu before
+// nu from x.  In the chiral basis sigma_munu commutes with g5 = diag(1,1,-1,-1), so
+// 1 + A is two 6x6 blocks per site (spins 0,1 and spins 2,3, colour fastest).
+//
+// Force: the clover part of delta S_f = -2 Re eta^+ (delta D) chi is
+// sum_{x,mu<nu} Re tr(M_munu(x) delta Q_munu(x)) with M = -i kappa c_sw (Lambda +
+// Lambda^+) / 4, Lambda_munu(x) = sum_{s,s'} (sigma_munu)_{s s'} chi_{s'}(x) eta_s(x)^+.
+// Its real-component gradient for U_m(y) gathers, for every plane (m, n), the two
+// plaquettes through the link and the insertion of M at each of their four
+// corners: with the rest of the plaquette after the link A1 A2 A3,
+//   G += (A1 A2 A3 M_0 + M_1 A1 A2 A3 + A1 M_2 A2 A3 + A1 A2 M_3 A3)^+ ,
+// M_j the insertion at corner j with the sign of the plaquette's orientation
+// relative to mu -> nu (mu < nu).
+#include "lgt_internal.h"
+#include "lgt_su3.cuh"
+
+namespace lgt {
+
+static inline int grid_for(long n) { return (int)((n + NT - 1) / NT); }
+
+// F_munu(x) (Hermitian) from the four leaves at x
+__device__ __forceinline__ dmat field_strength(const double2* U, const Geom& g, const int x[4], int mu, int nu) {
+    int xm[4] = {x[0], x[1], x[2], x[3]}, xn[4] = {x[0], x[1], x[2], x[3]};
+    shift(g, xm, mu, -1);
+    shift(g, xn, nu, -1);
+    int xp_mu[4] = {x[0], x[1], x[2], x[3]}, xp_nu[4] = {x[0], x[1], x[2], x[3]};
+    shift(g, xp_mu, mu, +1);
+    shift(g, xp_nu, nu, +1);
+    int xnm[4] = {xp_nu[0], xp_nu[1], xp_nu[2], xp_nu[3]};   // x + nu - mu
+    shift(g, xnm, mu, -1);
+    int xmn[4] = {xm[0], xm[1], xm[2], xm[3]};                // x - mu - nu
+    shift(g, xmn, nu, -1);
+    int xmp[4] = {xn[0], xn[1], xn[2], xn[3]};                // x - nu + mu
+    shift(g, xmp, mu, +1);
+    const dmat Umu = link_at(U, g, x, mu), Unu = link_at(U, g, x, nu);
+    // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    dmat Q = mul_nd(mul_nd(mul(Umu, link_at(U, g, xp_mu, nu)), link_at(U, g, xp_nu, mu)), Unu);
+    // leaf 2: U_nu(x) U_mu(x+nu-mu)^+ U_nu(x-mu)^+ U_mu(x-mu)
+    add_to(Q, mul(mul_nd(mul_nd(Unu, link_at(U, g, xnm, mu)), link_at(U, g, xm, nu)), link_at(U, g, xm, mu)));
+    // leaf 3: U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
+    add_to(Q, mul(mul(mul_dn(link_at(U, g, xm, mu), dag(link_at(U, g, xmn, nu))), link_at(U, g, xmn, mu)),
+                  link_at(U, g, xn, nu)));
+    // leaf 4: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
+    add_to(Q, mul_nd(mul(mul_dn(link_at(U, g, xn, nu), link_at(U, g, xn, mu)), link_at(U, g, xmp, nu)), Umu));
+    dmat F;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const dcx z = Q.e[a][b] - conj(Q.e[b][a]);
+            F.e[a][b] = {z.i * 0.125, -z.r * 0.125};   // z / (8i)
+        }
+    return F;
+}
+
+// plane p = (mu, nu), mu < nu, in the order (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
+__constant__ int PLANE_MU[6] = {0, 0, 0, 1, 1, 2};
+__constant__ int PLANE_NU[6] = {1, 2, 3, 2, 3, 3};
+
+// 1 + A as double2 [parity][72][Vh] (entry 36 c + 6 i + j of chiral block c) and the
+// FP32 copy float4 [parity][36][Vh] (entries 2k, 2k+1)
+__global__ void __launch_bounds__(NT) clover_field_kernel(const double2* U, Geom g, CloverSigma S, double coef,
+                                                          double2* C64, float4* C32) {
+    const int t = blockIdx.x * NT + threadIdx.x;
+    if (t >= 2 * g.Vh) return;
+    const int p = t >= g.Vh, i = t - p * g.Vh;
+    int x[4];
+    eo_coords(g, p, i, x);
+    dcx B[2][6][6];
+    for (int c = 0; c < 2; ++c)
+        for (int r = 0; r < 6; ++r)
+            for (int q = 0; q < 6; ++q) B[c][r][q] = {r == q ? 1.0 : 0.0, 0.0};
+#pragma unroll 1
+    for (int pl = 0; pl < 6; ++pl) {
+        const dmat F = field_strength(U, g, x, PLANE_MU[pl], PLANE_NU[pl]);
+        for (int c = 0; c < 2; ++c)
+            for (int s = 0; s < 2; ++s)
+                for (int u = 0; u < 2; ++u) {
+                    const double2 sg = S.s[pl][c][s][u];
+                    if (sg.x == 0.0 && sg.y == 0.0) continue;
+                    const dcx w = coef * dcx{sg.x, sg.y};
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) B[c][3 * s + a][3 * u + b] = cmad(B[c][3 * s + a][3 * u + b], w, F.e[a][b]);
+                }
+    }
+    double2* o64 = C64 + (size_t)p * 72 * g.Vh + i;
+    float4* o32 = C32 + (size_t)p * 36 * g.Vh + i;
+    for (int k = 0; k < 72; ++k) {
+        const dcx v = B[k / 36][(k % 36) / 6][k % 6];
+        o64[(size_t)k * g.Vh] = make_double2(v.r, v.i);
+    }
+    for (int k = 0; k < 36; ++k) {
+        const dcx v = B[(2 * k) / 36][((2 * k) % 36) / 6][(2 * k) % 6];
+        const dcx w = B[(2 * k + 1) / 36][((2 * k + 1) % 36) / 6][(2 * k + 1) % 6];
+        o32[(size_t)k * g.Vh] = make_float4((float)v.r, (float)v.i, (float)w.r, (float)w.i);
+    }
+}
+
+cudaError_t clover_field(const double2* U, const Geom& g, const CloverSigma& S, double kappa, double csw,
+                         double2* C64, float4* C32, cudaStream_t st) {
+    clover_field_kernel<<<grid_for(2L * g.Vh), NT, 0, st>>>(U, g, S, -kappa * csw, C64, C32);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// out = (1 + A) in on the sites of `parity` (0, 1 or 2 = both), spinor layout of the
+// precision; out may not alias in
+template <typename R> struct CloverIO;
+template <> struct CloverIO<double> {
+    static __device__ __forceinline__ void load(const void* f, int Vh, int i, dcx (&v)[12]) {
+        const double2* b = (const double2*)f + i;
+        for (int k = 0; k < 12; ++k) { const double2 z = __ldg(b + (size_t)k * Vh); v[k] = {z.x, z.y}; }
+    }
+    static __device__ __forceinline__ void store(void* f, int Vh, int i, const dcx (&v)[12]) {
+        double2* b = (double2*)f + i;
+        for (int k = 0; k < 12; ++k) b[(size_t)k * Vh] = make_double2(v[k].r, v[k].i);
+    }
+    static __device__ __forceinline__ dcx entry(const void* C, int Vh, int i, int k) {
+        const double2 z = __ldg((const double2*)C + (size_t)k * Vh + i);
+        return {z.x, z.y};
+    }
+};
+template <> struct CloverIO<float> {
+    static __device__ __forceinline__ void load(const void* f, int Vh, int i, dcx (&v)[12]) {
+        const float4* b = (const float4*)f + i;
+        for (int k = 0; k < 6; ++k) {
+            const float4 z = __ldg(b + (size_t)k * Vh);
+            v[2 * k] = {z.x, z.y};
+            v[2 * k + 1] = {z.z, z.w};
+        }
+    }
+    static __device__ __forceinline__ void store(void* f, int Vh, int i, const dcx (&v)[12]) {
+        float4* b = (float4*)f + i;
+        for (int k = 0; k < 6; ++k)
+            b[(size_t)k * Vh] = make_float4((float)v[2 * k].r, (float)v[2 * k].i, (float)v[2 * k + 1].r,
+                                            (float)v[2 * k + 1].i);
+    }
+    static __device__ __forceinline__ dcx entry(const void* C, int Vh, int i, int k) {
+        const float4 z = __ldg((const float4*)C + (size_t)(k / 2) * Vh + i);
+        return (k & 1) ? dcx{z.z, z.w} : dcx{z.x, z.y};
+    }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(NT) clover_apply_kernel(const void* C, const void* in, void* out, Geom g,
+                                                          int parity, size_t cstride, size_t fstride) {
+    const int t = blockIdx.x * NT + threadIdx.x;
+    const int n = parity == 2 ? 2 * g.Vh : g.Vh;
+    if (t >= n) return;
+    const int p = parity == 2 ? (t >= g.Vh) : parity, i = parity == 2 ? t - p * g.Vh : t;
+    const char* Cp = (const char*)C + p * cstride;
+    const size_t fo = parity == 2 ? p * fstride : 0;
+    dcx v[12], w[12];
+    CloverIO<R>::load((const char*)in + fo, g.Vh, i, v);
+    for (int c = 0; c < 2; ++c)
+        for (int r = 0; r < 6; ++r) {
+            dcx s = {0, 0};
+            for (int q = 0; q < 6; ++q) s = cmad(s, CloverIO<R>::entry(Cp, g.Vh, i, 36 * c + 6 * r + q), v[6 * c + q]);
+            w[6 * c + r] = s;
+        }
+    CloverIO<R>::store((char*)out + fo, g.Vh, i, w);
+}
+
+cudaError_t clover_apply(const void* C, const void* in, void* out, const Geom& g, int parity, bool fp64,
+                         cudaStream_t st) {
+    const int n = parity == 2 ? 2 * g.Vh : g.Vh;
+    if (fp64)
+        clover_apply_kernel<double><<<grid_for(n), NT, 0, st>>>(C, in, out, g, parity, (size_t)72 * g.Vh * 16,
+                                                                 (size_t)12 * g.Vh * 16);
+    else
+        clover_apply_kernel<float><<<grid_for(n), NT, 0, st>>>(C, in, out, g, parity, (size_t)36 * g.Vh * 16,
+                                                                (size_t)6 * g.Vh * 16);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// M_munu(x) = -i (kappa c_sw / 4) (Lambda + Lambda^+), Lambda_ab = sum_{s,t} sigma_{st} X_{t a} conj(Y_{s b}),
+// for X, Y full FP64 fields; M as double2 [parity][6 planes][9][Vh]
+__global__ void __launch_bounds__(NT) clover_insertion_kernel(const double2* X, const double2* Y, Geom g,
+                                                              CloverSigma S, double c, double2* Mout) {
+    const int t = blockIdx.x * NT + threadIdx.x;
+    if (t >= 2 * g.Vh) return;
+    const int p = t >= g.Vh, i = t - p * g.Vh;
+    const SpinorD Xs = load_spinor(X + (size_t)p * 12 * g.Vh, g.Vh, i);
+    const SpinorD Ys = load_spinor(Y + (size_t)p * 12 * g.Vh, g.Vh, i);
+    double2* o = Mout + (size_t)p * 54 * g.Vh + i;
+#pragma unroll 1
+    for (int pl = 0; pl < 6; ++pl) {
+        dmat Lam = zero3<double>();
+        for (int cb = 0; cb < 2; ++cb)
+            for (int s = 0; s < 2; ++s)
+                for (int u = 0; u < 2; ++u) {
+                    const double2 sg = S.s[pl][cb][s][u];
+                    if (sg.x == 0.0 && sg.y == 0.0) continue;
+                    const dcx w = {sg.x, sg.y};
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b)
+                            Lam.e[a][b] = cmad(Lam.e[a][b], w, Xs.c[2 * cb + u][a] * conj(Ys.c[2 * cb + s][b]));
+                }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                const dcx h = Lam.e[a][b] + conj(Lam.e[b][a]);
+                o[(size_t)(pl * 9 + 3 * a + b) * g.Vh] = make_double2(c * h.i, -c * h.r);   // -i c h
+            }
+    }
+}
+
+cudaError_t clover_insertion(const double2* X, const double2* Y, const Geom& g, const CloverSigma& S, double kappa,
+                             double csw, double2* M, cudaStream_t st) {
+    clover_insertion_kernel<<<grid_for(2L * g.Vh), NT, 0, st>>>(X, Y, g, S, 0.25 * kappa * csw, M);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ dmat insertion_at(const double2* M, const Geom& g, const int x[4], int pl, double sgn) {
+    const int lex = lex_of(g, x);
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const double2* b = M + (size_t)par * 54 * g.Vh + (lex >> 1);
+    dmat m;
+    for (int k = 0; k < 9; ++k) {
+        const double2 z = __ldg(b + (size_t)(pl * 9 + k) * g.Vh);
+        m.e[k / 3][k % 3] = {sgn * z.x, sgn * z.y};
+    }
+    return m;
+}
+__device__ __forceinline__ int plane_of(int a, int b) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? hi - 1 : (lo == 1 ? hi + 1 : 5);
+}
+
+// real-component gradient of the clover part for every link; form 0 writes Lie
+// components out = keep*out + coef*F_a (F_a = -Im tr(lambda^a U G^+) / 2), form 1
+// G-form out = keep*out + coef*G
+template <int FORM>
+__global__ void __launch_bounds__(NT) clover_force_kernel(const double2* U, const double2* M, Geom g, double coef,
+                                                          int keep, double2* out) {
+    int m, p, i;
+    if (!link_index(g, m, p, i)) return;
+    int y[4];
+    eo_coords(g, p, i, y);
+    dmat Gsum = zero3<double>();   // sum of the N (before the final ^+)
+    int ym[4] = {y[0], y[1], y[2], y[3]};
+    shift(g, ym, m, +1);
+#pragma unroll 1
+    for (int n = 0; n < 4; ++n) {
+        if (n == m) continue;
+        const int pl = plane_of(m, n);
+        const double s = m < n ? 1.0 : -1.0;
+        // plaquette above: corners y, y+m, y+m+n, y+n; A1 = U_n(y+m), A2 = U_m(y+n)^+, A3 = U_n(y)^+
+        {
+            int c2[4] = {ym[0], ym[1], ym[2], ym[3]};
+            shift(g, c2, n, +1);
+            int c3[4] = {y[0], y[1], y[2], y[3]};
+            shift(g, c3, n, +1);
+            const dmat A1 = link_at(U, g, ym, n);
+            const dmat A2 = dag(link_at(U, g, c3, m));
+            const dmat A3 = dag(link_at(U, g, y, n));
+            const dmat P12 = mul(A1, A2), P23 = mul(A2, A3), P123 = mul(P12, A3);
+            add_to(Gsum, mul(P123, insertion_at(M, g, y, pl, s)));
+            add_to(Gsum, mul(insertion_at(M, g, ym, pl, s), P123));
+            add_to(Gsum, mul(A1, mul(insertion_at(M, g, c2, pl, s), P23)));
+            add_to(Gsum, mul(mul(P12, insertion_at(M, g, c3, pl, s)), A3));
+        }
+        // plaquette below: corners y, y+m, y+m-n, y-n; B1 = U_n(y+m-n)^+, B2 = U_m(y-n)^+, B3 = U_n(y-n)
+        {
+            int c2[4] = {ym[0], ym[1], ym[2], ym[3]};
+            shift(g, c2, n, -1);
+            int c3[4] = {y[0], y[1], y[2], y[3]};
+            shift(g, c3, n, -1);
+            const dmat B1 = dag(link_at(U, g, c2, n));
+            const dmat B2 = dag(link_at(U, g, c3, m));
+            const dmat B3 = link_at(U, g, c3, n);
+            const dmat P12 = mul(B1, B2), P23 = mul(B2, B3), P123 = mul(P12, B3);
+            add_to(Gsum, mul(P123, insertion_at(M, g, y, pl, -s)));
+            add_to(Gsum, mul(insertion_at(M, g, ym, pl, -s), P123));
+            add_to(Gsum, mul(B1, mul(insertion_at(M, g, c2, pl, -s), P23)));
+            add_to(Gsum, mul(mul(P12, insertion_at(M, g, c3, pl, -s)), B3));
+        }
+    }
+    if (FORM == 0) {
+        // U G^+ with G = Gsum^+  ->  U Gsum
+        const dmat UG = mul(load_link(U, g.Vh, p, m, i), Gsum);
+        double c[8], f[8];
+        lie_im_tr(UG, c);
+        if (keep) load_mom(out, g.Vh, p, m, i, f);
+        for (int a = 0; a < 8; ++a) f[a] = (keep ? f[a] : 0.0) - 0.5 * coef * c[a];
+        store_mom(out, g.Vh, p, m, i, f);
+    } else {
+        dmat Go;
+        if (keep) Go = load_link(out, g.Vh, p, m, i);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                const dcx v = coef * conj(Gsum.e[b][a]);
+                Go.e[a][b] = keep ? Go.e[a][b] + v : v;
+            }
+        store_link(out, g.Vh, p, m, i, Go);
+    }
+}
+
+cudaError_t clover_force(const double2* U, const double2* M, const Geom& g, double coef, int keep, int form,
+                         double2* out, cudaStream_t st) {
+    if (form == 0) clover_force_kernel<0><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, M, g, coef, keep, out);
+    else clover_force_kernel<1><<<grid_for(8L * g.Vh), NT, 0, st>>>(U, M, g, coef, keep, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace lgt

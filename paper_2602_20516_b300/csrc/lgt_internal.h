@@ -196,6 +196,26 @@ cudaError_t gauge_force_df(const float4* Udf, const Geom& g, double beta, double
 cudaError_t fermion_force_df(const float4* Udf, const float4* Xdf, const float4* Ydf, const Geom& g, double kappa,
                              double coef, int keep, double2* out, cudaStream_t st);
 
+// ---------------------------------------------------------------- clover term (lgt_clover.cu)
+// sigma_munu = (i/2)[g_mu, g_nu] restricted to the chiral blocks: s[plane][block][row][col]
+// (planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3); block 0 = spins 0,1, block 1 = spins 2,3)
+struct CloverSigma {
+    double2 s[6][2][2][2];
+};
+// 1 + A, A = -kappa c_sw sum sigma F, from the FP64 links: C64 double2 [parity][72][Vh],
+// C32 float4 [parity][36][Vh]
+cudaError_t clover_field(const double2* U, const Geom& g, const CloverSigma& S, double kappa, double csw,
+                         double2* C64, float4* C32, cudaStream_t st);
+// out = (1 + A) in on parity 0 / 1 (half fields) or 2 (full fields)
+cudaError_t clover_apply(const void* C, const void* in, void* out, const Geom& g, int parity, bool fp64,
+                         cudaStream_t st);
+// insertion M = -i kappa c_sw (Lambda + Lambda^+)/4 per site and plane from full X, Y
+cudaError_t clover_insertion(const double2* X, const double2* Y, const Geom& g, const CloverSigma& S, double kappa,
+                             double csw, double2* M, cudaStream_t st);
+// clover part of the force: form 0 Lie (out = keep*out + coef*F), form 1 G form
+cudaError_t clover_force(const double2* U, const double2* M, const Geom& g, double coef, int keep, int form,
+                         double2* out, cudaStream_t st);
+
 // ---------------------------------------------------------------- stout (lgt_stout.cu)
 cudaError_t stout_forward(const double2* Uin, double2* Uout, const Geom& g, double rho, cudaStream_t st);
 // Gin = adjoint of one level applied to Gout, for the level whose input is Uin

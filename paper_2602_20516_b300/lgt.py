@@ -49,7 +49,8 @@ class SolveStats(C.Structure):
 class ActionParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("fermions", C.c_int),
                 ("even_odd", C.c_int), ("n_stout", C.c_int), ("rho", C.c_double),
-                ("stout_recompute", C.c_int), ("force_arith", C.c_int), ("c1", C.c_double)]
+                ("stout_recompute", C.c_int), ("force_arith", C.c_int), ("c1", C.c_double),
+                ("csw", C.c_double)]
 
 
 class HMCParams(C.Structure):
@@ -120,6 +121,7 @@ SIGNATURES = [
     ("lgt_unpack_momenta", _I, [_P, _P, _P]),
     ("lgt_pack_links_field", _I, [_P, _P, _P]),
     ("lgt_unpack_links_field", _I, [_P, _P, _P]),
+    ("lgt_set_clover", _I, [_P, _D, _D]),
     ("lgt_dslash", _I, [_P, _P, _P, _I, _I, _I, _D, _I]),
     ("lgt_cg_solve", _I, [_P, _P, _P, _D, _I, C.POINTER(SolverParams), C.POINTER(SolveStats)]),
     ("lgt_cg_solve_multi", _I, [_P, _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D), C.POINTER(SolverParams),
@@ -192,12 +194,13 @@ ARITH = {"fp64": 0, "fp32": 1, "df64": 2}
 
 
 def action_params(beta=0.0, kappa=0.0, fermions=True, even_odd=False, n_stout=0, rho=0.0,
-                  stout_recompute=False, force_arith="fp64", c1=0.0):
+                  stout_recompute=False, force_arith="fp64", c1=0.0, csw=0.0):
     """force_arith: arithmetic of Lie-form forces with the mixed solver ("fp64",
     "fp32" or "df64", the double-float FP32-pair format); c1: rectangle weight of the
-    gauge action (0 Wilson, -1/12 Symanzik, -0.331 Iwasaki, -1.4088 DBW2)."""
+    gauge action (0 Wilson, -1/12 Symanzik, -0.331 Iwasaki, -1.4088 DBW2); csw:
+    clover coefficient of the Wilson operator (full-lattice action only)."""
     return ActionParams(beta, kappa, int(fermions), int(even_odd), n_stout, rho, int(stout_recompute),
-                        ARITH[force_arith] if isinstance(force_arith, str) else int(force_arith), c1)
+                        ARITH[force_arith] if isinstance(force_arith, str) else int(force_arith), c1, csw)
 
 
 SEXTON_WEINGARTEN = 2
@@ -386,6 +389,10 @@ class Lattice:
         return c
 
     # ------------------------------------------------------------ operators
+    def set_clover(self, csw, kappa):
+        """Attach (csw != 0) or detach (csw = 0) the clover term for OP_D and full-lattice solves."""
+        check(lib().lgt_set_clover(self.h, csw, kappa))
+
     def dslash(self, inp, op=OP_D, out_parity=FULL, dagger=False, kappa=0.0, precision=FP64, out=None):
         if out is None:
             if op == OP_D:
