@@ -128,7 +128,11 @@ typedef struct {
 } lgt_action_params;
 
 typedef struct {
-    int precision;    /* LGT_FP64 or LGT_MIXED (FP32 inner CG, FP64 reliable updates) */
+    int precision;    /* LGT_FP64 or LGT_MIXED (FP32 inner CG, FP64 reliable updates; a
+                         breakdown of the FP32 recursion, <p,Ap> <= 0 from FP32 rounding near a
+                         nearly singular operator, restarts it from the FP64 residual, and
+                         two reliable updates that each fail to halve the residual hand the
+                         rest of the solve to FP64 CG) */
     double tol;       /* stop when |b - A x| / |b| <= tol (true residual, FP64) */
     int max_iter;     /* iteration cap -> LGT_ENOCONV */
     double delta;     /* mixed: reliable update when |r| < delta * max|r| since the last one */

@@ -147,6 +147,7 @@ struct lgt_lattice {
     struct {
         double2* hist[CHRONO_MAX];
         int n, head;
+        int last_iters;       // iterations of the last recorded solve
         double kappa;
         double2 *G, *g, *c;   // device: Gram matrix, projections, coefficients
         int* used;
@@ -762,9 +763,10 @@ static int true_residual(lgt_lattice* L, const Links& lk, bool eo, double kappa,
 
 // Chronological initial guess for Dhat^+Dhat x = b on even sites (kappa): with the
 // last N kept solutions v_i, x = sum c_i v_i with (V^+ A V) c = V^+ b.  The products
-// A v_i use the FP32 operator on all of them at once (a guess needs no more); the
-// solve that follows starts from the FP64 residual of x.  *used = false (x untouched)
-// when nothing of this operator is kept.
+// A v_i use the FP32 operator on all of them at once (a guess needs no more).  The
+// guess's residual is formed in FP64 by the solver: from the FP32 products it would be
+// wrong by ~eps32 cond(A) |b|, as large as the residual of a good guess.
+// *used = false (x untouched) when nothing of this operator is kept.
 static int chrono_guess(lgt_lattice* L, const Links& lk, const double2* b, double2* x, double kappa, int want,
                         bool* used) {
     *used = false;
@@ -814,10 +816,11 @@ static int chrono_guess(lgt_lattice* L, const Links& lk, const double2* b, doubl
     *used = true;
     return LGT_OK;
 }
-static int chrono_record(lgt_lattice* L, const double2* x, double kappa) {
+static int chrono_record(lgt_lattice* L, const double2* x, double kappa, int iters) {
     auto& C = L->ch;
     if (C.n > 0 && C.kappa != kappa) C.n = C.head = 0;
     C.kappa = kappa;
+    if (iters > 0) C.last_iters = iters;
     CK(cudaMemcpyAsync(C.hist[C.head], x, (size_t)12 * L->g.Vh * sizeof(double2), cudaMemcpyDeviceToDevice, L->st));
     C.head = (C.head + 1) % CHRONO_MAX;
     C.n = std::min(C.n + 1, CHRONO_MAX);
@@ -886,20 +889,74 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     double rr_true = rr0;
     int rc = LGT_OK;
     const bool record = eo && sp->chrono > 0;
+    // Near a nearly singular operator the FP32 recursion can break down (<p, Ap> <= 0 from
+    // FP32 rounding) or stop reducing the true residual; a chronological guess can then
+    // also carry an error in the lowest modes that the FP32 recursion cannot remove, so
+    // a guessed solve that breaks down, stalls or reduces its residual by less than 2x
+    // across a reliable update is redone once from x = 0.  A breakdown is handled as a
+    // reliable update that also restarts the search direction (at most 16 times); two
+    // reliable updates in a row that each fail to halve the true residual (including
+    // cycles ended after kMaxCycle iterations) end the FP32 iterations and the solve
+    // continues in FP64 CG from the current x and residual.
+    bool use32 = mixed;
+    bool guessed = guess;   // still iterating from a chronological guess
+    int breakdowns = 0, poor = 0, iters_at_update = 0;
+    double rr_prev = rr0;
+    // an FP32 cycle that runs this long without its stop test firing is ended by a
+    // reliable update as well (its progress is then judged like any other); a solve from
+    // a guess gets 1.5 times the iterations of the last recorded solve before it is
+    // redone from x = 0
+    constexpr int kMaxCycle = 1000;
+    const int guess_cap = std::max(64, (3 * L->ch.last_iters) / 2 + 32);
+    // back to x = 0, r = b (the zero-guess solve), keeping the iteration count
+    auto restart_from_zero = [&]() -> int {
+        CK(cudaMemsetAsync(x, 0, b64, L->st));
+        CK(cudaMemcpyAsync(L->r, b, b64, cudaMemcpyDeviceToDevice, L->st));
+        use32 = mixed;
+        if (mixed) {
+            CK(blas_d2f(L->r32, b, n, L->g.Vh, L->st));
+            CK(cudaMemcpyAsync(L->p32, L->r32, b32, cudaMemcpyDeviceToDevice, L->st));
+            CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
+        } else {
+            CK(cudaMemcpyAsync(L->p, b, b64, cudaMemcpyDeviceToDevice, L->st));
+        }
+        rr_true = rr_prev = bb;
+        poor = breakdowns = 0;
+        guessed = false;
+        hs->rr = hs->rr_max = bb;
+        hs->done = 0;
+        hs->nan = 0;
+        hs->delta2 = mixed ? sp->delta * sp->delta : 0.0;
+        TRY(push_scalars(L));
+        return LGT_OK;
+    };
     if (guess && rr0 <= target) {   // the guess already solves the system
         L->cap_valid = L->cap_X && L->cap_Y && (const double2*)x == L->cap_X;
-        if (record) TRY(chrono_record(L, x, kappa));
+        if (record) TRY(chrono_record(L, x, kappa, hs->iters));
     }
     for (; !(guess && rr0 <= target);) {
         for (int k = 0; k < K; ++k) {
-            if (mixed) TRY(cg_iteration(L, lk, false, eo, kappa, L->x32, L->r32, L->p32, L->u32, L->t32));
+            if (use32) TRY(cg_iteration(L, lk, false, eo, kappa, L->x32, L->r32, L->p32, L->u32, L->t32));
             else TRY(cg_iteration(L, lk, true, eo, kappa, x, L->r, L->p, L->u, L->t));
         }
         TRY(sync_scalars(L));
-        if (hs->nan) { rc = fail(LGT_ENAN, "non-finite value in CG after %d iterations", hs->iters); break; }
+        const bool breakdown = hs->nan != 0;
         const bool hit_cap = hs->iters >= sp->max_iter;
-        if (hs->done || hit_cap) {
-            if (mixed) {
+        const bool long_cycle = guessed ? hs->iters - iters_at_update >= guess_cap
+                                        : use32 && hs->iters - iters_at_update >= kMaxCycle;
+        // a guessed solve that runs into trouble is redone from x = 0 (once)
+        if (guessed && !hit_cap && (breakdown || long_cycle)) {
+            iters_at_update = hs->iters;
+            TRY(restart_from_zero());
+            continue;
+        }
+        if (breakdown && (!use32 || ++breakdowns > 16)) {
+            rc = fail(LGT_ENAN, "non-finite value in CG after %d iterations", hs->iters);
+            break;
+        }
+        if (hs->done || hit_cap || breakdown || long_cycle) {
+            iters_at_update = hs->iters;
+            if (use32) {
                 CK(blas_add_f2d(x, L->x32, n, L->g.Vh, L->st));
                 CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
             }
@@ -907,10 +964,14 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
             TRY(sync_scalars(L));
             rr_true = hs->slot[0];
             st.reliable_updates += 1;
-            if (!std::isfinite(rr_true)) { rc = fail(LGT_ENAN, "non-finite true residual"); break; }
+            if (!std::isfinite(rr_true)) {
+                if (guessed && !hit_cap) { TRY(restart_from_zero()); continue; }
+                rc = fail(LGT_ENAN, "non-finite true residual");
+                break;
+            }
             if (rr_true <= target) {
                 L->cap_valid = L->cap_X && L->cap_Y && (const double2*)x == L->cap_X;
-                if (record) TRY(chrono_record(L, x, kappa));
+                if (record) TRY(chrono_record(L, x, kappa, hs->iters));
                 break;
             }
             if (hit_cap) {
@@ -918,10 +979,25 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
                           std::sqrt(rr_true / bb));
                 break;
             }
-            if (mixed) CK(blas_d2f(L->r32, L->r, n, L->g.Vh, L->st));
+            const bool slow = rr_true > 0.25 * rr_prev;   // |r| shrank by less than 2x since the last update
+            if (guessed && slow) { TRY(restart_from_zero()); continue; }
+            if (use32) {
+                poor = slow ? poor + 1 : 0;
+                if (poor >= 2) {   // the FP32 iterations stopped making progress: FP64 from here
+                    use32 = false;
+                    CK(cudaMemcpyAsync(L->p, L->r, b64, cudaMemcpyDeviceToDevice, L->st));
+                }
+            }
+            rr_prev = rr_true;
+            if (use32) {
+                CK(blas_d2f(L->r32, L->r, n, L->g.Vh, L->st));
+                if (breakdown) CK(cudaMemcpyAsync(L->p32, L->r32, b32, cudaMemcpyDeviceToDevice, L->st));
+            }
             hs->rr = rr_true;
             hs->rr_max = rr_true;
             hs->done = 0;
+            hs->nan = 0;
+            hs->delta2 = use32 ? sp->delta * sp->delta : 0.0;
             TRY(push_scalars(L));
         }
     }

@@ -113,6 +113,23 @@ __device__ __forceinline__ dfmat df_mul(const dfmat& A, const dfmat& B) {
         }
     return C;
 }
+// C += op(A) op(B): the accumulators start from the entries of C (hi, lo)
+template <bool DA, bool DB>
+__device__ __forceinline__ void df_mul_acc(dfmat& C, const dfmat& A, const dfmat& B) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dacc re = {C.e[i][j].r.h, C.e[i][j].r.l}, im = {C.e[i][j].i.h, C.e[i][j].i.l};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const dfc& a = DA ? A.e[k][i] : A.e[i][k];
+                const dfc& b = DB ? B.e[j][k] : B.e[k][j];
+                cacc_mul<DA, DB>(re, im, a, b);
+            }
+            C.e[i][j] = {dacc_get(re), dacc_get(im)};
+        }
+}
 __device__ __forceinline__ void df_add_to(dfmat& A, const dfmat& B) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)

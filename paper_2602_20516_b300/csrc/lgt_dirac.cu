@@ -194,8 +194,11 @@ __device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk) {
 #ifndef LGT_HOP32_EPI_MIN_BLOCKS
 #define LGT_HOP32_EPI_MIN_BLOCKS 4
 #endif
+#ifndef LGT_HOP64_MIN_BLOCKS
+#define LGT_HOP64_MIN_BLOCKS 1
+#endif
 template <typename R, int EPI> constexpr int hop_min_blocks() {
-    return sizeof(R) == 4 ? (EPI == EPI_HOP ? LGT_HOP32_MIN_BLOCKS : LGT_HOP32_EPI_MIN_BLOCKS) : 1;
+    return sizeof(R) == 4 ? (EPI == EPI_HOP ? LGT_HOP32_MIN_BLOCKS : LGT_HOP32_EPI_MIN_BLOCKS) : LGT_HOP64_MIN_BLOCKS;
 }
 
 template <typename R, bool DAG, int EPI>

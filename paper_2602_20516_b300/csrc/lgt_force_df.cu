@@ -86,11 +86,11 @@ __global__ void __launch_bounds__(NT) gauge_force_df_kernel(const float4* U, Geo
         shift(g, xpmn, nu, -1);
         {
             const dfmat a = df_mul<false, true>(link_df_at(U, g, xp, nu), link_df_at(U, g, xpn, mu));
-            df_add_to(V, df_mul<false, true>(a, link_df_at(U, g, x, nu)));
+            df_mul_acc<false, true>(V, a, link_df_at(U, g, x, nu));
         }
         {
             const dfmat b = df_mul<true, true>(link_df_at(U, g, xpmn, nu), link_df_at(U, g, xmn, mu));
-            df_add_to(V, df_mul<false, false>(b, link_df_at(U, g, xmn, nu)));
+            df_mul_acc<false, false>(V, b, link_df_at(U, g, xmn, nu));
         }
     }
     const dfmat M = df_mul<false, false>(load_link_df(U, g.Vh, p, mu, i), V);

@@ -186,6 +186,7 @@ cudaError_t chrono_solve(const double2* G, const double2* g, double2* c, int N, 
 // x = sum_i c_i v_i (FP64 half fields)
 cudaError_t chrono_combine(double2* x, const double2* const* v, const double2* c, int N, int Vh, cudaStream_t st);
 
+
 // ---------------------------------------------------------------- double-float forces (lgt_force_df.cu)
 // FP64 links / full spinor field -> double-float copies (float4 per complex entry)
 cudaError_t links_to_df(float4* Udf, const double2* U, const Geom& g, cudaStream_t st);
