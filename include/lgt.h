@@ -254,6 +254,14 @@ int lgt_set_clover(lgt_lattice_t lat, double csw, double kappa);
 int lgt_dslash(lgt_lattice_t lat, const void *in, void *out, int op, int out_parity,
                int dagger, double kappa, int precision);
 
+/* Sweep order of the even-odd CG kernels (not in the paper; a B300 design choice):
+ * alternate = 1 (the default) makes every hop and vector-update launch of a CG
+ * iteration walk the sites in the direction opposite to the launch before it, so it
+ * starts on the sites whose links and fields the previous launch left in L2; 0 walks
+ * every launch forward.  The order of the sites only: results are bitwise the same. */
+int lgt_set_sweep_order(lgt_lattice_t lat, int alternate);
+
+
 /* Solve A x = b, A = Dhat^+ Dhat on even sites (even_odd = 1; b, x FP64 half
  * fields) or A = D^+ D (even_odd = 0; full FP64 fields), by CG from x = 0
  * (Eq. S3.4: the solve is not differentiated).  Synchronous. */
@@ -403,11 +411,13 @@ double lgt_clock(void);
 int lgt_measure_fp64_peak(double *flops, double *seconds);
 /* CUDA-event timing of the Wilson hop launches: start arms up to max_launches
  * event pairs (recorded on the launching stream around each hop launch of any
- * handle); stop waits for them and fills ms[10] / n[10] with the summed
- * durations (ms) and counts per kind = 5 * fp64 + epilogue (0 hop, 1 xpay,
- * 2 xpay + norm, 3 fused CG update, 4 true residual).  Launches shorter than
- * min_ms are only counted (n_short): inside a CG batch, hops enqueued after the
- * solver stopped return at entry and do no work.  Process-wide; not thread safe. */
+ * handle); stop waits for them and fills ms[LGT_TIMING_KINDS] / n[LGT_TIMING_KINDS]
+ * with the summed durations (ms) and counts per kind = 5 * fp64 + epilogue (0 hop,
+ * 1 xpay, 2 xpay + norm, 3 fused CG residual update, 4 true residual).  Launches
+ * shorter than min_ms are only counted (n_short): inside a CG batch, hops enqueued
+ * after the solver stopped return at entry and do no work.  Process-wide; not
+ * thread safe. */
+#define LGT_TIMING_KINDS 10
 int lgt_kernel_timing_start(int max_launches);
 int lgt_kernel_timing_stop(double min_ms, double *ms, int64_t *n, int64_t *n_short);
 /* Kernel launches the library enqueued on this thread since the last reset. */

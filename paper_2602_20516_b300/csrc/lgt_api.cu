@@ -155,6 +155,10 @@ struct lgt_lattice {
         unsigned* counter;
         long cap;
     } ch;
+    // alternate sweep order of the CG kernels (lgt_set_sweep_order) and the direction
+    // of the last launch
+    int alternate = 1;
+    int sweep = 0;
     // HMC / force workspace
     double2 *mom, *Ubak, *phi, *xi, *F, *G;
     bool have_md;
@@ -644,6 +648,12 @@ extern "C" int lgt_set_clover(lgt_lattice_t L, double csw, double kappa) {
     return LGT_OK;
 }
 
+extern "C" int lgt_set_sweep_order(lgt_lattice_t L, int alternate) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    L->alternate = alternate != 0;
+    return LGT_OK;
+}
+
 extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, int out_parity, int dagger,
                           double kappa, int precision) {
     if (!L || !in || !out) return fail(LGT_EINVAL, "null argument");
@@ -679,24 +689,29 @@ extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, in
 static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, double kappa, void* x, void* r, void* p,
                         void* u, void* t) {
     if (eo) {
+        // with alternate order on, every launch walks the sites in the direction opposite
+        // to the one before, so it starts on the sites whose data the previous launch
+        // left in L2
+        auto dir = [&]() { return L->alternate ? (L->sweep ^= 1) : 0; };
         HopArgs A = hop_base(L, lk, fp64);
         A.skip = 1;
-        A.parity = 1; A.in[0] = p; A.out[1] = t;
+        A.parity = 1; A.in[0] = p; A.out[1] = t; A.reverse = dir();
         CK(timed_hop(A, fp64, false, EPI_HOP, L->st));
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 0; A.in[1] = t; A.out[0] = u; A.y[0] = p; A.a = -kappa * kappa; A.red_op = RED_PAP;
+        A.reverse = dir();
         CK(timed_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
         A = hop_base(L, lk, fp64);
         A.skip = 1;
-        A.parity = 1; A.in[0] = u; A.out[1] = t;
+        A.parity = 1; A.in[0] = u; A.out[1] = t; A.reverse = dir();
         CK(timed_hop(A, fp64, true, EPI_HOP, L->st));
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 0; A.in[1] = t; A.y[0] = u; A.a = -kappa * kappa; A.red_op = RED_RR;
-        A.x[0] = x; A.r[0] = r; A.pv[0] = p;
+        A.r[0] = r; A.reverse = dir();
         CK(timed_hop(A, fp64, true, EPI_CG, L->st));
-        CK(blas_cg_p_update(p, r, L->g.Vh, L->g.Vh, fp64, red(L), L->st));
+        CK(blas_cg_p_update(p, r, x, L->g.Vh, L->g.Vh, fp64, red(L), L->st, dir() != 0));
     } else {
         const void* yp = clover_y(L, lk, fp64, p);
         if (!yp) return fail(LGT_ECUDA, "clover apply failed");
@@ -715,11 +730,11 @@ static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, dou
         A.parity = 2;
         for (int q = 0; q < 2; ++q) {
             A.in[q] = half(u, L, fp64, q); A.y[q] = half(yu, L, fp64, q);
-            A.x[q] = half(x, L, fp64, q); A.r[q] = half(r, L, fp64, q); A.pv[q] = half(p, L, fp64, q);
+            A.r[q] = half(r, L, fp64, q);
         }
         A.a = -kappa; A.red_op = RED_RR;
         CK(timed_hop(A, fp64, true, EPI_CG, L->st));
-        CK(blas_cg_p_update(p, r, 2 * L->g.Vh, L->g.Vh, fp64, red(L), L->st));
+        CK(blas_cg_p_update(p, r, x, 2 * L->g.Vh, L->g.Vh, fp64, red(L), L->st));
     }
     return LGT_OK;
 }
@@ -1074,7 +1089,7 @@ static int cg_iteration_multi(lgt_lattice* L, int n, const int* sys, const doubl
     for (int j = 0; j < n; ++j) {
         const int k = sys[j];
         A.in[j] = W.t32[k]; A.y[j] = W.u32[k]; A.a[j] = -kappa[k] * kappa[k];
-        A.x[j] = W.x32[k]; A.r[j] = W.r32[k]; A.pv[j] = W.p32[k];
+        A.r[j] = W.r32[k];
     }
     CK(launch_hop_multi(A, false, true, EPI_CG, L->st));
     PUpdateM P;
@@ -1082,7 +1097,7 @@ static int cg_iteration_multi(lgt_lattice* L, int n, const int* sys, const doubl
     P.nrhs = n;
     for (int j = 0; j < n; ++j) {
         const int k = sys[j];
-        P.p[j] = W.p32[k]; P.r[j] = W.r32[k];
+        P.p[j] = W.p32[k]; P.r[j] = W.r32[k]; P.x[j] = W.x32[k];
         P.red[j] = RedArgs{W.s + k, W.partials[k], (unsigned*)((char*)W.counter + 64 * k), L->n_partials};
     }
     CK(blas_cg_p_update_multi(P, L->g.Vh, false, L->st));
@@ -1714,8 +1729,8 @@ extern "C" int lgt_kernel_timing_start(int max_launches) {
 
 extern "C" int lgt_kernel_timing_stop(double min_ms, double* ms, int64_t* n, int64_t* n_short) {
     g_kt.on = false;
-    double acc[10] = {0};
-    int64_t cnt[10] = {0}, nshort = 0;
+    double acc[LGT_TIMING_KINDS] = {0};
+    int64_t cnt[LGT_TIMING_KINDS] = {0}, nshort = 0;
     for (size_t k = 0; k + 1 < g_kt.used; k += 2) {
         CK(cudaEventSynchronize(g_kt.ev[k + 1]));
         float t = 0.f;
@@ -1729,7 +1744,7 @@ extern "C" int lgt_kernel_timing_stop(double min_ms, double* ms, int64_t* n, int
         cnt[kind] += 1;
     }
     g_kt.used = 0;
-    for (int k = 0; k < 10; ++k) {
+    for (int k = 0; k < LGT_TIMING_KINDS; ++k) {
         if (ms) ms[k] = acc[k];
         if (n) n[k] = cnt[k];
     }

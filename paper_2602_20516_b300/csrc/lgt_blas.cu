@@ -66,7 +66,19 @@ cudaError_t blas_redot(const double2* a, const double2* b, int n, int Vh, const 
     return cudaGetLastError();
 }
 
-// p = r + beta p over the flat element array; the last block moves done 1 -> 2
+// x += alpha p, then p = r + beta p over the flat element array; the last block
+// moves done 1 -> 2
+__device__ __forceinline__ void axpy(double2& x, double2 p, double a) {
+    x.x = fma(a, p.x, x.x);
+    x.y = fma(a, p.y, x.y);
+}
+__device__ __forceinline__ void axpy(float4& x, float4 p, double ad) {
+    const float a = (float)ad;
+    x.x = fmaf(a, p.x, x.x);
+    x.y = fmaf(a, p.y, x.y);
+    x.z = fmaf(a, p.z, x.z);
+    x.w = fmaf(a, p.w, x.w);
+}
 __device__ __forceinline__ void xpby(double2& p, double2 r, double b) {
     p.x = fma(b, p.x, r.x);
     p.y = fma(b, p.y, r.y);
@@ -80,11 +92,14 @@ __device__ __forceinline__ void xpby(float4& p, float4 r, double bd) {
 }
 
 template <typename T>
-__device__ __forceinline__ void p_update_body(T* p, const T* r, long ne, const RedArgs& R, int blk, int nblk) {
+__device__ __forceinline__ void p_update_body(T* p, const T* r, T* x, long ne, const RedArgs& R, int blk,
+                                              int nblk) {
     if (R.s->done >= 2) return;
     const long e = (long)blk * NT + threadIdx.x;
     if (e < ne) {
-        T pv = p[e];
+        T pv = p[e], xv = x[e];
+        axpy(xv, pv, R.s->alpha);
+        x[e] = xv;
         xpby(pv, __ldg(r + e), R.s->beta);
         p[e] = pv;
     }
@@ -103,8 +118,42 @@ __device__ __forceinline__ void p_update_body(T* p, const T* r, long ne, const R
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) p_update_kernel(T* p, const T* r, long ne, RedArgs R) {
-    p_update_body<T>(p, r, ne, R, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(NT) p_update_kernel(T* p, const T* r, T* x, long ne, RedArgs R) {
+    p_update_body<T>(p, r, x, ne, R, blockIdx.x, gridDim.x);
+}
+
+// The same on one half field ([NC][Vh]) with a thread per site over its NC components,
+// so that a block touches whole sites: block b works on site block nblk - 1 - b when
+// reverse is set (the order of the sites only; the values are the same).
+template <typename T, int NC>
+__global__ void __launch_bounds__(NT) p_update_sites_kernel(T* p, const T* r, T* x, int Vh, RedArgs R, int reverse) {
+    if (R.s->done >= 2) return;
+    const int blk = reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int i = blk * NT + threadIdx.x;
+    if (i < Vh) {
+        const double a = R.s->alpha, b = R.s->beta;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const size_t e = (size_t)k * Vh + i;
+            T pv = p[e], xv = x[e];
+            axpy(xv, pv, a);
+            x[e] = xv;
+            xpby(pv, __ldg(r + e), b);
+            p[e] = pv;
+        }
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned prev = atomicAdd(R.counter, 1u);
+        last = (prev == (unsigned)gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        *R.counter = 0u;
+        if (R.s->done == 1) R.s->done = 2;
+    }
 }
 
 template <typename T>
@@ -117,7 +166,7 @@ __global__ void __launch_bounds__(NT) p_update_batch_kernel(const BatchAxpy* __r
         else hi = mid - 1;
     }
     const BatchAxpy& e = d[lo];
-    p_update_body<T>((T*)e.p, (const T*)e.r, e.ne, e.red, b - e.first, e.nblk);
+    p_update_body<T>((T*)e.p, (const T*)e.r, (T*)e.x, e.ne, e.red, b - e.first, e.nblk);
 }
 
 cudaError_t launch_p_update_batch(const BatchAxpy* d, int n, int total_blocks, bool fp64, cudaStream_t st) {
@@ -132,7 +181,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) p_update_multi_kernel(PUpdateM P, long ne) {
     const int k = blockIdx.y;
     if (k >= P.nrhs) return;
-    p_update_body<T>((T*)P.p[k], (const T*)P.r[k], ne, P.red[k], blockIdx.x, gridDim.x);
+    p_update_body<T>((T*)P.p[k], (const T*)P.r[k], (T*)P.x[k], ne, P.red[k], blockIdx.x, gridDim.x);
 }
 cudaError_t blas_cg_p_update_multi(const PUpdateM& P, int n, bool fp64, cudaStream_t st) {
     if (P.nrhs < 1 || P.nrhs > KMAX_RHS) return cudaErrorInvalidValue;
@@ -144,15 +193,22 @@ cudaError_t blas_cg_p_update_multi(const PUpdateM& P, int n, bool fp64, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t blas_cg_p_update(void* p, const void* r, int n, int Vh, bool fp64, const RedArgs& R,
-                             cudaStream_t st) {
-    (void)Vh;
-    if (fp64) {
+cudaError_t blas_cg_p_update(void* p, const void* r, void* x, int n, int Vh, bool fp64, const RedArgs& R,
+                             cudaStream_t st, bool reverse) {
+    const int rev = reverse ? 1 : 0;
+    if (n == Vh) {   // one half field: site blocks
+        if (fp64)
+            p_update_sites_kernel<double2, 12><<<grid_for(n), NT, 0, st>>>((double2*)p, (const double2*)r,
+                                                                          (double2*)x, Vh, R, rev);
+        else
+            p_update_sites_kernel<float4, 6><<<grid_for(n), NT, 0, st>>>((float4*)p, (const float4*)r, (float4*)x,
+                                                                        Vh, R, rev);
+    } else if (fp64) {
         long ne = (long)n * 12;
-        p_update_kernel<double2><<<grid_for(ne), NT, 0, st>>>((double2*)p, (const double2*)r, ne, R);
+        p_update_kernel<double2><<<grid_for(ne), NT, 0, st>>>((double2*)p, (const double2*)r, (double2*)x, ne, R);
     } else {
         long ne = (long)n * 6;
-        p_update_kernel<float4><<<grid_for(ne), NT, 0, st>>>((float4*)p, (const float4*)r, ne, R);
+        p_update_kernel<float4><<<grid_for(ne), NT, 0, st>>>((float4*)p, (const float4*)r, (float4*)x, ne, R);
     }
     count_launch();
     return cudaGetLastError();

@@ -342,6 +342,19 @@ __device__ __forceinline__ void apply_reduce_op(Scalars* s, int op, int slot, do
     }
 }
 
+// Sum of partials[0 .. n) by the whole block in a fixed order (result in thread 0):
+// eight independent loads in flight per thread, the same result on every run.
+__device__ __forceinline__ double ordered_sum(const double* partials, int n) {
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < n; k += 8 * NT) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (k + j * NT < n) a[j] += __ldcg(partials + k + j * NT);
+    }
+    const double acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    return block_sum(acc);
+}
+
 // Deterministic grid reduction over the nblk blocks of one problem (blk = this
 // block's index among them): each block stores its partial, the last block to
 // finish sums all partials in index order and applies `op` to the scalars.
@@ -357,16 +370,7 @@ __device__ __forceinline__ void grid_reduce(double block_partial, double* partia
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // eight independent loads in flight per thread (a fixed summation order, so the
-    // result is the same on every run)
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int k = threadIdx.x; k < nblk; k += 8 * NT) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (k + j * NT < nblk) a[j] += __ldcg(partials + k + j * NT);
-    }
-    double acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    acc = block_sum(acc);
+    const double acc = ordered_sum(partials, nblk);
     if (threadIdx.x == 0) {
         *counter = 0u;
         apply_reduce_op(s, op, slot, acc);

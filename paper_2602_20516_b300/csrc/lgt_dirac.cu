@@ -9,8 +9,8 @@
 // component (site-major SoA), so every load and store is a coalesced 128-bit access.
 //
 // Epilogues fuse the CG vector work into the last hop of an operator
-// application: xpay (y + a H in), its squared norm, and the CG update
-// x += alpha p, r -= alpha A p with |r|^2, or the true residual b - A x.
+// application: xpay (y + a H in), its squared norm, and the CG residual update
+// r -= alpha A p with |r|^2, or the true residual b - A x.
 #include "lgt_internal.h"
 #include "lgt_spin.cuh"
 
@@ -46,37 +46,43 @@ __device__ __forceinline__ void mult(const mat3<R>& M, const cx<R> (&h)[2][3], c
         }
 }
 
-template <int MU, int SF, int SB, typename R>
-__device__ __forceinline__ void hop_dir(const HopArgs& A, int p, int lex, const int (&x)[4],
-                                        int i, cx<R> (&out)[4][3]) {
+// Input half field of a hop, read through the read-only path: load(j) is the spinor
+// of half-field site j.
+template <typename R> struct PlainIn {
+    const typename Prec<R>::T* f;
+    int Vh;
+    __device__ __forceinline__ typename Prec<R>::S load(int j) const { return load_spinor(f, Vh, j); }
+};
+template <int MU, int SF, int SB, typename R, typename IN>
+__device__ __forceinline__ void hop_dir(const void* U, const Geom& g, const IN& in, int p, int lex,
+                                        const int (&x)[4], int i, cx<R> (&out)[4][3]) {
     using P = Prec<R>;
-    const int Vh = A.g.Vh;
-    const typename P::T* in = (const typename P::T*)A.in[1 - p];
+    const int Vh = g.Vh;
     // forward: b (1 + SF g) U_mu(x) psi(x+mu)
     {
-        int j = nb_lex(A.g, lex, x, MU, +1) >> 1;
-        typename P::S s = load_spinor(in, Vh, j);
+        int j = nb_lex(g, lex, x, MU, +1) >> 1;
+        typename P::S s = in.load(j);
         cx<R> h[2][3], uh[2][3];
         project<MU, SF>(s.c, h);
-        if (MU == 3 && x[3] == A.g.L[3] - 1) {
+        if (MU == 3 && x[3] == g.L[3] - 1) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) { h[0][c] = -h[0][c]; h[1][c] = -h[1][c]; }
         }
-        mat3<R> M = P::link(A.U, Vh, p, MU, i);
+        mat3<R> M = P::link(U, Vh, p, MU, i);
         mult<false>(M, h, uh);
         accumulate<MU, SF>(out, uh);
     }
     // backward: b (1 + SB g) U_mu(x-mu)^+ psi(x-mu)
     {
-        int j = nb_lex(A.g, lex, x, MU, -1) >> 1;
-        typename P::S s = load_spinor(in, Vh, j);
+        int j = nb_lex(g, lex, x, MU, -1) >> 1;
+        typename P::S s = in.load(j);
         cx<R> h[2][3], uh[2][3];
         project<MU, SB>(s.c, h);
         if (MU == 3 && x[3] == 0) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) { h[0][c] = -h[0][c]; h[1][c] = -h[1][c]; }
         }
-        mat3<R> M = P::link(A.U, Vh, 1 - p, MU, j);
+        mat3<R> M = P::link(U, Vh, 1 - p, MU, j);
         mult<true>(M, h, uh);
         accumulate<MU, SB>(out, uh);
     }
@@ -94,6 +100,22 @@ template <typename R> __device__ __forceinline__ double sq(const cx<R> (&v)[4][3
     return (double)acc;
 }
 
+// the 8 hops into output site (p, i) at coordinates x, lexicographic index lex
+template <typename R, bool DAG, typename IN>
+__device__ __forceinline__ void hop_accum(const void* U, const Geom& g, const IN& in, int p, int lex,
+                                          const int (&x)[4], int i, cx<R> (&out)[4][3]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[a][c] = {0, 0};
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    hop_dir<0, SF, SB, R>(U, g, in, p, lex, x, i, out);
+    hop_dir<1, SF, SB, R>(U, g, in, p, lex, x, i, out);
+    hop_dir<2, SF, SB, R>(U, g, in, p, lex, x, i, out);
+    hop_dir<3, SF, SB, R>(U, g, in, p, lex, x, i, out);
+}
+
 // The work of one output site t (t < n): accumulate the 8 hops, apply the epilogue
 // and return this site's contribution to the epilogue's reduction.
 template <typename R, bool DAG, int EPI>
@@ -107,16 +129,7 @@ __device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
     int x[4];
     int lex = eo_coords(A.g, p, i, x);
     cx<R> out[4][3];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) out[a][c] = {0, 0};
-    constexpr int SF = DAG ? +1 : -1;
-    constexpr int SB = -SF;
-    hop_dir<0, SF, SB, R>(A, p, lex, x, i, out);
-    hop_dir<1, SF, SB, R>(A, p, lex, x, i, out);
-    hop_dir<2, SF, SB, R>(A, p, lex, x, i, out);
-    hop_dir<3, SF, SB, R>(A, p, lex, x, i, out);
+    hop_accum<R, DAG>(A.U, A.g, PlainIn<R>{(const T*)A.in[1 - p], A.g.Vh}, p, lex, x, i, out);
     const R a = (R)A.a;
     const int Vh = A.g.Vh;
     if (EPI == EPI_HOP) {
@@ -144,21 +157,17 @@ __device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
             store_spinor((T*)A.out[p], Vh, i, o);
             if (EPI == EPI_XPAY_NORM) red = sq<R>(o.c);
         } else if (EPI == EPI_CG) {
-            // o = A p at this site: x += alpha p, r -= alpha A p, red = |r|^2
+            // o = A p at this site: r -= alpha A p, red = |r|^2 (x += alpha p is left to
+            // the p update, which reads p anyway)
             const R alpha = (R)A.s->alpha;
-            typename P::S xv = load_spinor((const T*)A.x[p], Vh, i);
             typename P::S rv = load_spinor((const T*)A.r[p], Vh, i);
-            typename P::S pv = load_spinor((const T*)A.pv[p], Vh, i);
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    xv.c[s][c].r = fma(alpha, pv.c[s][c].r, xv.c[s][c].r);
-                    xv.c[s][c].i = fma(alpha, pv.c[s][c].i, xv.c[s][c].i);
                     rv.c[s][c].r = fma(-alpha, o.c[s][c].r, rv.c[s][c].r);
                     rv.c[s][c].i = fma(-alpha, o.c[s][c].i, rv.c[s][c].i);
                 }
-            store_spinor((T*)A.x[p], Vh, i, xv);
             store_spinor((T*)A.r[p], Vh, i, rv);
             red = sq<R>(rv.c);
         } else {  // EPI_RESID: out = b - A x, b in pv
@@ -203,7 +212,7 @@ template <typename R, int EPI> constexpr int hop_min_blocks() {
 
 template <typename R, bool DAG, int EPI>
 __global__ void __launch_bounds__(NT, (hop_min_blocks<R, EPI>())) hop_kernel(HopArgs A) {
-    hop_body<R, DAG, EPI>(A, blockIdx.x, gridDim.x);
+    hop_body<R, DAG, EPI>(A, A.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x, gridDim.x);
 }
 
 // Many independent problems (lattices of any size) in one launch: block b runs
@@ -376,19 +385,14 @@ __global__ void __launch_bounds__(NT, (K == 1 ? 4 : (K == 2 ? 3 : 2))) hop_multi
                     if (EPI == EPI_XPAY_NORM) red[k] = sq<R>(o.c);
                 } else {  // EPI_CG
                     const R alpha = (R)A.s[k]->alpha;
-                    typename P::S xv = load_spinor((const T*)A.x[k], Vh, i);
                     typename P::S rv = load_spinor((const T*)A.r[k], Vh, i);
-                    const typename P::S pv = load_spinor((const T*)A.pv[k], Vh, i);
 #pragma unroll
                     for (int s = 0; s < 4; ++s)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            xv.c[s][c].r = fma(alpha, pv.c[s][c].r, xv.c[s][c].r);
-                            xv.c[s][c].i = fma(alpha, pv.c[s][c].i, xv.c[s][c].i);
                             rv.c[s][c].r = fma(-alpha, o.c[s][c].r, rv.c[s][c].r);
                             rv.c[s][c].i = fma(-alpha, o.c[s][c].i, rv.c[s][c].i);
                         }
-                    store_spinor((T*)A.x[k], Vh, i, xv);
                     store_spinor((T*)A.r[k], Vh, i, rv);
                     red[k] = sq<R>(rv.c);
                 }

@@ -18,9 +18,8 @@ struct HopArgs {
     const void* in[2];
     void* out[2];
     const void* y[2];     // xpay addend (same parity as the output)
-    void* x[2];           // EPI_CG: solution
     void* r[2];           // EPI_CG: residual
-    const void* pv[2];    // EPI_CG: search direction;  EPI_RESID: right-hand side
+    const void* pv[2];    // EPI_RESID: right-hand side
     double a;             // coefficient of H in
     Geom g;
     int parity;
@@ -30,6 +29,7 @@ struct HopArgs {
     int red_op, red_slot;
     int skip;             // 1: return at once when the solver scalars say done
     int red_capacity;     // entries of partials (reducing epilogues need one per block)
+    int reverse;          // 1: block b works on site block nblk - 1 - b (same results)
 };
 
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st);
@@ -52,9 +52,7 @@ struct HopArgsM {
     const void* in[KMAX_RHS];   // half fields of parity 1 - parity
     void* out[KMAX_RHS];
     const void* y[KMAX_RHS];
-    void* x[KMAX_RHS];
     void* r[KMAX_RHS];
-    const void* pv[KMAX_RHS];
     double a[KMAX_RHS];
     Scalars* s[KMAX_RHS];
     double* partials[KMAX_RHS];
@@ -92,22 +90,27 @@ cudaError_t blas_zero(void* f, size_t bytes, cudaStream_t st);
 cudaError_t blas_norm2(const void* a, int n, int Vh, bool fp64, const RedArgs& R, int slot, cudaStream_t st);
 // Re <a, b> -> slot   (FP64 fields)
 cudaError_t blas_redot(const double2* a, const double2* b, int n, int Vh, const RedArgs& R, int slot, cudaStream_t st);
-// p = r + beta p  (beta from scalars), skipped once done >= 2; marks done 1 -> 2
-cudaError_t blas_cg_p_update(void* p, const void* r, int n, int Vh, bool fp64, const RedArgs& R, cudaStream_t st);
+// x += alpha p, then p = r + beta p  (alpha, beta from scalars), skipped once
+// done >= 2; marks done 1 -> 2.  n == Vh (one half field): a thread per site, and
+// reverse walks the site blocks from the end
+cudaError_t blas_cg_p_update(void* p, const void* r, void* x, int n, int Vh, bool fp64, const RedArgs& R,
+                             cudaStream_t st, bool reverse = false);
 // the same for many problems in one launch (each with its own scalars and counter)
 struct BatchAxpy {
     void* p;
     const void* r;
+    void* x;
     long ne;         // elements (double2 for FP64, float4 for FP32)
     RedArgs red;
     int first, nblk;
 };
 cudaError_t launch_p_update_batch(const BatchAxpy* d_desc, int n, int total_blocks, bool fp64, cudaStream_t st);
-// p_k = r_k + beta_k p_k for nrhs systems of n sites each (one launch, blockIdx.y = k),
-// each with its own scalars and counter, as blas_cg_p_update
+// x_k += alpha_k p_k, p_k = r_k + beta_k p_k for nrhs systems of n sites each (one
+// launch, blockIdx.y = k), each with its own scalars and counter, as blas_cg_p_update
 struct PUpdateM {
     void* p[KMAX_RHS];
     const void* r[KMAX_RHS];
+    void* x[KMAX_RHS];
     RedArgs red[KMAX_RHS];
     int nrhs;
 };

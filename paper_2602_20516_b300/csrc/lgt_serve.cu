@@ -303,14 +303,14 @@ int batch_iterations(lgt_server* S, bool fp64, int K) {
         s3.parity = 1; s3.in[0] = u; s3.out[1] = t;
         HopArgs s4 = a;
         s4.parity = 0; s4.in[1] = t; s4.y[0] = u; s4.a = -k2; s4.red_op = RED_RR;
-        s4.x[0] = x; s4.r[0] = r; s4.pv[0] = p;
+        s4.r[0] = r;
         h[0 * S->max_active + n] = BatchHop{s1, total, nb};
         h[1 * S->max_active + n] = BatchHop{s2, total, nb};
         h[2 * S->max_active + n] = BatchHop{s3, total, nb};
         h[3 * S->max_active + n] = BatchHop{s4, total, nb};
         const long ne = (long)G.g.Vh * (fp64 ? 12 : 6);
         const int nbp = (int)((ne + NT - 1) / NT);
-        ha[n] = BatchAxpy{p, r, ne, RedArgs{S->s + R->slot, R->partials, R->counter, nblk(G.g) + 64}, total_p, nbp};
+        ha[n] = BatchAxpy{p, r, x, ne, RedArgs{S->s + R->slot, R->partials, R->counter, nblk(G.g) + 64}, total_p, nbp};
         total += nb;
         total_p += nbp;
         ++n;

@@ -122,6 +122,7 @@ SIGNATURES = [
     ("lgt_pack_links_field", _I, [_P, _P, _P]),
     ("lgt_unpack_links_field", _I, [_P, _P, _P]),
     ("lgt_set_clover", _I, [_P, _D, _D]),
+    ("lgt_set_sweep_order", _I, [_P, _I]),
     ("lgt_dslash", _I, [_P, _P, _P, _I, _I, _I, _D, _I]),
     ("lgt_cg_solve", _I, [_P, _P, _P, _D, _I, C.POINTER(SolverParams), C.POINTER(SolveStats)]),
     ("lgt_cg_solve_multi", _I, [_P, _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D), C.POINTER(SolverParams),
@@ -222,17 +223,18 @@ def kernel_timing_start(max_launches=65536):
 
 
 HOP_EPILOGUES = ["hop", "xpay", "xpay_norm", "cg_update", "residual"]
+TIMING_KINDS = 10   # LGT_TIMING_KINDS
 
 
 def kernel_timing_stop(min_ms=0.0):
     """Per hop kind since kernel_timing_start: ({(precision, epilogue): (ms, count)},
     n_short); launches shorter than min_ms are only counted in n_short."""
-    ms = (C.c_double * 10)()
-    n = (C.c_int64 * 10)()
+    ms = (C.c_double * TIMING_KINDS)()
+    n = (C.c_int64 * TIMING_KINDS)()
     short = C.c_int64()
     check(lib().lgt_kernel_timing_stop(min_ms, ms, n, C.byref(short)))
     out = {}
-    for k in range(10):
+    for k in range(TIMING_KINDS):
         if n[k]:
             out[("fp64" if k >= 5 else "fp32", HOP_EPILOGUES[k % 5])] = (ms[k], n[k])
     return out, short.value
@@ -392,6 +394,10 @@ class Lattice:
     def set_clover(self, csw, kappa):
         """Attach (csw != 0) or detach (csw = 0) the clover term for OP_D and full-lattice solves."""
         check(lib().lgt_set_clover(self.h, csw, kappa))
+
+    def set_sweep_order(self, alternate=True):
+        """Alternate the site order of consecutive CG launches (default) or walk forward."""
+        check(lib().lgt_set_sweep_order(self.h, int(bool(alternate))))
 
     def dslash(self, inp, op=OP_D, out_parity=FULL, dagger=False, kappa=0.0, precision=FP64, out=None):
         if out is None:
