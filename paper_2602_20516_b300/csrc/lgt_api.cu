@@ -700,11 +700,13 @@ static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, dou
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 0; A.in[1] = t; A.out[0] = u; A.y[0] = p; A.a = -kappa * kappa; A.red_op = RED_PAP;
-        A.reverse = dir();
+        A.reverse = dir(); A.defer = 1;
         CK(timed_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
+        // the hop of Dhat^+ does not need alpha: its block 0 finishes <p, A p> -> alpha
         A = hop_base(L, lk, fp64);
         A.skip = 1;
         A.parity = 1; A.in[0] = u; A.out[1] = t; A.reverse = dir();
+        A.fin_n = hop_grid(L->g, 0); A.fin_op = RED_PAP;
         CK(timed_hop(A, fp64, true, EPI_HOP, L->st));
         A = hop_base(L, lk, fp64);
         A.skip = 1;

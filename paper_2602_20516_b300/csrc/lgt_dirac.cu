@@ -184,14 +184,22 @@ __device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
 }
 
 template <typename R, bool DAG, int EPI>
-__device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk) {
+__device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk, bool first) {
     if (A.skip && A.s->done >= 1) return;
+    if (A.fin_n > 0 && first) {   // finish the deferred reduction of an earlier launch
+        const double acc = ordered_sum(A.partials, A.fin_n);
+        if (threadIdx.x == 0) apply_reduce_op(A.s, A.fin_op, A.red_slot, acc);
+    }
     const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
     const int t = blk * NT + threadIdx.x;
     const double red = (t < n) ? hop_site<R, DAG, EPI>(A, t) : 0.0;
     if (EPI == EPI_XPAY_NORM || EPI == EPI_CG || EPI == EPI_RESID) {
         double b = block_sum(red);
-        grid_reduce(b, A.partials, A.counter, A.s, A.red_op, A.red_slot, blk, nblk);
+        if (A.defer) {
+            if (threadIdx.x == 0) A.partials[blk] = b;
+        } else {
+            grid_reduce(b, A.partials, A.counter, A.s, A.red_op, A.red_slot, blk, nblk);
+        }
     }
 }
 
@@ -212,7 +220,7 @@ template <typename R, int EPI> constexpr int hop_min_blocks() {
 
 template <typename R, bool DAG, int EPI>
 __global__ void __launch_bounds__(NT, (hop_min_blocks<R, EPI>())) hop_kernel(HopArgs A) {
-    hop_body<R, DAG, EPI>(A, A.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x, gridDim.x);
+    hop_body<R, DAG, EPI>(A, A.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x, gridDim.x, blockIdx.x == 0);
 }
 
 // Many independent problems (lattices of any size) in one launch: block b runs
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(NT) hop_batch_kernel(const BatchHop* __restric
         else hi = mid - 1;
     }
     const BatchHop& e = d[lo];
-    hop_body<R, DAG, EPI>(e.a, b - e.first, e.nblk);
+    hop_body<R, DAG, EPI>(e.a, b - e.first, e.nblk, false);
 }
 
 template <typename R, bool DAG>
@@ -259,6 +267,7 @@ static cudaError_t launch_epi(const HopArgs& A, int epi, cudaStream_t st) {
     const int grid = (n + NT - 1) / NT;
     const bool reduces = epi == EPI_XPAY_NORM || epi == EPI_CG || epi == EPI_RESID;
     if (reduces && (!A.partials || grid > A.red_capacity)) return cudaErrorInvalidValue;
+    if (A.fin_n > 0 && (!A.partials || !A.s || A.fin_n > A.red_capacity)) return cudaErrorInvalidValue;
     switch (epi) {
     case EPI_HOP: hop_kernel<R, DAG, EPI_HOP><<<grid, NT, 0, st>>>(A); break;
     case EPI_XPAY: hop_kernel<R, DAG, EPI_XPAY><<<grid, NT, 0, st>>>(A); break;

@@ -30,6 +30,14 @@ struct HopArgs {
     int skip;             // 1: return at once when the solver scalars say done
     int red_capacity;     // entries of partials (reducing epilogues need one per block)
     int reverse;          // 1: block b works on site block nblk - 1 - b (same results)
+    // Deferred reduction: with defer set, a reducing epilogue only stores its block
+    // partials (no per-block fence and atomic); a later hop launch with fin_n > 0 has
+    // its block 0 sum those fin_n partials (the same fixed order as the last block of a
+    // reducing launch) and apply fin_op to the scalars before its own work.  For an
+    // epilogue whose result the next launch does not read (<p, A p> before the hop of
+    // Dhat^+).
+    int defer;
+    int fin_n, fin_op;
 };
 
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st);
