@@ -957,6 +957,31 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
             else TRY(cg_iteration(L, lk, true, eo, kappa, x, L->r, L->p, L->u, L->t));
         }
         TRY(sync_scalars(L));
+        // An FP32 cycle whose recursion residual grew 1e3-fold (in |r|^2) above the true
+        // residual it started from has diverged (seen when the search direction kept
+        // across a reliable update no longer suits a residual that differed from the
+        // recursion's by 2x): its correction is dropped, and the cycle restarts from that
+        // residual with p = r (counted as a breakdown)
+        if (use32 && !hs->nan && hs->rr_max > 1e3 * rr_prev) {
+            if (guessed) {
+                iters_at_update = hs->iters;
+                TRY(restart_from_zero());
+                continue;
+            }
+            if (++breakdowns > 16) {
+                rc = fail(LGT_ENAN, "FP32 CG diverged repeatedly after %d iterations", hs->iters);
+                break;
+            }
+            iters_at_update = hs->iters;
+            CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
+            CK(blas_d2f(L->r32, L->r, n, L->g.Vh, L->st));
+            CK(cudaMemcpyAsync(L->p32, L->r32, b32, cudaMemcpyDeviceToDevice, L->st));
+            hs->rr = rr_prev;
+            hs->rr_max = rr_prev;
+            hs->done = 0;
+            TRY(push_scalars(L));
+            continue;
+        }
         const bool breakdown = hs->nan != 0;
         const bool hit_cap = hs->iters >= sp->max_iter;
         const bool long_cycle = guessed ? hs->iters - iters_at_update >= guess_cap
@@ -1157,6 +1182,15 @@ static int cg_multi(lgt_lattice* L, int nrhs, const double2* const* b, double2* 
         for (int k = 0; k < nrhs; ++k) {
             if (fin[k]) continue;
             Scalars& h = W.hs[k];
+            // a diverged FP32 cycle restarts from its last true residual (as cg_core)
+            if (!h.nan && h.rr_max > 1e3 * rr_true[k]) {
+                CK(cudaMemsetAsync(W.x32[k], 0, b32, L->st));
+                CK(blas_d2f(W.r32[k], W.r64[k], n, L->g.Vh, L->st));
+                CK(cudaMemcpyAsync(W.p32[k], W.r32[k], b32, cudaMemcpyDeviceToDevice, L->st));
+                h.rr = h.rr_max = rr_true[k];
+                h.done = 0;
+                continue;
+            }
             if (h.nan) {
                 if (rc == LGT_OK) rc = fail(LGT_ENAN, "non-finite value in CG of system %d", k);
                 fin[k] = true; h.done = 2;

@@ -409,11 +409,33 @@ __global__ void __launch_bounds__(NT, (K == 1 ? 4 : (K == 2 ? 3 : 2))) hop_multi
         }
     }
     if (EPI == EPI_XPAY_NORM || EPI == EPI_CG) {
+        // the last-block reductions of the K systems with one fence and K atomics in
+        // flight together (the partials and their summation order are grid_reduce's)
+        double b[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) b[k] = act[k] ? block_sum(red[k]) : 0.0;   // act: the same in every block
+        __shared__ bool last[K];
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (act[k]) A.partials[k][blockIdx.x] = b[k];
+            __threadfence();
+            unsigned prev[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) prev[k] = act[k] ? atomicAdd(A.counter[k], 1u) : 0u;
+#pragma unroll
+            for (int k = 0; k < K; ++k) last[k] = act[k] && prev[k] == gridDim.x - 1;
+        }
+        __syncthreads();
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            if (!act[k]) continue;   // the same for every block of the launch
-            const double b = block_sum(red[k]);
-            grid_reduce(b, A.partials[k], A.counter[k], A.s[k], A.red_op, 0, blockIdx.x, gridDim.x);
+            if (!last[k]) continue;
+            __threadfence();
+            const double acc = ordered_sum(A.partials[k], gridDim.x);
+            if (threadIdx.x == 0) {
+                *A.counter[k] = 0u;
+                apply_reduce_op(A.s[k], A.red_op, 0, acc);
+            }
         }
     }
 }

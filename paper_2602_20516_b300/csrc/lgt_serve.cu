@@ -74,6 +74,11 @@ struct Req {
     int iters = 0;
     bool running = false;
     bool reported = false;
+    // mixed requests near a nearly singular operator (as lgt_cg_solve): FP32 breakdowns
+    // restart from the FP64 residual, two slow cycles in a row hand over to FP64 CG
+    int breakdowns = 0, poor = 0, iters_at_update = 0;
+    double rr_prev = 0.0;
+    bool restart_p = false;
 };
 
 size_t half64(const Geom& g) { return (size_t)12 * g.Vh * sizeof(double2); }
@@ -482,6 +487,7 @@ extern "C" int lgt_server_step(lgt_server_t S, int* n_active, int* n_queued) {
         for (Req* R : admitted) {
             Scalars& h = S->hs[R->slot];
             R->bb = h.slot[0];
+            R->rr_prev = R->bb;
             memset(&h, 0, sizeof(Scalars));
             h.rr = R->bb;
             h.rr_max = R->bb;
@@ -498,21 +504,46 @@ extern "C" int lgt_server_step(lgt_server_t S, int* n_active, int* n_queued) {
     // 3. stop conditions -> true residuals (reliable updates for mixed requests)
     STRY(sync_all_scalars(S));
     std::vector<Req*> check;
+    // an FP32 cycle this long without its stop test firing is ended by a reliable
+    // update as well
+    constexpr int kMaxCycle = 1000;
     for (Req* R : S->active) {
         if (!R->running) continue;
         Scalars& h = S->hs[R->slot];
-        if (h.nan) {
+        // a diverged FP32 cycle (|r|^2 of the recursion 1e3 above the true residual it
+        // started from): its correction is dropped and it restarts from that residual
+        if (!R->fp64 && !h.nan && h.rr_max > 1e3 * R->rr_prev) {
+            if (++R->breakdowns > 16) {
+                R->status = LGT_ENAN;
+                R->running = false;
+                continue;
+            }
+            const Geom& g = S->gauges[R->q.gauge_id].g;
+            R->iters_at_update = h.iters;
+            SCK(cudaMemsetAsync(R->x32, 0, half32(g), S->st));
+            SCK(blas_d2f(R->r32, R->r, g.Vh, g.Vh, S->st));
+            SCK(cudaMemcpyAsync(R->p32, R->r32, half32(g), cudaMemcpyDeviceToDevice, S->st));
+            h.rr = R->rr_prev;
+            h.rr_max = R->rr_prev;
+            h.done = 0;
+            SCK(cudaMemcpyAsync(S->s + R->slot, &h, sizeof(Scalars), cudaMemcpyHostToDevice, S->st));
+            continue;
+        }
+        const bool breakdown = h.nan != 0;
+        if (breakdown && (R->fp64 || ++R->breakdowns > 16)) {
             R->status = LGT_ENAN;
             R->running = false;
             continue;
         }
-        if (h.done >= 1 || h.iters >= R->q.max_iter) {
+        const bool long_cycle = !R->fp64 && h.iters - R->iters_at_update >= kMaxCycle;
+        if (h.done >= 1 || h.iters >= R->q.max_iter || breakdown || long_cycle) {
             const Geom& g = S->gauges[R->q.gauge_id].g;
             if (!R->fp64) {
                 SCK(blas_add_f2d(R->x, R->x32, g.Vh, g.Vh, S->st));
                 SCK(cudaMemsetAsync(R->x32, 0, half32(g), S->st));
             }
             STRY(true_residual(S, R));
+            R->restart_p = breakdown;
             check.push_back(R);
         }
     }
@@ -536,10 +567,27 @@ extern "C" int lgt_server_step(lgt_server_t S, int* n_active, int* n_queued) {
                 R->running = false;
             } else {
                 const Geom& g = S->gauges[R->q.gauge_id].g;
-                if (!R->fp64) SCK(blas_d2f(R->r32, R->r, g.Vh, g.Vh, S->st));
+                if (!R->fp64) {
+                    // |r| shrank by less than 2x since the last update, twice in a row:
+                    // the FP32 iterations stopped making progress, FP64 CG from here
+                    const bool slow = rr > 0.25 * R->rr_prev;
+                    R->poor = slow ? R->poor + 1 : 0;
+                    if (R->poor >= 2) {
+                        R->fp64 = true;
+                        SCK(cudaMemcpyAsync(R->p, R->r, half64(g), cudaMemcpyDeviceToDevice, S->st));
+                    }
+                }
+                R->rr_prev = rr;
+                R->iters_at_update = h.iters;
+                if (!R->fp64) {
+                    SCK(blas_d2f(R->r32, R->r, g.Vh, g.Vh, S->st));
+                    if (R->restart_p) SCK(cudaMemcpyAsync(R->p32, R->r32, half32(g), cudaMemcpyDeviceToDevice, S->st));
+                }
                 h.rr = rr;
                 h.rr_max = rr;
                 h.done = 0;
+                h.nan = 0;
+                h.delta2 = R->fp64 ? 0.0 : S->delta * S->delta;
                 SCK(cudaMemcpyAsync(S->s + R->slot, &h, sizeof(Scalars), cudaMemcpyHostToDevice, S->st));
             }
         }

@@ -6,6 +6,7 @@ reliable updates, epilogues) runs in liblgt; this module marshals arguments and
 drives the clock.
 """
 import ctypes as C
+import collections
 import time
 
 import numpy as np
@@ -181,4 +182,6 @@ def latency_stats(done):
         return {"p50_ms": None, "p99_ms": None, "n": 0}
     return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "mean_ms": 1e3 * float(lat.mean()), "n": int(lat.size),
-            "failed": int(sum(1 for c in done if c["status"] != 0))}
+            "failed": int(sum(1 for c in done if c["status"] != 0)),
+            "failed_by_status": {str(k): v for k, v in
+                                 collections.Counter(c["status"] for c in done if c["status"] != 0).items()}}

@@ -128,3 +128,31 @@ def test_poisson_latency_smoke(serve):
     st = serve.latency_stats(done)
     assert st["n"] == 55 and st["p99_ms"] >= st["p50_ms"] > 0
     srv.close()
+
+
+def test_near_critical_mixed_requests_succeed(serve):
+    """Smooth fields (alpha 0.3) with kappa at the top of the request range make
+    Dhat^+ Dhat nearly singular; FP32 rounding can then break the mixed CG recursion
+    (<p, A p> <= 0) or stall it.  The server restarts such a request from its FP64
+    residual (and hands a stalled one over to FP64 CG), so every request completes, to
+    its tolerance, with the solution of the FP64 request."""
+    srv = serve.Server(8 * GB, max_active=16, batch_iters=4)
+    dims = (8, 8, 8, 8)
+    g = [srv.add_gauge(dims, 20 + k, 0.3) for k in range(2)]
+    reqs = {}
+    for k, kappa in enumerate((0.150, 0.155, 0.157)):
+        for gi in g:
+            for prec in ("mixed", "fp64"):
+                rid = srv.submit(gi, serve.SOLVE, kappa, prec, tol=1e-10, source_seed=40 + k, keep_result=True)
+                reqs[rid] = (gi, kappa, prec)
+    done = {c["id"]: c for c in srv.run_until_idle()}
+    for rid, (gi, kappa, prec) in reqs.items():
+        assert done[rid]["status"] == 0, (gi, kappa, prec, done[rid])
+        assert done[rid]["true_rel_residual"] <= 1e-10
+    for rid, (gi, kappa, prec) in reqs.items():
+        if prec != "mixed":
+            continue
+        twin = next(r for r, v in reqs.items() if v == (gi, kappa, "fp64"))
+        a, b = srv.result(rid), srv.result(twin)
+        assert (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item() < 1e-6, (gi, kappa)
+    srv.close()
