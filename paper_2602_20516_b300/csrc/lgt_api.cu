@@ -1101,14 +1101,15 @@ static int cg_iteration_multi(lgt_lattice* L, int n, const int* sys, const doubl
     for (int j = 0; j < n; ++j) { A.in[j] = W.p32[sys[j]]; A.out[j] = W.t32[sys[j]]; }
     CK(launch_hop_multi(A, false, false, EPI_HOP, L->st));
     A = hop_multi_base(L, n, sys);
-    A.parity = 0; A.red_op = RED_PAP;
+    A.parity = 0; A.red_op = RED_PAP; A.defer = 1;
     for (int j = 0; j < n; ++j) {
         const int k = sys[j];
         A.in[j] = W.t32[k]; A.out[j] = W.u32[k]; A.y[j] = W.p32[k]; A.a[j] = -kappa[k] * kappa[k];
     }
     CK(launch_hop_multi(A, false, false, EPI_XPAY_NORM, L->st));
+    // the hop of Dhat^+ does not need alpha: its block 0 finishes <p, A p> -> alpha
     A = hop_multi_base(L, n, sys);
-    A.parity = 1;
+    A.parity = 1; A.fin_n = hop_grid(L->g, 0); A.fin_op = RED_PAP;
     for (int j = 0; j < n; ++j) { A.in[j] = W.u32[sys[j]]; A.out[j] = W.t32[sys[j]]; }
     CK(launch_hop_multi(A, false, true, EPI_HOP, L->st));
     A = hop_multi_base(L, n, sys);

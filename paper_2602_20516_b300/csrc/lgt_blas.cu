@@ -126,9 +126,8 @@ __global__ void __launch_bounds__(NT) p_update_kernel(T* p, const T* r, T* x, lo
 // so that a block touches whole sites: block b works on site block nblk - 1 - b when
 // reverse is set (the order of the sites only; the values are the same).
 template <typename T, int NC>
-__global__ void __launch_bounds__(NT) p_update_sites_kernel(T* p, const T* r, T* x, int Vh, RedArgs R, int reverse) {
+__device__ __forceinline__ void p_update_sites_body(T* p, const T* r, T* x, int Vh, const RedArgs& R, int blk) {
     if (R.s->done >= 2) return;
-    const int blk = reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
     const int i = blk * NT + threadIdx.x;
     if (i < Vh) {
         const double a = R.s->alpha, b = R.s->beta;
@@ -154,6 +153,16 @@ __global__ void __launch_bounds__(NT) p_update_sites_kernel(T* p, const T* r, T*
         *R.counter = 0u;
         if (R.s->done == 1) R.s->done = 2;
     }
+}
+template <typename T, int NC>
+__global__ void __launch_bounds__(NT) p_update_sites_kernel(T* p, const T* r, T* x, int Vh, RedArgs R, int reverse) {
+    p_update_sites_body<T, NC>(p, r, x, Vh, R, reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x);
+}
+// several systems (blockIdx.y), FP32 half fields
+__global__ void __launch_bounds__(NT) p_update_sites_multi_kernel(PUpdateM P, int Vh) {
+    const int k = blockIdx.y;
+    if (k >= P.nrhs) return;
+    p_update_sites_body<float4, 6>((float4*)P.p[k], (const float4*)P.r[k], (float4*)P.x[k], Vh, P.red[k], blockIdx.x);
 }
 
 template <typename T>
@@ -185,10 +194,14 @@ __global__ void __launch_bounds__(NT) p_update_multi_kernel(PUpdateM P, long ne)
 }
 cudaError_t blas_cg_p_update_multi(const PUpdateM& P, int n, bool fp64, cudaStream_t st) {
     if (P.nrhs < 1 || P.nrhs > KMAX_RHS) return cudaErrorInvalidValue;
-    const long ne = (long)n * (fp64 ? 12 : 6);
+    if (!fp64) {   // one FP32 half field per system: site blocks
+        p_update_sites_multi_kernel<<<dim3(grid_for(n), P.nrhs), NT, 0, st>>>(P, n);
+        count_launch();
+        return cudaGetLastError();
+    }
+    const long ne = (long)n * 12;
     const dim3 grid(grid_for(ne), P.nrhs);
-    if (fp64) p_update_multi_kernel<double2><<<grid, NT, 0, st>>>(P, ne);
-    else p_update_multi_kernel<float4><<<grid, NT, 0, st>>>(P, ne);
+    p_update_multi_kernel<double2><<<grid, NT, 0, st>>>(P, ne);
     count_launch();
     return cudaGetLastError();
 }

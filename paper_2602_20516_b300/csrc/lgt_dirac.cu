@@ -346,6 +346,14 @@ __global__ void __launch_bounds__(NT, (K == 1 ? 4 : (K == 2 ? 3 : 2))) hop_multi
         any = any || act[k];
     }
     if (!any) return;
+    if (A.fin_n > 0 && blockIdx.x == 0) {   // finish the deferred reductions of an earlier launch
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (!act[k]) continue;
+            const double acc = ordered_sum(A.partials[k], A.fin_n);
+            if (threadIdx.x == 0) apply_reduce_op(A.s[k], A.fin_op, 0, acc);
+        }
+    }
     const int t = blockIdx.x * NT + threadIdx.x;
     double red[K];
 #pragma unroll
@@ -414,6 +422,13 @@ __global__ void __launch_bounds__(NT, (K == 1 ? 4 : (K == 2 ? 3 : 2))) hop_multi
         double b[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) b[k] = act[k] ? block_sum(red[k]) : 0.0;   // act: the same in every block
+        if (A.defer) {
+            if (threadIdx.x == 0)
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (act[k]) A.partials[k][blockIdx.x] = b[k];
+            return;
+        }
         __shared__ bool last[K];
         if (threadIdx.x == 0) {
 #pragma unroll
@@ -471,6 +486,7 @@ cudaError_t launch_hop_multi(const HopArgsM& A, bool fp64, bool dagger, int epi,
         if (!A.in[k]) return cudaErrorInvalidValue;
     const bool reduces = epi == EPI_XPAY_NORM || epi == EPI_CG;
     if (reduces && (A.g.Vh + NT - 1) / NT > A.red_capacity) return cudaErrorInvalidValue;
+    if (A.fin_n > A.red_capacity) return cudaErrorInvalidValue;
     return dagger ? launch_multi_k<true>(A, epi, st) : launch_multi_k<false>(A, epi, st);
 }
 

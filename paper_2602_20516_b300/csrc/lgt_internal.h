@@ -65,6 +65,8 @@ struct HopArgsM {
     Scalars* s[KMAX_RHS];
     double* partials[KMAX_RHS];
     unsigned* counter[KMAX_RHS];
+    int defer;            // as HopArgs: the reducing epilogue only stores block partials,
+    int fin_n, fin_op;    // block 0 of a later launch sums fin_n of them per system
 };
 cudaError_t launch_hop_multi(const HopArgsM& A, bool fp64, bool dagger, int epi, cudaStream_t st);
 
