@@ -548,6 +548,11 @@ def run_hmc(args):
                         "dH_abs_diff": abs(rd["dH"] - r["dH"]), "fp64_seconds": time.perf_counter() - t1})
         trajs.append(rec)
         print(json.dumps({"progress": rec}), file=sys.stderr, flush=True)
+        if args.log:   # one JSON line per trajectory
+            with open(args.log, "a") as f:
+                f.write(json.dumps(rec) + "\n")
+        if args.checkpoint:   # the chain's state after trajectory k: links, seed, k + 1
+            lat.save_checkpoint(args.checkpoint, SEED, k + 1)
     acc = sum(t["accepted"] for t in trajs) / max(len(trajs), 1)
     mixed_s = statistics.mean(t["seconds"] for t in trajs)
     out = {"metric": "HMC trajectories at 32^3x64 (Omelyan 2MN, 20 steps, tau 1), mixed vs FP64",
@@ -621,6 +626,8 @@ def main():
     ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")
     ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
     ap.add_argument("--hmc-fp64", type=int, default=2, help="trajectories replayed on the FP64 path")
+    ap.add_argument("--log", default="", help="HMC mode: append one JSON line per trajectory to this file")
+    ap.add_argument("--checkpoint", default="", help="HMC mode: write the chain's checkpoint here after every trajectory")
     ap.add_argument("--chrono", type=int, default=0,
                     help="HMC mode: MD solves start from the last N solutions (chronological guess)")
     ap.add_argument("--kernel", choices=["hop32", "hop64", "force_df"])

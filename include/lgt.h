@@ -343,6 +343,20 @@ int lgt_gaussian_momenta(lgt_lattice_t lat, double *mom, uint64_t seed, uint32_t
  * (counter (s, component, traj, field)); field = 2 is the HMC heatbath xi. */
 int lgt_gaussian_spinor(lgt_lattice_t lat, double *field, uint64_t seed, uint32_t traj,
                         uint32_t field_id, int parity);
+/* Checkpoint of an HMC chain (not in the paper): its state is the FP64 links, the seed
+ * and the index of the next trajectory (every random number is drawn by Philox from
+ * seed, trajectory and site, so there is no generator state); a chain resumed from a
+ * checkpoint repeats the next trajectory bitwise.  File (little-endian): 7 header words
+ * of 64 bits (magic "LGTCKPT1"; version 1; dims[0] | dims[1] << 32; dims[2] | dims[3]
+ * << 32; seed; next trajectory; payload bytes), the canonical links (complex128
+ * [V][4][3][3]), and the FNV-1a hash (basis 0xcbf29ce484222325, prime 0x100000001b3)
+ * of header and payload taken over 64-bit words.  load checks magic, version, the
+ * handle's dims, the length and the hash (LGT_EINVAL on any mismatch, the handle's
+ * links untouched), then sets the links (FP64 and the FP32 copy); seed and next_traj
+ * may be NULL.  Both synchronous; the handle keeps one link field of staging memory. */
+int lgt_save_checkpoint(lgt_lattice_t lat, const char *path, uint64_t seed, uint64_t next_traj);
+int lgt_load_checkpoint(lgt_lattice_t lat, const char *path, uint64_t *seed, uint64_t *next_traj);
+
 /* One HMC trajectory (Sec. III B): momentum and pseudofermion heatbaths
  * (phi = M^+ xi), integration, Metropolis with u from Philox (counter
  * (0,0,traj,4)), U restored on reject, then reunitarisation.  Synchronous. */

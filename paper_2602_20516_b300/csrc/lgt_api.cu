@@ -161,6 +161,8 @@ struct lgt_lattice {
     int sweep = 0;
     // HMC / force workspace
     double2 *mom, *Ubak, *phi, *xi, *F, *G;
+    // canonical links staged for lgt_save_checkpoint / lgt_load_checkpoint
+    double2* ckpt = nullptr;
     bool have_md;
     // stout stack: a pool of FP64 link fields holding the smeared levels the adjoint
     // needs (placement by StoutPlan), the FP32 copy of the top level, gradient
@@ -478,6 +480,84 @@ extern "C" int lgt_get_links(lgt_lattice_t L, double* canon) {
     CK(gauge_unpack_links(canon, L->thin.U, L->g, L->st));
     return LGT_OK;
 }
+// ---------------------------------------------------------------- checkpoint
+// File: header of 7 little-endian 64-bit words (magic "LGTCKPT1"; version | flags << 32;
+// dims[0] | dims[1] << 32; dims[2] | dims[3] << 32; seed; next trajectory; payload
+// bytes), the canonical links (complex128 [V][4][3][3]), then the FNV-1a hash of the
+// header and payload taken over 64-bit words (offset basis 0xcbf29ce484222325,
+// prime 0x100000001b3).
+namespace {
+constexpr uint64_t kCkptMagic = 0x3154504b4354474cull;   // "LGTCKPT1" read little-endian
+constexpr uint64_t kCkptVersion = 1;
+uint64_t fnv1a_words(uint64_t h, const uint64_t* w, size_t n) {
+    for (size_t k = 0; k < n; ++k) {
+        h ^= w[k];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+}  // namespace
+
+static int ensure_ckpt(lgt_lattice* L) {
+    if (!L->ckpt) TRY(A(L, links64(L), &L->ckpt));
+    return LGT_OK;
+}
+
+extern "C" int lgt_save_checkpoint(lgt_lattice_t L, const char* path, uint64_t seed, uint64_t next_traj) {
+    if (!L || !path) return fail(LGT_EINVAL, "null argument");
+    TRY(ensure_ckpt(L));
+    const size_t bytes = links64(L);
+    std::vector<uint64_t> buf(7 + bytes / 8);
+    uint64_t* h = buf.data();
+    h[0] = kCkptMagic;
+    h[1] = kCkptVersion;
+    h[2] = (uint64_t)(uint32_t)L->dims[0] | ((uint64_t)(uint32_t)L->dims[1] << 32);
+    h[3] = (uint64_t)(uint32_t)L->dims[2] | ((uint64_t)(uint32_t)L->dims[3] << 32);
+    h[4] = seed;
+    h[5] = next_traj;
+    h[6] = bytes;
+    CK(gauge_unpack_links((double*)L->ckpt, L->thin.U, L->g, L->st));
+    CK(cudaMemcpyAsync(h + 7, L->ckpt, bytes, cudaMemcpyDeviceToHost, L->st));
+    CK(cudaStreamSynchronize(L->st));
+    const uint64_t sum = fnv1a_words(0xcbf29ce484222325ull, buf.data(), buf.size());
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(LGT_EINVAL, "cannot open %s for writing", path);
+    const bool ok = fwrite(buf.data(), 8, buf.size(), f) == buf.size() && fwrite(&sum, 8, 1, f) == 1;
+    if (fclose(f) != 0 || !ok) return fail(LGT_EINVAL, "writing %s failed", path);
+    return LGT_OK;
+}
+
+extern "C" int lgt_load_checkpoint(lgt_lattice_t L, const char* path, uint64_t* seed, uint64_t* next_traj) {
+    if (!L || !path) return fail(LGT_EINVAL, "null argument");
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(LGT_EINVAL, "cannot open %s", path);
+    const size_t bytes = links64(L);
+    std::vector<uint64_t> buf(7 + bytes / 8);
+    uint64_t sum = 0, extra = 0;
+    const size_t got = fread(buf.data(), 8, buf.size(), f);
+    const bool have_sum = fread(&sum, 8, 1, f) == 1;
+    const bool at_end = fread(&extra, 1, 1, f) == 0;
+    fclose(f);
+    const uint64_t* h = buf.data();
+    if (got < 7 || h[0] != kCkptMagic) return fail(LGT_EINVAL, "%s is not a checkpoint", path);
+    if ((h[1] & 0xffffffffull) != kCkptVersion) return fail(LGT_EINVAL, "checkpoint version %llu", (unsigned long long)h[1]);
+    const int d[4] = {(int)(uint32_t)h[2], (int)(uint32_t)(h[2] >> 32), (int)(uint32_t)h[3], (int)(uint32_t)(h[3] >> 32)};
+    for (int m = 0; m < 4; ++m)
+        if (d[m] != L->dims[m])
+            return fail(LGT_EINVAL, "checkpoint lattice %dx%dx%dx%d differs from the handle's", d[0], d[1], d[2], d[3]);
+    if (h[6] != bytes || got != buf.size() || !have_sum || !at_end)
+        return fail(LGT_EINVAL, "checkpoint %s is truncated or too long", path);
+    if (fnv1a_words(0xcbf29ce484222325ull, buf.data(), buf.size()) != sum)
+        return fail(LGT_EINVAL, "checkpoint %s: checksum mismatch", path);
+    TRY(ensure_ckpt(L));
+    CK(cudaMemcpyAsync(L->ckpt, h + 7, bytes, cudaMemcpyHostToDevice, L->st));
+    CK(gauge_pack_links(L->thin.U, L->thin.U12, L->ckpt, L->g, L->st));
+    CK(cudaStreamSynchronize(L->st));
+    if (seed) *seed = h[4];
+    if (next_traj) *next_traj = h[5];
+    return LGT_OK;
+}
+
 extern "C" int lgt_random_links(lgt_lattice_t L, uint64_t seed, double alpha) {
     if (!L) return fail(LGT_EINVAL, "null lattice");
     CK(gauge_random(L->thin.U, L->thin.U12, L->g, seed, alpha, L->st));
@@ -846,6 +926,7 @@ static int chrono_record(lgt_lattice* L, const double2* x, double kappa, int ite
 
 static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x, double kappa, bool eo,
                    const lgt_solver_params* sp, lgt_solve_stats* stats) {
+    NvtxRange nvtx("lgt cg");
     auto t0 = std::chrono::steady_clock::now();
     if (!sp) return fail(LGT_EINVAL, "null solver parameters");
     if (sp->precision != LGT_FP64 && sp->precision != LGT_MIXED) return fail(LGT_EINVAL, "solver precision %d", sp->precision);
@@ -1419,6 +1500,7 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
 static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk, const lgt_action_params* ap,
                     const double2* phi, const lgt_solver_params* sp, double coef, int keep, int form, double2* out,
                     lgt_solve_stats* stats) {
+    NvtxRange nvtx("lgt force");
     const int arith = (form == 0 && sp && sp->precision == LGT_MIXED) ? ap->force_arith : LGT_ARITH_FP64;
     const bool fp32 = arith == LGT_ARITH_FP32, dfa = arith == LGT_ARITH_DF64;
     if (dfa) TRY(ensure_df(L));
@@ -1606,6 +1688,7 @@ static int kick(lgt_lattice* L, double2* mom, double eps, const lgt_action_param
 extern "C" int lgt_md_update(lgt_lattice_t L, double* mom, double eps, int which, const lgt_action_params* ap,
                              const double* phi, const lgt_solver_params* sp, lgt_solve_stats* stats) {
     if (!L || !mom) return fail(LGT_EINVAL, "null argument");
+    NvtxRange nvtx(which == LGT_UPDATE_U ? "lgt update U" : "lgt update P");
     if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
     if (which == LGT_UPDATE_U) {
         CK(gauge_update_links(L->thin.U, L->thin.U12, (const double2*)mom, eps, L->g, L->st));
@@ -1698,6 +1781,7 @@ static int integrate(lgt_lattice* L, const lgt_action_params* ap, const lgt_hmc_
 extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, const lgt_hmc_params* hp,
                                   uint64_t seed, uint32_t traj, lgt_hmc_result* res) {
     if (!L || !hp || !res) return fail(LGT_EINVAL, "null argument");
+    NvtxRange nvtx("lgt trajectory");
     TRY(check_action(ap));
     if (hp->n_steps <= 0) return fail(LGT_EINVAL, "n_steps must be positive");
     TRY(ensure_md(L));

@@ -5,8 +5,17 @@
 #include <stdint.h>
 
 #include "lgt_common.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 namespace lgt {
+
+// NVTX range for the duration of a scope (a no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 enum Epilogue { EPI_HOP = 0, EPI_XPAY = 1, EPI_XPAY_NORM = 2, EPI_CG = 3, EPI_RESID = 4 };
 

@@ -456,6 +456,7 @@ extern "C" int lgt_server_submit(lgt_server_t S, const lgt_request* q, uint64_t*
 
 extern "C" int lgt_server_step(lgt_server_t S, int* n_active, int* n_queued) {
     if (!S) return set_error(LGT_EINVAL, "null server");
+    NvtxRange nvtx("lgt server step");
     // 1. admission (arrival order; a request that cannot fit even alone is refused)
     std::vector<Req*> admitted;
     while (!S->queue.empty() && (int)S->active.size() < S->max_active) {

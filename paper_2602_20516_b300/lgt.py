@@ -123,6 +123,8 @@ SIGNATURES = [
     ("lgt_unpack_links_field", _I, [_P, _P, _P]),
     ("lgt_set_clover", _I, [_P, _D, _D]),
     ("lgt_set_sweep_order", _I, [_P, _I]),
+    ("lgt_save_checkpoint", _I, [_P, C.c_char_p, C.c_uint64, C.c_uint64]),
+    ("lgt_load_checkpoint", _I, [_P, C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     ("lgt_dslash", _I, [_P, _P, _P, _I, _I, _I, _D, _I]),
     ("lgt_cg_solve", _I, [_P, _P, _P, _D, _I, C.POINTER(SolverParams), C.POINTER(SolveStats)]),
     ("lgt_cg_solve_multi", _I, [_P, _I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_D), C.POINTER(SolverParams),
@@ -394,6 +396,16 @@ class Lattice:
     def set_clover(self, csw, kappa):
         """Attach (csw != 0) or detach (csw = 0) the clover term for OP_D and full-lattice solves."""
         check(lib().lgt_set_clover(self.h, csw, kappa))
+
+    def save_checkpoint(self, path, seed, next_traj):
+        """Write the links, seed and next trajectory index (lgt_save_checkpoint)."""
+        check(lib().lgt_save_checkpoint(self.h, os.fsencode(path), int(seed), int(next_traj)))
+
+    def load_checkpoint(self, path):
+        """Set the links from a checkpoint; returns (seed, next trajectory index)."""
+        seed, nxt = C.c_uint64(), C.c_uint64()
+        check(lib().lgt_load_checkpoint(self.h, os.fsencode(path), C.byref(seed), C.byref(nxt)))
+        return seed.value, nxt.value
 
     def set_sweep_order(self, alternate=True):
         """Alternate the site order of consecutive CG launches (default) or walk forward."""
