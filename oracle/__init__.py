@@ -83,6 +83,16 @@ def lib():
             "ora_pf_action_grad_sw": (C.c_int, [_ip, _cp, C.c_double, C.c_double, _cp, C.c_double, C.c_int, _cp]),
             "ora_pf_force_sw": (C.c_int, [_ip, _cp, C.c_double, C.c_double, _cp, C.c_double, C.c_int,
                                           C.c_double, _dp]),
+            "ora_dhat_sw": (None, [_ip, _cp, C.c_double, C.c_double, _cp, _cp, C.c_int]),
+            "ora_clover_logdet_odd": (C.c_double, [_ip, _cp, C.c_double, C.c_double]),
+            "ora_cg_sw_eo": (C.c_int, [_ip, _cp, C.c_double, C.c_double, _cp, _cp, C.c_double, C.c_int,
+                                       C.POINTER(C.c_double)]),
+            "ora_pf_action_sw_eo": (C.c_double, [_ip, _cp, C.c_double, C.c_double, _cp, C.c_double, C.c_int,
+                                                 C.POINTER(C.c_int)]),
+            "ora_pf_action_grad_sw_eo": (C.c_int, [_ip, _cp, C.c_double, C.c_double, _cp, C.c_double, C.c_int,
+                                                   _cp]),
+            "ora_pf_force_sw_eo": (C.c_int, [_ip, _cp, C.c_double, C.c_double, _cp, C.c_double, C.c_int,
+                                             C.c_double, _dp]),
             "ora_gauge_force_imp": (None, [_ip, _cp, C.c_double, C.c_double, C.c_double, _dp]),
             "ora_gauge_action_grad_imp": (None, [_ip, _cp, C.c_double, C.c_double, _cp]),
             "ora_pf_action": (C.c_double, [_ip, _cp, C.c_double, C.c_int, _cp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
@@ -286,6 +296,48 @@ def pf_force_sw(dims, U, kappa, csw, phi, tol=1e-12, max_iter=10000):
     return F, it
 
 
+def dhat_sw(dims, U, kappa, csw, psi, dagger=False):
+    """Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe (M = 1 + A) on the even sites of psi."""
+    d = _dims(dims)
+    out = np.zeros_like(_c(psi))
+    lib().ora_dhat_sw(d, _c(U), kappa, csw, _c(psi), out, int(dagger))
+    return out
+
+
+def clover_logdet_odd(dims, U, kappa, csw):
+    """sum over odd sites x of ln det (1 + A(x))."""
+    return lib().ora_clover_logdet_odd(_dims(dims), _c(U), kappa, csw)
+
+
+def cg_sw_eo(dims, U, kappa, csw, b, tol=1e-12, max_iter=10000):
+    d = _dims(dims)
+    x = np.zeros_like(_c(b))
+    res = C.c_double()
+    it = lib().ora_cg_sw_eo(d, _c(U), kappa, csw, _c(b), x, tol, max_iter, C.byref(res))
+    return x, it, res.value
+
+
+def pf_action_sw_eo(dims, U, kappa, csw, phi, tol=1e-12, max_iter=10000):
+    """phi_e^+ (Dhat^+ Dhat)^{-1} phi_e - 2 ln det M_oo."""
+    it = C.c_int()
+    S = lib().ora_pf_action_sw_eo(_dims(dims), _c(U), kappa, csw, _c(phi), tol, max_iter, C.byref(it))
+    return S, it.value
+
+
+def pf_action_grad_sw_eo(dims, U, kappa, csw, phi, tol=1e-12, max_iter=10000):
+    d = _dims(dims)
+    G = np.zeros((volume(d), 4, 3, 3), np.complex128)
+    it = lib().ora_pf_action_grad_sw_eo(d, _c(U), kappa, csw, _c(phi), tol, max_iter, G)
+    return G, it
+
+
+def pf_force_sw_eo(dims, U, kappa, csw, phi, tol=1e-12, max_iter=10000):
+    d = _dims(dims)
+    F = np.zeros((volume(d), 4, 8))
+    it = lib().ora_pf_force_sw_eo(d, _c(U), kappa, csw, _c(phi), tol, max_iter, 1.0, F)
+    return F, it
+
+
 def rectangle_sum(dims, U):
     """sum over x and ordered mu != nu of Re tr R_munu(x) / 3 (2 x 1 loops, long side mu)."""
     return lib().ora_rectangle_sum(_dims(dims), _c(U))
@@ -384,8 +436,6 @@ INTEGRATORS = {"leapfrog": 0, "omelyan": 1, "sexton_weingarten": 2}
 def hmc_params(beta, kappa, eo=False, fermions=True, integrator="leapfrog", n_steps=10,
                tau=1.0, tol_md=1e-12, tol_action=1e-12, max_iter=10000, n_inner=1, n_stout=0, rho=0.0, c1=0.0,
                csw=0.0):
-    if csw != 0.0 and eo:
-        raise ValueError("the clover term is implemented for the full-lattice action only")
     return HMCParams(beta, kappa, int(eo), int(fermions), INTEGRATORS[integrator], n_steps, tau, tol_md,
                      tol_action, max_iter, n_inner, n_stout, rho, c1, csw)
 

@@ -7,7 +7,8 @@
  *   Q_munu(x) = the four plaquettes ("leaves") of the mu-nu plane at x, each
  *   traversed mu before nu and starting and ending at x.
  * A is Hermitian, so D_sw^+ = 1 - kappa H^+ + A and gamma_5 D_sw gamma_5 = D_sw^+.
- * Only the full-lattice pseudofermion action is covered.
+ * The full-lattice and the even-odd pseudofermion actions are covered (the even-odd
+ * one with the odd-site determinant, see below).
  *
  * Force: with chi = (D^+D)^{-1} phi and eta = D chi, delta S_f = -2 Re eta^+ (delta D) chi,
  * whose clover part is 2 kappa c_sw Re sum_{x,mu<nu} tr(delta F_munu Lambda_munu) with
@@ -20,6 +21,7 @@
  */
 #include "oracle.h"
 #include "ora_internal.h"
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -123,6 +125,51 @@ void ora_clover_term(const int d[4], const ocplx *U, double kappa, double csw, o
     }
 }
 
+/* inverse of a 12x12 complex matrix by Gauss-Jordan elimination with partial pivoting;
+ * returns ln |det| (the sum of ln |pivot|) */
+static double inv12(const ocplx *Min, ocplx *Mout)
+{
+    ocplx a[12][24];
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 24; ++j) a[i][j] = j < 12 ? Min[i * 12 + j] : (j - 12 == i ? 1.0 : 0.0);
+    double logdet = 0.0;
+    for (int c = 0; c < 12; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 12; ++r)
+            if (cabs(a[r][c]) > cabs(a[piv][c])) piv = r;
+        if (piv != c)
+            for (int j = 0; j < 24; ++j) { ocplx t = a[c][j]; a[c][j] = a[piv][j]; a[piv][j] = t; }
+        const ocplx pv = a[c][c];
+        logdet += log(cabs(pv));
+        for (int j = 0; j < 24; ++j) a[c][j] /= pv;
+        for (int r = 0; r < 12; ++r) {
+            if (r == c) continue;
+            const ocplx f = a[r][c];
+            if (f == 0) continue;
+            for (int j = 0; j < 24; ++j) a[r][j] -= f * a[c][j];
+        }
+    }
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j) Mout[i * 12 + j] = a[i][12 + j];
+    return logdet;
+}
+
+/* M = 1 + C is Hermitian positive definite for the couplings used (det M > 0, so ln det
+ * M = ln |det M|) */
+double ora_clover_inverse_odd(const int d[4], const ocplx *C, ocplx *Minv)
+{
+    long V = ora_volume(d);
+    double sum = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : sum)
+    for (long x = 0; x < V; ++x) {
+        if (ora_parity(d, x) != 1) continue;
+        ocplx M[144];
+        for (int i = 0; i < 144; ++i) M[i] = C[x * 144 + i] + ((i / 12 == i % 12) ? 1.0 : 0.0);
+        sum += inv12(M, &Minv[x * 144]);
+    }
+    return sum;
+}
+
 static ocplx *clover_or_null(const int d[4], const ocplx *U, double kappa, double csw)
 {
     if (csw == 0.0) return NULL;
@@ -157,9 +204,13 @@ double ora_pf_action_sw(const int d[4], const ocplx *U, double kappa, double csw
     return S;
 }
 
-/* clover part of the real-component gradient, added to G (serial scatter) */
+/* clover part of the real-component gradient, added to G (serial scatter).  With Minv
+ * (even-odd action) the gradient of -2 ln det M_oo is added on odd sites: its variation
+ * -2 tr(M^{-1} delta A) has the same form as -2 Re eta^+ delta A chi with the spin-colour
+ * matrix chi eta^+ replaced by M^{-1}, so it enters Lambda as
+ * sum_{s,t} sigma_{st} (M^{-1})_{(t a),(s b)}. */
 static void clover_grad_add(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *X,
-                            const ocplx *Y, ocplx *G)
+                            const ocplx *Y, const ocplx *Minv, ocplx *G)
 {
     long V = ora_volume(d);
     for (long x = 0; x < V; ++x)
@@ -172,8 +223,11 @@ static void clover_grad_add(const int d[4], const ocplx *U, double kappa, double
                     for (int t = 0; t < 4; ++t) {
                         if (sg[s * 4 + t] == 0) continue;
                         for (int a = 0; a < 3; ++a)
-                            for (int b = 0; b < 3; ++b)
+                            for (int b = 0; b < 3; ++b) {
                                 Lam[a * 3 + b] += sg[s * 4 + t] * X[x * 12 + t * 3 + a] * conj(Y[x * 12 + s * 3 + b]);
+                                if (Minv && ora_parity(d, x) == 1)
+                                    Lam[a * 3 + b] += sg[s * 4 + t] * Minv[x * 144 + (t * 3 + a) * 12 + s * 3 + b];
+                            }
                     }
                 for (int a = 0; a < 3; ++a)
                     for (int b = 0; b < 3; ++b)
@@ -214,10 +268,92 @@ int ora_pf_action_grad_sw(const int d[4], const ocplx *U, double kappa, double c
     ocplx *Y = calloc(n, sizeof(ocplx));
     int it = ora_force_vectors_c(d, U, kappa, A, 0, phi, tol, max_iter, X, Y);
     ora_fermion_grad_xy(d, kappa, X, Y, G);
-    if (csw != 0.0) clover_grad_add(d, U, kappa, csw, X, Y, G);
+    if (csw != 0.0) clover_grad_add(d, U, kappa, csw, X, Y, NULL, G);
     free(A);
     free(X);
     free(Y);
+    return it;
+}
+
+/* ---- even-odd preconditioned clover operator:
+ *   Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe,  M = 1 + A,
+ *   S_f = phi_e^+ (Dhat^+ Dhat)^{-1} phi_e - 2 ln det M_oo
+ * (det D = det M_oo det Dhat, so det(D^+ D) = det(M_oo)^2 det(Dhat^+ Dhat)). */
+void ora_dhat_sw(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *in, ocplx *out,
+                 int dagger)
+{
+    ocplx *A = clover_or_null(d, U, kappa, csw);
+    ocplx *Minv = NULL;
+    if (A) {
+        Minv = calloc(144 * ora_volume(d), sizeof(ocplx));
+        ora_clover_inverse_odd(d, A, Minv);
+    }
+    ora_dhat_c(d, U, kappa, A, Minv, in, out, dagger);
+    free(A);
+    free(Minv);
+}
+
+double ora_clover_logdet_odd(const int d[4], const ocplx *U, double kappa, double csw)
+{
+    ocplx *A = clover_or_null(d, U, kappa, csw);
+    if (!A) return 0.0;
+    ocplx *Minv = calloc(144 * ora_volume(d), sizeof(ocplx));
+    double s = ora_clover_inverse_odd(d, A, Minv);
+    free(A);
+    free(Minv);
+    return s;
+}
+
+int ora_cg_sw_eo(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *b, ocplx *x, double tol,
+                 int max_iter, double *true_res)
+{
+    ocplx *A = clover_or_null(d, U, kappa, csw);
+    int it = ora_cg_c(d, U, kappa, A, 1, b, x, tol, max_iter, true_res);
+    free(A);
+    return it;
+}
+
+double ora_pf_action_sw_eo(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *phi,
+                           double tol, int max_iter, int *iters)
+{
+    ocplx *A = clover_or_null(d, U, kappa, csw);
+    double S = ora_pf_action_c(d, U, kappa, A, 1, phi, tol, max_iter, iters);
+    free(A);
+    return S;
+}
+
+int ora_pf_action_grad_sw_eo(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *phi,
+                             double tol, int max_iter, ocplx *G)
+{
+    long n = ora_volume(d) * 12;
+    ocplx *A = clover_or_null(d, U, kappa, csw);
+    ocplx *X = calloc(n, sizeof(ocplx));
+    ocplx *Y = calloc(n, sizeof(ocplx));
+    int it = ora_force_vectors_c(d, U, kappa, A, 1, phi, tol, max_iter, X, Y);
+    ora_fermion_grad_xy(d, kappa, X, Y, G);
+    if (A) {
+        ocplx *Minv = calloc(n * 12, sizeof(ocplx));
+        ora_clover_inverse_odd(d, A, Minv);
+        clover_grad_add(d, U, kappa, csw, X, Y, Minv, G);
+        free(Minv);
+    }
+    free(A);
+    free(X);
+    free(Y);
+    return it;
+}
+
+int ora_pf_force_sw_eo(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *phi, double tol,
+                       int max_iter, double coef, double *F)
+{
+    long V = ora_volume(d);
+    ocplx *G = calloc(36 * V, sizeof(ocplx));
+    double *Fl = calloc(32 * V, sizeof(double));
+    int it = ora_pf_action_grad_sw_eo(d, U, kappa, csw, phi, tol, max_iter, G);
+    ora_grad_to_force(d, U, G, Fl);
+    for (long i = 0; i < 32 * V; ++i) F[i] += coef * Fl[i];
+    free(G);
+    free(Fl);
     return it;
 }
 

@@ -86,21 +86,55 @@ void ora_dirac(const int d[4], const ocplx *U, double kappa, const ocplx *in, oc
     ora_dirac_c(d, U, kappa, NULL, in, out, dagger);
 }
 
-void ora_dhat(const int d[4], const ocplx *U, double kappa, const ocplx *in, ocplx *out,
-              int dagger)
+/* out[x] = Ms[x] in[x] on the sites of parity p, Ms a [V][12][12] field of site matrices */
+static void site_apply(const int d[4], const ocplx *Ms, int p, const ocplx *in, ocplx *out)
+{
+    long V = ora_volume(d);
+    for (long x = 0; x < V; ++x) {
+        if (ora_parity(d, x) != p) continue;
+        for (int i = 0; i < 12; ++i) {
+            ocplx acc = 0;
+            for (int j = 0; j < 12; ++j) acc += Ms[(x * 12 + i) * 12 + j] * in[x * 12 + j];
+            out[x * 12 + i] = acc;
+        }
+    }
+}
+
+/* Schur complement on even sites of D = [[M_ee, -kappa H_eo], [-kappa H_oe, M_oo]]:
+ *   Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe,
+ * M = 1 without a clover term (C = NULL), M = 1 + C with one (Minv = M^{-1} on odd
+ * sites).  M is Hermitian, so the adjoint swaps H for H^+ only. */
+void ora_dhat_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, const ocplx *Minv,
+                const ocplx *in, ocplx *out, int dagger)
 {
     long V = ora_volume(d);
     ocplx *t = calloc(V * 12, sizeof(ocplx));
     ocplx *u = calloc(V * 12, sizeof(ocplx));
+    ocplx *m = NULL;
     ora_hop(d, U, in, t, 2, dagger);   /* odd sites from even in */
+    if (C) {
+        ocplx *t2 = calloc(V * 12, sizeof(ocplx));
+        site_apply(d, Minv, 1, t, t2);
+        free(t);
+        t = t2;
+        m = calloc(V * 12, sizeof(ocplx));
+        site_apply(d, C, 0, in, m);    /* A_ee in */
+    }
     ora_hop(d, U, t, u, 1, dagger);    /* even sites from odd t */
     for (long x = 0; x < V; ++x) {
         int even = (ora_parity(d, x) == 0);
         for (int i = 0; i < 12; ++i)
-            out[x * 12 + i] = even ? in[x * 12 + i] - kappa * kappa * u[x * 12 + i] : 0;
+            out[x * 12 + i] = even ? in[x * 12 + i] + (m ? m[x * 12 + i] : 0) - kappa * kappa * u[x * 12 + i] : 0;
     }
     free(t);
     free(u);
+    free(m);
+}
+
+void ora_dhat(const int d[4], const ocplx *U, double kappa, const ocplx *in, ocplx *out,
+              int dagger)
+{
+    ora_dhat_c(d, U, kappa, NULL, NULL, in, out, dagger);
 }
 
 ocplx ora_dot(const int d[4], const ocplx *a, const ocplx *b, int mask)
@@ -119,13 +153,14 @@ double ora_norm2(const int d[4], const ocplx *a, int mask)
     return creal(ora_dot(d, a, a, mask));
 }
 
-/* A = M^+ M with M = D (full, with clover term C if given) or Dhat (even sites) */
-static void apply_A(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo, const ocplx *in,
-                    ocplx *out, ocplx *tmp)
+/* A = M^+ M with M = D (full, with clover term C if given) or Dhat (even sites; with
+ * C, Minv = (1 + C)^{-1} on odd sites) */
+static void apply_A(const int d[4], const ocplx *U, double kappa, const ocplx *C, const ocplx *Minv, int eo,
+                    const ocplx *in, ocplx *out, ocplx *tmp)
 {
     if (eo) {
-        ora_dhat(d, U, kappa, in, tmp, 0);
-        ora_dhat(d, U, kappa, tmp, out, 1);
+        ora_dhat_c(d, U, kappa, C, Minv, in, tmp, 0);
+        ora_dhat_c(d, U, kappa, C, Minv, tmp, out, 1);
     } else {
         ora_dirac_c(d, U, kappa, C, in, tmp, 0);
         ora_dirac_c(d, U, kappa, C, tmp, out, 1);
@@ -147,6 +182,11 @@ int ora_cg_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int e
     ocplx *p = malloc(n * sizeof(ocplx));
     ocplx *Ap = malloc(n * sizeof(ocplx));
     ocplx *tmp = malloc(n * sizeof(ocplx));
+    ocplx *Minv = NULL;
+    if (eo && C) {
+        Minv = calloc(n * 12, sizeof(ocplx));
+        ora_clover_inverse_odd(d, C, Minv);
+    }
     double bb = ora_norm2(d, b, mask);
     for (long i = 0; i < n; ++i) { x[i] = 0; r[i] = b[i]; p[i] = b[i]; }
     double rr = bb;
@@ -154,14 +194,14 @@ int ora_cg_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int e
     double res = (bb > 0) ? 1.0 : 0.0;
     if (bb == 0) converged = 1;
     while (!converged && k < max_iter) {
-        apply_A(d, U, kappa, C, eo, p, Ap, tmp);
+        apply_A(d, U, kappa, C, Minv, eo, p, Ap, tmp);
         double pAp = creal(ora_dot(d, p, Ap, mask));
         double alpha = rr / pAp;
         for (long i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * Ap[i]; }
         double rr_new = ora_norm2(d, r, mask);
         ++k;
         if (rr_new <= tol * tol * bb) {
-            apply_A(d, U, kappa, C, eo, x, Ap, tmp);
+            apply_A(d, U, kappa, C, Minv, eo, x, Ap, tmp);
             for (long i = 0; i < n; ++i) r[i] = b[i] - Ap[i];
             rr_new = ora_norm2(d, r, mask);
             res = sqrt(rr_new / bb);
@@ -172,12 +212,12 @@ int ora_cg_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int e
         rr = rr_new;
     }
     if (!converged) {
-        apply_A(d, U, kappa, C, eo, x, Ap, tmp);
+        apply_A(d, U, kappa, C, Minv, eo, x, Ap, tmp);
         for (long i = 0; i < n; ++i) r[i] = b[i] - Ap[i];
         res = sqrt(ora_norm2(d, r, mask) / bb);
     }
     if (true_res) *true_res = res;
-    free(r); free(p); free(Ap); free(tmp);
+    free(r); free(p); free(Ap); free(tmp); free(Minv);
     return converged ? k : -k;
 }
 
@@ -199,9 +239,20 @@ double ora_pf_action_c(const int d[4], const ocplx *U, double kappa, const ocplx
     double res;
     int it = ora_cg_c(d, U, kappa, C, eo, phi, chi, tol, max_iter, &res);
     if (iters) *iters = it;
-    if (eo) ora_dhat(d, U, kappa, chi, eta, 0);
-    else ora_dirac_c(d, U, kappa, C, chi, eta, 0);
-    double S = 2 * creal(ora_dot(d, phi, chi, mask)) - ora_norm2(d, eta, mask);
+    double S_det = 0.0;
+    if (eo && C) {
+        /* det(D^+ D) = det(M_oo)^2 det(Dhat^+ Dhat): the odd-site clover determinant is
+         * part of the even-odd action, -2 ln det M_oo */
+        ocplx *Minv = calloc(n * 12, sizeof(ocplx));
+        S_det = -2.0 * ora_clover_inverse_odd(d, C, Minv);
+        ora_dhat_c(d, U, kappa, C, Minv, chi, eta, 0);
+        free(Minv);
+    } else if (eo) {
+        ora_dhat(d, U, kappa, chi, eta, 0);
+    } else {
+        ora_dirac_c(d, U, kappa, C, chi, eta, 0);
+    }
+    double S = 2 * creal(ora_dot(d, phi, chi, mask)) - ora_norm2(d, eta, mask) + S_det;
     free(chi);
     free(eta);
     return S;
@@ -291,8 +342,11 @@ void ora_fermion_grad_xy(const int d[4], double kappa, const ocplx *X, const ocp
 }
 
 /* X and Y of the force: full lattice X = chi, Y = D chi; even-odd
- * X = (chi_e, kappa H_oe chi_e), Y = (eta_e, kappa (H^+)_oe eta_e), eta_e = Dhat chi_e,
- * from eta_e^+ (delta Dhat) chi_e = Y^+ (-kappa delta H) X. */
+ * X = (chi_e, kappa M_oo^{-1} H_oe chi_e), Y = (eta_e, kappa M_oo^{-1} (H^+)_oe eta_e),
+ * eta_e = Dhat chi_e (M_oo = 1 without a clover term), from
+ *   eta_e^+ (delta Dhat) chi_e = Y^+ (-kappa delta H + delta A) X
+ * (delta Dhat = delta A_ee - kappa^2 delta H_eo M^{-1} H_oe - kappa^2 H_eo M^{-1} delta H_oe
+ *  + kappa^2 H_eo M^{-1} delta A_oo M^{-1} H_oe, the last term being Y_o^+ delta A_oo X_o). */
 int ora_force_vectors_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo,
                         const ocplx *phi, double tol, int max_iter, ocplx *X, ocplx *Y)
 {
@@ -303,18 +357,26 @@ int ora_force_vectors_c(const int d[4], const ocplx *U, double kappa, const ocpl
         ora_dirac_c(d, U, kappa, C, X, Y, 0);
         return it;
     }
-    ora_dhat(d, U, kappa, X, Y, 0);            /* eta_e on even sites, 0 on odd */
+    ocplx *Minv = NULL;
+    if (C) {
+        Minv = calloc(n * 12, sizeof(ocplx));
+        ora_clover_inverse_odd(d, C, Minv);
+    }
+    ora_dhat_c(d, U, kappa, C, Minv, X, Y, 0);   /* eta_e on even sites, 0 on odd */
     ocplx *t = calloc(n, sizeof(ocplx));
-    ora_hop(d, U, X, t, 2, 0);
-    for (long x = 0; x < ora_volume(d); ++x)
-        if (ora_parity(d, x) == 1)
-            for (int i = 0; i < 12; ++i) X[x * 12 + i] = kappa * t[x * 12 + i];
-    memset(t, 0, n * sizeof(ocplx));
-    ora_hop(d, U, Y, t, 2, 1);
-    for (long x = 0; x < ora_volume(d); ++x)
-        if (ora_parity(d, x) == 1)
-            for (int i = 0; i < 12; ++i) Y[x * 12 + i] = kappa * t[x * 12 + i];
+    ocplx *t2 = calloc(n, sizeof(ocplx));
+    for (int which = 0; which < 2; ++which) {
+        ocplx *F = which ? Y : X;
+        memset(t, 0, n * sizeof(ocplx));
+        ora_hop(d, U, F, t, 2, which);
+        if (C) site_apply(d, Minv, 1, t, t2);
+        for (long x = 0; x < ora_volume(d); ++x)
+            if (ora_parity(d, x) == 1)
+                for (int i = 0; i < 12; ++i) F[x * 12 + i] = kappa * (C ? t2 : t)[x * 12 + i];
+    }
     free(t);
+    free(t2);
+    free(Minv);
     return it;
 }
 

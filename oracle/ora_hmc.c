@@ -2,7 +2,8 @@
  * ora_hmc.c -- molecular dynamics and one HMC trajectory with the left update
  * of Eq. S2.1 / S2.2: leapfrog (PQP), Omelyan 2MN, or a Sexton-Weingarten
  * nested leapfrog (gauge force on the inner time scale), Metropolis on Delta H.
- * The pseudofermion operator may carry the clover term (full lattice, csw).
+ * The pseudofermion operator may carry the clover term (csw; full lattice or even-odd,
+ * the even-odd action with its -2 ln det M_oo).
  * With stout smearing the pseudofermion action sees the smeared links and its
  * force is taken back through every level (the reverse recursion of Eq. 3);
  * the gauge action sees the thin links.
@@ -44,7 +45,8 @@ int ora_md_force_part(const int d[4], const ocplx *U, const ora_hmc_params *p, c
     if (p->n_stout == 0 && p->csw == 0.0) {
         it = ora_pf_force(d, U, p->kappa, p->eo, phi, p->tol_md, p->max_iter, 1.0, F);
     } else if (p->n_stout == 0) {
-        it = ora_pf_force_sw(d, U, p->kappa, p->csw, phi, p->tol_md, p->max_iter, 1.0, F);
+        it = p->eo ? ora_pf_force_sw_eo(d, U, p->kappa, p->csw, phi, p->tol_md, p->max_iter, 1.0, F)
+                   : ora_pf_force_sw(d, U, p->kappa, p->csw, phi, p->tol_md, p->max_iter, 1.0, F);
     } else {
         ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
         ocplx *G = malloc(sizeof(ocplx) * 36 * V);
@@ -52,6 +54,8 @@ int ora_md_force_part(const int d[4], const ocplx *U, const ora_hmc_params *p, c
         double *Ff = malloc(sizeof(double) * 32 * V);
         if (p->csw == 0.0)
             it = ora_pf_action_grad(d, lv[p->n_stout], p->kappa, p->eo, phi, p->tol_md, p->max_iter, G);
+        else if (p->eo)
+            it = ora_pf_action_grad_sw_eo(d, lv[p->n_stout], p->kappa, p->csw, phi, p->tol_md, p->max_iter, G);
         else
             it = ora_pf_action_grad_sw(d, lv[p->n_stout], p->kappa, p->csw, phi, p->tol_md, p->max_iter, G);
         for (int k = p->n_stout; k >= 1; --k) {
@@ -78,7 +82,8 @@ static double pf_action_smeared(const int d[4], const ocplx *U, const ora_hmc_pa
     ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
     double S = (p->csw == 0.0)
                    ? ora_pf_action(d, lv[p->n_stout], p->kappa, p->eo, phi, p->tol_action, p->max_iter, it)
-                   : ora_pf_action_sw(d, lv[p->n_stout], p->kappa, p->csw, phi, p->tol_action, p->max_iter, it);
+               : p->eo ? ora_pf_action_sw_eo(d, lv[p->n_stout], p->kappa, p->csw, phi, p->tol_action, p->max_iter, it)
+                       : ora_pf_action_sw(d, lv[p->n_stout], p->kappa, p->csw, phi, p->tol_action, p->max_iter, it);
     free_levels(lv, p->n_stout);
     return S;
 }
@@ -169,10 +174,12 @@ int ora_hmc_trajectory(const int d[4], ocplx *U, const ora_hmc_params *p, uint64
         ora_gaussian_spinor(d, seed, traj, ORA_FIELD_XI, mask, xi);
         /* phi = M^+ xi on the links the pseudofermion action sees: S_f(old) = xi^+ xi */
         ocplx **lv = smear_levels(d, U, p->n_stout, p->rho);
-        if (p->eo) ora_dhat(d, lv[p->n_stout], p->kappa, xi, phi, 1);
+        if (p->eo) ora_dhat_sw(d, lv[p->n_stout], p->kappa, p->csw, xi, phi, 1);
         else ora_dirac_sw(d, lv[p->n_stout], p->kappa, p->csw, xi, phi, 1);
-        free_levels(lv, p->n_stout);
         res->Sf_old = ora_norm2(d, xi, mask);
+        /* the even-odd clover action also holds -2 ln det M_oo */
+        if (p->eo && p->csw != 0.0) res->Sf_old -= 2.0 * ora_clover_logdet_odd(d, lv[p->n_stout], p->kappa, p->csw);
+        free_levels(lv, p->n_stout);
     }
     int evals = 0;
     res->cg_iters = integrate(d, U, mom, phi, p, &evals);

@@ -27,6 +27,12 @@ double ora_pf_action_c(const int d[4], const ocplx *U, double kappa, const ocplx
                        double tol, int max_iter, int *iters);
 int ora_force_vectors_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, int eo,
                         const ocplx *phi, double tol, int max_iter, ocplx *X, ocplx *Y);
+/* Dhat with the clover term C (NULL: Wilson) and Minv = (1 + C)^{-1} on odd sites */
+void ora_dhat_c(const int d[4], const ocplx *U, double kappa, const ocplx *C, const ocplx *Minv,
+                const ocplx *in, ocplx *out, int dagger);
+/* (1 + C(x))^{-1} on odd sites x into Minv ([V][12][12], even sites untouched); returns
+ * the sum over odd sites of ln det (1 + C(x)) */
+double ora_clover_inverse_odd(const int d[4], const ocplx *C, ocplx *Minv);
 /* real-component gradient of the hopping part of S_f from X, Y (written to G) */
 void ora_fermion_grad_xy(const int d[4], double kappa, const ocplx *X, const ocplx *Y, ocplx *G);
 

@@ -115,7 +115,7 @@ double ora_gauge_action_imp(const int d[4], const ocplx *U, double beta, double 
 void ora_gauge_force_imp(const int d[4], const ocplx *U, double beta, double c1, double coef, double *F);
 void ora_gauge_action_grad_imp(const int d[4], const ocplx *U, double beta, double c1, ocplx *G);
 
-/* clover (Sheikholeslami-Wohlert) term, full lattice only:
+/* clover (Sheikholeslami-Wohlert) term, full lattice (below: even-odd form):
  * D_sw = 1 - kappa H + A, A(x) = -kappa c_sw sum_{mu<nu} sigma_munu F_munu(x),
  * sigma_munu = (i/2)[g_mu, g_nu], F_munu = (Q_munu - Q_munu^+)/(8i), Q the four leaves */
 void ora_clover_field_strength(const int d[4], const ocplx *U, int mu, int nu, ocplx *F);   /* [V][3][3] */
@@ -130,6 +130,21 @@ int ora_pf_action_grad_sw(const int d[4], const ocplx *U, double kappa, double c
                           double tol, int max_iter, ocplx *G);
 int ora_pf_force_sw(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *phi, double tol,
                     int max_iter, double coef, double *F);
+/* even-odd form: Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe (M = 1 + A) on even half fields
+ * (canonical full fields, odd sites ignored / zero), the sum over odd sites of ln det M,
+ * CG on Dhat^+ Dhat, S_f = phi_e^+ (Dhat^+ Dhat)^{-1} phi_e - 2 ln det M_oo, its
+ * real-component gradient and its force */
+void ora_dhat_sw(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *in, ocplx *out,
+                 int dagger);
+double ora_clover_logdet_odd(const int d[4], const ocplx *U, double kappa, double csw);
+int ora_cg_sw_eo(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *b, ocplx *x, double tol,
+                 int max_iter, double *true_res);
+double ora_pf_action_sw_eo(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *phi,
+                           double tol, int max_iter, int *iters);
+int ora_pf_action_grad_sw_eo(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *phi,
+                             double tol, int max_iter, ocplx *G);
+int ora_pf_force_sw_eo(const int d[4], const ocplx *U, double kappa, double csw, const ocplx *phi, double tol,
+                       int max_iter, double coef, double *F);
 
 /* ---------------- link update ---------------- */
 /* U <- exp(i eps Pi) U for every link (Eq. S2.1), Pi = sum_a mom_a T^a */
@@ -161,7 +176,7 @@ typedef struct {
     int n_stout;         /* stout levels in front of the Wilson operator (S_G: thin links) */
     double rho;
     double c1;           /* rectangle coefficient of the gauge action (0: Wilson) */
-    double csw;          /* clover coefficient of the pseudofermion operator (full lattice only) */
+    double csw;          /* clover coefficient of the pseudofermion operator (full lattice or even-odd) */
 } ora_hmc_params;
 
 /* parts of the MD force: 0 all, 1 gauge only, 2 fermion only */

@@ -183,3 +183,34 @@ def test_clover_hmc_reversible_and_dt_squared(ora):
         Ux, mx, _ = ora.md_integrate(D4, U, mom, phi, pp)
         dh.append(abs(energy(Ux, mx, pp) - energy(U, mom, pp)))
     assert 3.2 < dh[0] / dh[1] < 4.8, dh
+
+
+def test_even_odd_clover_hmc_reversible_and_dt_squared(ora):
+    """Even-odd Wilson-clover fermions (c_sw = 1.5; the action carries -2 ln det M_oo):
+    the integrator is reversible, Delta H falls by ~4 when the leapfrog step halves, and a
+    trajectory's S_f(old) is xi^+ xi - 2 ln det M_oo."""
+    global ORA
+    ORA = ora
+    U, mom = _setup(seed=11)
+    phi = synth.gaussian_spinor(D4, 12, parity_mask=1)
+    p = ora.hmc_params(5.7, 0.13, eo=True, integrator="leapfrog", n_steps=5, tau=0.5, tol_md=1e-14, csw=1.5)
+    U1, m1, _ = ora.md_integrate(D4, U, mom, phi, p)
+    U2, m2, _ = ora.md_integrate(D4, U1, -m1, phi, p)
+    assert H.rel(U2, U) < 1e-11 and H.rel(-m2, mom) < 1e-10
+
+    def energy(Ux, mx, pp):
+        return (ora.gauge_action(D4, Ux, pp.beta) + ora.momentum_energy(D4, mx)
+                + ora.pf_action_sw_eo(D4, Ux, pp.kappa, pp.csw, phi, tol=1e-14)[0])
+
+    dh = []
+    for n in (10, 20):
+        pp = ora.hmc_params(5.7, 0.13, eo=True, integrator="leapfrog", n_steps=n, tau=1.0, tol_md=1e-14, csw=1.5)
+        Ux, mx, _ = ora.md_integrate(D4, U, mom, phi, pp)
+        dh.append(abs(energy(Ux, mx, pp) - energy(U, mom, pp)))
+    assert 3.2 < dh[0] / dh[1] < 4.8, dh
+    pt = ora.hmc_params(5.7, 0.13, eo=True, integrator="leapfrog", n_steps=4, tau=0.4, tol_md=1e-13,
+                        tol_action=1e-13, csw=1.5)
+    _, r = ora.hmc_trajectory(D4, U, pt, 21, 0)
+    xi = ora.gaussian_spinor(D4, 21, 0, ora.FIELD_XI, 1)
+    S_old = float(np.vdot(xi, xi).real) - 2 * ora.clover_logdet_odd(D4, U, 0.13, 1.5)
+    assert abs(r["Sf_old"] - S_old) < 1e-10 * abs(S_old)

@@ -529,3 +529,98 @@ def test_clover_force_and_gradient_finite_difference(ora):
     # c_sw = 0 is the Wilson force
     F0, _ = ora.pf_force_sw(d, U, kappa, 0.0, phi, tol=1e-14)
     assert H.rel(F0, ora.pf_force(d, U, kappa, phi, tol=1e-14)[0]) < 1e-10
+
+
+# ---------------------------------------------------------------- even-odd clover
+def _dense(apply, n):
+    """Dense matrix of a linear map on C^n from its action on the unit vectors."""
+    M = np.zeros((n, n), np.complex128)
+    for k in range(n):
+        e = np.zeros(n, np.complex128)
+        e[k] = 1.0
+        M[:, k] = apply(e)
+    return M
+
+
+def test_clover_even_odd_schur_complement_and_determinant(ora):
+    """On a 2x2x2x4 lattice the dense clover operator D is built column by column; with
+    sites ordered even then odd, its Schur complement D_ee - D_eo D_oo^{-1} D_oe (numpy)
+    is the oracle's Dhat, det D = det D_oo det Dhat, and ln det D_oo is the oracle's sum
+    over odd sites of ln det (1 + A) (D_oo is site-diagonal: no hop joins two odd sites)."""
+    d = (2, 2, 2, 4)
+    V = int(np.prod(d))
+    U = synth.random_links(d, 0.5, 301)
+    kappa, csw = 0.13, 1.7
+    par = synth.parity(d)
+    ev, od = np.where(par == 0)[0], np.where(par == 1)[0]
+
+    def full_apply(vec):
+        return ora.dirac_sw(d, U, kappa, csw, vec.reshape(V, 4, 3)).reshape(-1)
+
+    D = _dense(full_apply, V * 12)
+    idx_e = (ev[:, None] * 12 + np.arange(12)[None, :]).reshape(-1)
+    idx_o = (od[:, None] * 12 + np.arange(12)[None, :]).reshape(-1)
+    Dee, Deo = D[np.ix_(idx_e, idx_e)], D[np.ix_(idx_e, idx_o)]
+    Doe, Doo = D[np.ix_(idx_o, idx_e)], D[np.ix_(idx_o, idx_o)]
+    schur = Dee - Deo @ np.linalg.solve(Doo, Doe)
+
+    def dhat_apply(vec):
+        full = np.zeros(V * 12, np.complex128)
+        full[idx_e] = vec
+        return ora.dhat_sw(d, U, kappa, csw, full.reshape(V, 4, 3)).reshape(-1)[idx_e]
+
+    Dhat = _dense(dhat_apply, len(idx_e))
+    assert np.abs(Dhat - schur).max() < 1e-12 * np.abs(schur).max()
+    s_full, l_full = np.linalg.slogdet(D)
+    s_oo, l_oo = np.linalg.slogdet(Doo)
+    s_hat, l_hat = np.linalg.slogdet(Dhat)
+    assert abs(l_full - (l_oo + l_hat)) < 1e-9 * abs(l_full)
+    assert abs(s_full - s_oo * s_hat) < 1e-9
+    # D_oo = 1 + A_oo is Hermitian positive definite: det real positive
+    assert abs(s_oo - 1.0) < 1e-12
+    assert abs(ora.clover_logdet_odd(d, U, kappa, csw) - l_oo) < 1e-10 * abs(l_oo)
+    # the adjoint: gamma5 Dhat gamma5 = Dhat^+
+    def dhat_dag_apply(vec):
+        full = np.zeros(V * 12, np.complex128)
+        full[idx_e] = vec
+        return ora.dhat_sw(d, U, kappa, csw, full.reshape(V, 4, 3), dagger=True).reshape(-1)[idx_e]
+    assert np.abs(_dense(dhat_dag_apply, len(idx_e)) - Dhat.conj().T).max() < 1e-12 * np.abs(schur).max()
+
+
+def test_clover_even_odd_action_force_finite_difference(ora):
+    """S_f = phi_e^+ (Dhat^+ Dhat)^{-1} phi_e - 2 ln det M_oo: the Lie force against central
+    differences in Lie directions (links on both parities, so the determinant term and both
+    clover insertions are exercised), the real-component gradient against differences on
+    entries, and c_sw = 0 giving the Wilson even-odd force."""
+    d = (4, 4, 4, 4)
+    U = synth.random_links(d, 0.5, 302)
+    kappa, csw = 0.13, 1.5
+    phi = synth.gaussian_spinor(d, 303, parity_mask=1)
+    F, _ = ora.pf_force_sw_eo(d, U, kappa, csw, phi, tol=1e-14)
+    h = 1e-5
+    for (s, mu) in LINKS:
+        for a in (0, 4, 7):
+            Sp, _ = ora.pf_action_sw_eo(d, H.lie_perturb(U, s, mu, a, h), kappa, csw, phi, tol=1e-14)
+            Sm, _ = ora.pf_action_sw_eo(d, H.lie_perturb(U, s, mu, a, -h), kappa, csw, phi, tol=1e-14)
+            fd = (Sp - Sm) / (2 * h)
+            assert abs(fd - F[s, mu, a]) < 2e-6 * max(1.0, abs(F[s, mu, a])), (s, mu, a, fd, F[s, mu, a])
+    G, _ = ora.pf_action_grad_sw_eo(d, U, kappa, csw, phi, tol=1e-14)
+    h = 3e-5
+    for (s, mu) in LINKS[:2]:
+        for (i, j) in ((0, 2), (1, 1)):
+            for unit, part in ((1.0, "re"), (1j, "im")):
+                Up = U.copy(); Up[s, mu, i, j] += h * unit
+                Um = U.copy(); Um[s, mu, i, j] -= h * unit
+                fd = (ora.pf_action_sw_eo(d, Up, kappa, csw, phi, tol=1e-14)[0]
+                      - ora.pf_action_sw_eo(d, Um, kappa, csw, phi, tol=1e-14)[0]) / (2 * h)
+                ga = G[s, mu, i, j].real if part == "re" else G[s, mu, i, j].imag
+                assert abs(fd - ga) < 3e-6 * max(1.0, abs(ga))
+    F0, _ = ora.pf_force_sw_eo(d, U, kappa, 0.0, phi, tol=1e-14)
+    assert H.rel(F0, ora.pf_force(d, U, kappa, phi, eo=True, tol=1e-14)[0]) < 1e-10
+    # the determinant term alone: its force is that of -2 sum_odd ln det M (phi = 0)
+    Fd, _ = ora.pf_force_sw_eo(d, U, kappa, csw, np.zeros_like(phi), tol=1e-14)
+    for (s, mu) in LINKS[:3]:
+        a = 2
+        Lp = ora.clover_logdet_odd(d, H.lie_perturb(U, s, mu, a, h), kappa, csw)
+        Lm = ora.clover_logdet_odd(d, H.lie_perturb(U, s, mu, a, -h), kappa, csw)
+        assert abs(-2 * (Lp - Lm) / (2 * h) - Fd[s, mu, a]) < 1e-6 * max(1.0, abs(Fd[s, mu, a]))
