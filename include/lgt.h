@@ -123,8 +123,13 @@ typedef struct {
                             of Sec. IV): D = 1 - kappa H + A, A(x) = -kappa csw sum_{mu<nu}
                             sigma_munu F_munu(x), sigma_munu = (i/2)[g_mu, g_nu], F_munu =
                             (Q_munu - Q_munu^+)/(8i) with Q_munu the four plaquettes (leaves) of
-                            the mu-nu plane at x.  Full-lattice action only (even_odd = 1 with
-                            csw != 0 is LGT_EINVAL); the clover force is FP64 arithmetic. */
+                            the mu-nu plane at x.  With even_odd = 1, M = 1 + A and
+                            Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe (M_oo^{-1} by Cholesky of the
+                            two 6x6 chiral blocks per odd site), and S_f = phi_e^+ (Dhat^+
+                            Dhat)^{-1} phi_e - 2 ln det M_oo (det D = det M_oo det Dhat); its force
+                            adds the insertion of M_oo^{-1} to the clover force.  1 + A must be
+                            positive definite on the odd sites (else LGT_ENAN).  The clover
+                            force is FP64 arithmetic; chronological guesses are not used. */
 } lgt_action_params;
 
 typedef struct {
@@ -241,8 +246,10 @@ int lgt_unpack_links_field(lgt_lattice_t lat, const double *field, double *canon
 /* ------------------------------------------------------------------ operators */
 /* Attach the clover term with coefficient csw (see lgt_action_params.csw) for hopping
  * parameter kappa, built from the handle's current links, to the operators that act
- * on them directly: lgt_dslash with LGT_OP_D and the full-lattice lgt_cg_solve (use the
- * same kappa there).  csw = 0 detaches it.  It is not refreshed when the links change.
+ * on them directly: lgt_dslash (LGT_OP_D, and LGT_OP_DHAT / LGT_OP_DHAT_NORMAL as the
+ * even-odd clover Dhat) and lgt_cg_solve (use the same kappa there).  csw = 0 detaches
+ * it.  It is not refreshed when the links change (LGT_ENAN if 1 + A is not positive
+ * definite on some odd site).
  * lgt_action, lgt_force, lgt_md_update and lgt_hmc_trajectory take the clover term
  * from lgt_action_params.csw instead.  Synchronous. */
 int lgt_set_clover(lgt_lattice_t lat, double csw, double kappa);

@@ -100,6 +100,11 @@ struct Links {
     // clover term 1 + A of these links (null: Wilson operator)
     const double2* C64 = nullptr;
     const float4* C32 = nullptr;
+    // even-odd form: (1 + A)^{-1} on odd sites (layout of C64 / C32) and the sum over the
+    // odd sites of ln det (1 + A)
+    const double2* I64 = nullptr;
+    const float4* I32 = nullptr;
+    double logdet_odd = 0.0;
 };
 
 struct lgt_lattice {
@@ -129,6 +134,9 @@ struct lgt_lattice {
     // the insertion field of the clover force
     double2 *thin_c64, *call_c64, *cins;
     float4 *thin_c32, *call_c32;
+    // (1 + A)^{-1} on odd sites for the even-odd form, of the thin and of the call links
+    double2 *thin_i64, *call_i64;
+    float4 *thin_i32, *call_i32;
     double2* ct64;
     float4* ct32;
     // several right-hand sides (lgt_cg_solve_multi): per system FP32 even/odd half
@@ -246,10 +254,14 @@ static int ensure_multi(lgt_lattice* L) {
 
 static int ensure_clover(lgt_lattice* L, bool thin) {
     const size_t c64 = (size_t)2 * 72 * L->g.Vh * sizeof(double2), c32 = (size_t)2 * 36 * L->g.Vh * sizeof(float4);
-    if (thin && !L->thin_c64) { TRY(A(L, c64, &L->thin_c64)); TRY(A(L, c32, &L->thin_c32)); }
+    if (thin && !L->thin_c64) {
+        TRY(A(L, c64, &L->thin_c64)); TRY(A(L, c32, &L->thin_c32));
+        TRY(A(L, c64, &L->thin_i64)); TRY(A(L, c32, &L->thin_i32));
+    }
     if (!thin && !L->call_c64) {
         TRY(A(L, c64, &L->call_c64));
         TRY(A(L, c32, &L->call_c32));
+        TRY(A(L, c64, &L->call_i64)); TRY(A(L, c32, &L->call_i32));
         TRY(A(L, (size_t)2 * 54 * L->g.Vh * sizeof(double2), &L->cins));
     }
     if (!L->ct64) { TRY(A(L, spinor64_full(L), &L->ct64)); TRY(A(L, spinor32_full(L), &L->ct32)); }
@@ -361,6 +373,8 @@ static int ensure_stout(lgt_lattice* L, int n, int m) {
 
 static RedArgs red(lgt_lattice* L) { return RedArgs{L->s, L->partials, L->counter, L->n_partials}; }
 
+
+
 static int sync_scalars(lgt_lattice* L) {
     CK(cudaMemcpyAsync(L->hs, L->s, sizeof(Scalars), cudaMemcpyDeviceToHost, L->st));
     CK(cudaStreamSynchronize(L->st));
@@ -368,6 +382,19 @@ static int sync_scalars(lgt_lattice* L) {
 }
 static int push_scalars(lgt_lattice* L) {
     CK(cudaMemcpyAsync(L->s, L->hs, sizeof(Scalars), cudaMemcpyHostToDevice, L->st));
+    return LGT_OK;
+}
+
+// (1 + A)^{-1} on the odd sites of lk's clover term into I64 / I32, and the sum of
+// ln det (1 + A) over them (synchronous: the sum is read back)
+static int clover_inverse_odd(lgt_lattice* L, Links* lk, double2* I64, float4* I32) {
+    CK(clover_invert(lk->C64, L->g, 1, I64, I32, red(L), 5, L->st));
+    TRY(sync_scalars(L));
+    if (!std::isfinite(L->hs->slot[5]))
+        return fail(LGT_ENAN, "the clover term 1 + A is not positive definite on some odd site");
+    lk->I64 = I64;
+    lk->I32 = I32;
+    lk->logdet_odd = L->hs->slot[5];
     return LGT_OK;
 }
 
@@ -708,6 +735,19 @@ static int dfull(lgt_lattice* L, const Links& lk, bool fp64, bool dag, const voi
 // Dhat^(+) on even half fields: out = in - kappa^2 H_eo H_oe in, tmp an odd half field
 static int dhat(lgt_lattice* L, const Links& lk, bool fp64, bool dag, const void* in, void* out, void* tmp,
                 double kappa) {
+    if (lk.C64) {
+        // with the clover term: Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe, M = 1 + A Hermitian
+        // (tmp: odd intermediate; the clover temporaries hold M_oo^{-1} tmp and M_ee in)
+        if (!lk.I64) return fail(LGT_EINVAL, "the even-odd clover operator needs (1 + A)^{-1} on odd sites");
+        void* ct = fp64 ? (void*)L->ct64 : (void*)L->ct32;
+        void* t2 = half(ct, L, fp64, 1);
+        void* y = half(ct, L, fp64, 0);
+        TRY(hop1(L, lk, fp64, dag, 1, in, tmp, 1.0));
+        CK(clover_apply(fp64 ? (const void*)lk.I64 : (const void*)lk.I32, tmp, t2, L->g, 1, fp64, L->st));
+        CK(clover_apply(fp64 ? (const void*)lk.C64 : (const void*)lk.C32, in, y, L->g, 0, fp64, L->st));
+        TRY(hop1(L, lk, fp64, dag, 0, t2, out, -kappa * kappa, EPI_XPAY, y));
+        return LGT_OK;
+    }
     TRY(hop1(L, lk, fp64, dag, 1, in, tmp, 1.0));
     TRY(hop1(L, lk, fp64, dag, 0, tmp, out, -kappa * kappa, EPI_XPAY, in));
     return LGT_OK;
@@ -718,13 +758,24 @@ extern "C" int lgt_set_clover(lgt_lattice_t L, double csw, double kappa) {
     if (csw == 0.0) {
         L->thin.C64 = nullptr;
         L->thin.C32 = nullptr;
+        L->thin.I64 = nullptr;
+        L->thin.I32 = nullptr;
+        L->thin.logdet_odd = 0.0;
         return LGT_OK;
     }
     TRY(ensure_clover(L, true));
     CK(clover_field(L->thin.U, L->g, clover_sigma(), kappa, csw, L->thin_c64, L->thin_c32, L->st));
-    CK(cudaStreamSynchronize(L->st));
     L->thin.C64 = L->thin_c64;
     L->thin.C32 = L->thin_c32;
+    // the even-odd operators need (1 + A)^{-1} on the odd sites
+    const int rc = clover_inverse_odd(L, &L->thin, L->thin_i64, L->thin_i32);
+    if (rc != LGT_OK) {
+        L->thin.C64 = nullptr;
+        L->thin.C32 = nullptr;
+        L->thin.I64 = nullptr;
+        L->thin.I32 = nullptr;
+        return rc;
+    }
     return LGT_OK;
 }
 
@@ -737,8 +788,6 @@ extern "C" int lgt_set_sweep_order(lgt_lattice_t L, int alternate) {
 extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, int out_parity, int dagger,
                           double kappa, int precision) {
     if (!L || !in || !out) return fail(LGT_EINVAL, "null argument");
-    if (L->thin.C64 && (op == LGT_OP_DHAT || op == LGT_OP_DHAT_NORMAL))
-        return fail(LGT_EINVAL, "the clover term is attached: even-odd operators are not available");
     if (in == out) return fail(LGT_EINVAL, "in and out must be distinct buffers");
     if (precision != LGT_FP64 && precision != LGT_FP32) return fail(LGT_EINVAL, "precision %d", precision);
     const bool fp64 = precision == LGT_FP64;
@@ -768,6 +817,38 @@ extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, in
 // return at once after the stop flag is raised on the device.
 static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, double kappa, void* x, void* r, void* p,
                         void* u, void* t) {
+    if (eo && lk.C64) {
+        // with the clover term (Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe): the odd
+        // intermediate goes through M_oo^{-1}, and M_ee p / M_ee u enter the xpay hops
+        void* ct = fp64 ? (void*)L->ct64 : (void*)L->ct32;
+        void* t2 = half(ct, L, fp64, 1);
+        void* y = half(ct, L, fp64, 0);
+        const void* Iv = fp64 ? (const void*)lk.I64 : (const void*)lk.I32;
+        const void* Cv = fp64 ? (const void*)lk.C64 : (const void*)lk.C32;
+        HopArgs A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 1; A.in[0] = p; A.out[1] = t;
+        CK(timed_hop(A, fp64, false, EPI_HOP, L->st));
+        CK(clover_apply(Iv, t, t2, L->g, 1, fp64, L->st));
+        CK(clover_apply(Cv, p, y, L->g, 0, fp64, L->st));
+        A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 0; A.in[1] = t2; A.out[0] = u; A.y[0] = y; A.a = -kappa * kappa; A.red_op = RED_PAP;
+        CK(timed_hop(A, fp64, false, EPI_XPAY_NORM, L->st));
+        A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 1; A.in[0] = u; A.out[1] = t;
+        CK(timed_hop(A, fp64, true, EPI_HOP, L->st));
+        CK(clover_apply(Iv, t, t2, L->g, 1, fp64, L->st));
+        CK(clover_apply(Cv, u, y, L->g, 0, fp64, L->st));
+        A = hop_base(L, lk, fp64);
+        A.skip = 1;
+        A.parity = 0; A.in[1] = t2; A.y[0] = y; A.a = -kappa * kappa; A.red_op = RED_RR;
+        A.r[0] = r;
+        CK(timed_hop(A, fp64, true, EPI_CG, L->st));
+        CK(blas_cg_p_update(p, r, x, L->g.Vh, L->g.Vh, fp64, red(L), L->st));
+        return LGT_OK;
+    }
     if (eo) {
         // with alternate order on, every launch walks the sites in the direction opposite
         // to the one before, so it starts on the sites whose data the previous launch
@@ -827,10 +908,38 @@ static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, dou
 //   even-odd: X_o = kappa H_oe x, eta = x - kappa H_eo X_o (= Dhat x), Y_o = kappa (H^+)_oe eta,
 //             A x = eta - kappa (H^+)_eo Y_o;
 //   full:     Y = D x, A x = D^+ Y.
+// The force vectors of the even-odd clover operator from x_e (FP64):
+//   X_o = kappa M_oo^{-1} H_oe x_e,  Y_e = M_ee x_e - kappa H_eo X_o (= Dhat x_e),
+//   Y_o = kappa M_oo^{-1} (H^+)_oe Y_e;
+// the odd half of the FP64 clover temporary is the scratch field (Xo and Yo may alias).
+static int eo_clover_xy(lgt_lattice* L, const Links& lk, double kappa, const double2* x, double2* Xo, double2* Ye,
+                        double2* Yo) {
+    double2* cto = (double2*)half(L->ct64, L, true, 1);
+    double2* cte = L->ct64;
+    TRY(hop1(L, lk, true, false, 1, x, cto, kappa));
+    CK(clover_apply(lk.I64, cto, Xo, L->g, 1, true, L->st));
+    CK(clover_apply(lk.C64, x, cte, L->g, 0, true, L->st));
+    TRY(hop1(L, lk, true, false, 0, Xo, Ye, -kappa, EPI_XPAY, cte));
+    TRY(hop1(L, lk, true, true, 1, Ye, cto, kappa));
+    CK(clover_apply(lk.I64, cto, Yo, L->g, 1, true, L->st));
+    return LGT_OK;
+}
+
 static int true_residual(lgt_lattice* L, const Links& lk, bool eo, double kappa, const double2* b, const double2* x,
                          double2* res) {
     const bool cap = L->cap_X && L->cap_Y;
-    if (eo) {
+    if (eo && lk.C64) {
+        // A x = Dhat^+ Y_e = M_ee Y_e - kappa (H^+)_eo Y_o
+        double2* Xo = cap ? (double2*)half(L->cap_X, L, true, 1) : L->t;
+        double2* Ye = cap ? L->cap_Y : L->u;
+        double2* Yo = cap ? (double2*)half(L->cap_Y, L, true, 1) : L->t;
+        TRY(eo_clover_xy(L, lk, kappa, x, Xo, Ye, Yo));
+        CK(clover_apply(lk.C64, Ye, L->ct64, L->g, 0, true, L->st));
+        HopArgs A = hop_base(L, lk, true);
+        A.parity = 0; A.in[1] = Yo; A.y[0] = L->ct64; A.a = -kappa; A.out[0] = res; A.pv[0] = b;
+        A.red_op = RED_STORE; A.red_slot = 0;
+        CK(timed_hop(A, true, true, EPI_RESID, L->st));
+    } else if (eo) {
         double2* Xo = cap ? (double2*)half(L->cap_X, L, true, 1) : L->t;
         double2* Ye = cap ? L->cap_Y : L->u;
         double2* Yo = cap ? (double2*)half(L->cap_Y, L, true, 1) : L->t;
@@ -953,7 +1062,8 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     Scalars* hs = L->hs;
     // start: x = 0, r = b; or the chronological guess x0 with its FP64 residual
     bool guess = false;
-    if (eo && sp->chrono > 0) {
+    // (the guess's FP32 products have no clover term: not used with one)
+    if (eo && sp->chrono > 0 && !lk.C64) {
         TRY(ensure_chrono(L));
         TRY(chrono_guess(L, lk, b, x, kappa, std::min(sp->chrono, CHRONO_MAX), &guess));
     }
@@ -986,7 +1096,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     TRY(push_scalars(L));
     double rr_true = rr0;
     int rc = LGT_OK;
-    const bool record = eo && sp->chrono > 0;
+    const bool record = eo && sp->chrono > 0 && !lk.C64;
     // Near a nearly singular operator the FP32 recursion can break down (<p, Ap> <= 0 from
     // FP32 rounding) or stop reducing the true residual; a chronological guess can then
     // also carry an error in the lowest modes that the FP32 recursion cannot remove, so
@@ -1142,7 +1252,6 @@ static void add_stats(lgt_solve_stats* acc, const lgt_solve_stats& s) {
 extern "C" int lgt_cg_solve(lgt_lattice_t L, const double* b, double* x, double kappa, int even_odd,
                             const lgt_solver_params* sp, lgt_solve_stats* stats) {
     if (!L || !b || !x) return fail(LGT_EINVAL, "null argument");
-    if (L->thin.C64 && even_odd) return fail(LGT_EINVAL, "the clover term is attached: even-odd solve not available");
     if (b == x) return fail(LGT_EINVAL, "b and x must be distinct");
     return cg_core(L, L->thin, (const double2*)b, (double2*)x, kappa, even_odd != 0, sp, stats);
 }
@@ -1358,8 +1467,6 @@ static int check_action(const lgt_action_params* ap) {
     if (ap->n_stout < 0 || ap->n_stout > MAX_STOUT)
         return fail(LGT_EINVAL, "n_stout = %d outside 0..%d", ap->n_stout, MAX_STOUT);
     if (ap->stout_recompute < 0) return fail(LGT_EINVAL, "stout_recompute = %d", ap->stout_recompute);
-    if (ap->csw != 0.0 && ap->even_odd && ap->fermions)
-        return fail(LGT_EINVAL, "the clover term needs the full-lattice action (even_odd = 0)");
     if (ap->force_arith < LGT_ARITH_FP64 || ap->force_arith > LGT_ARITH_DF64)
         return fail(LGT_EINVAL, "force_arith = %d", ap->force_arith);
     return LGT_OK;
@@ -1391,6 +1498,7 @@ static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out
         CK(clover_field(lk.U, L->g, clover_sigma(), ap->kappa, ap->csw, L->call_c64, L->call_c32, L->st));
         lk.C64 = L->call_c64;
         lk.C32 = L->call_c32;
+        if (ap->even_odd) TRY(clover_inverse_odd(L, &lk, L->call_i64, L->call_i32));
     }
     *out = lk;
     return LGT_OK;
@@ -1418,6 +1526,8 @@ static int pf_action_on(lgt_lattice* L, const Links& lk, const lgt_action_params
     CK(blas_action_parts(phi, L->X, L->Y, n, L->g.Vh, red(L), L->st));
     TRY(sync_scalars(L));
     *S_f = 2.0 * L->hs->slot[0] - L->hs->slot[1];
+    // even-odd clover: det(D^+ D) = det(M_oo)^2 det(Dhat^+ Dhat), so S_f holds -2 ln det M_oo
+    if (eo && lk.C64) *S_f -= 2.0 * lk.logdet_odd;
     return LGT_OK;
 }
 
@@ -1463,6 +1573,18 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
     const int rc = cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats);
     L->cap_X = L->cap_Y = nullptr;
     TRY(rc);
+    if (eo && lk.C64) {
+        // the FP64 vectors (from the solver's final residual, else computed here); the
+        // FP32 force arithmetic takes their FP32 copies
+        if (!L->cap_valid)
+            TRY(eo_clover_xy(L, lk, ap->kappa, L->X, (double2*)half(L->X, L, true, 1), L->Y,
+                             (double2*)half(L->Y, L, true, 1)));
+        if (fp32) {
+            CK(blas_d2f(L->X32, L->X, 2 * L->g.Vh, L->g.Vh, L->st));
+            CK(blas_d2f(L->Y32, L->Y, 2 * L->g.Vh, L->g.Vh, L->st));
+        }
+        return LGT_OK;
+    }
     if (fp32) {
         if (eo) {
             float4* Xo = (float4*)half(L->X32, L, false, 1);
@@ -1527,9 +1649,12 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
             CK(fermion_force_df(L->Udf, L->Xdf, L->Ydf, L->g, ap->kappa, coef, keep, out, L->st));
         } else CK(fermion_force(ferm_lk.U, L->X, L->Y, L->g, ap->kappa, coef, keep, form, out, L->st));
         keep = 1;
-        if (ferm_lk.C64) {   // clover part, FP64 from X = chi, Y = D chi (full lattice)
-            if (fp32 && !L->cap_valid) TRY(dfull(L, ferm_lk, true, false, L->X, L->Y, ap->kappa));
+        if (ferm_lk.C64) {   // clover part, FP64 from X, Y (full lattice: X = chi, Y = D chi)
+            if (fp32 && !L->cap_valid && !ap->even_odd) TRY(dfull(L, ferm_lk, true, false, L->X, L->Y, ap->kappa));
             CK(clover_insertion(L->X, L->Y, L->g, clover_sigma(), ap->kappa, ap->csw, L->cins, L->st));
+            // even-odd: the odd-site determinant -2 ln det M_oo
+            if (ap->even_odd)
+                CK(clover_det_insertion(ferm_lk.I64, L->g, 1, clover_sigma(), ap->kappa, ap->csw, L->cins, L->st));
             CK(clover_force(ferm_lk.U, L->cins, L->g, coef, 1, form, out, L->st));
         }
     }
@@ -1805,6 +1930,7 @@ extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, 
         CK(blas_norm2(L->xi, eo ? L->g.Vh : 2 * L->g.Vh, L->g.Vh, true, red(L), 0, L->st));
         TRY(sync_scalars(L));
         res->Sf_old = L->hs->slot[0];
+        if (eo && lk.C64) res->Sf_old -= 2.0 * lk.logdet_odd;
     }
     int evals = 0;
     TRY(integrate(L, ap, hp, L->phi, &res->total, &evals));

@@ -308,4 +308,122 @@ cudaError_t clover_force(const double2* U, const double2* M, const Geom& g, doub
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- even-odd form
+// M = 1 + A on the sites of one parity: its inverse, block by block (Cholesky of the
+// Hermitian positive definite 6x6 chiral block, M = L L^+, M^{-1} = L^{-+} L^{-1}), in
+// the layout of the clover field, and ln det M = 2 sum ln L_ii summed over the sites
+// (fixed-order reduction into the scalars' slot).
+__global__ void __launch_bounds__(NT) clover_invert_kernel(const double2* C64, Geom g, int parity, double2* I64,
+                                                           float4* I32, RedArgs R, int slot) {
+    const int i = blockIdx.x * NT + threadIdx.x;
+    double logdet = 0.0;
+    if (i < g.Vh) {
+        const double2* cb = C64 + (size_t)parity * 72 * g.Vh + i;
+        double2* o64 = I64 + (size_t)parity * 72 * g.Vh + i;
+        float4* o32 = I32 + (size_t)parity * 36 * g.Vh + i;
+        dcx pending = {0, 0};   // FP32 float4 k holds entries 2k, 2k+1 (36 is even: no pair spans blocks)
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            dcx L[6][6];
+            for (int r = 0; r < 6; ++r)
+                for (int q = 0; q < 6; ++q) {
+                    const double2 z = __ldg(cb + (size_t)(36 * c + 6 * r + q) * g.Vh);
+                    L[r][q] = {z.x, z.y};
+                }
+            // Cholesky, lower triangle in place (the diagonal real and positive)
+            for (int j = 0; j < 6; ++j) {
+                double dj = L[j][j].r;
+                for (int k = 0; k < j; ++k) dj -= L[j][k].r * L[j][k].r + L[j][k].i * L[j][k].i;
+                dj = sqrt(dj);
+                logdet += 2.0 * log(dj);
+                L[j][j] = {dj, 0.0};
+                const double inv = 1.0 / dj;
+                for (int r = j + 1; r < 6; ++r) {
+                    dcx s = L[r][j];
+                    for (int k = 0; k < j; ++k) s = s - L[r][k] * conj(L[j][k]);
+                    L[r][j] = inv * s;
+                }
+            }
+            // W = L^{-1} (lower triangular), column by column
+            dcx W[6][6];
+            for (int r = 0; r < 6; ++r)
+                for (int q = 0; q < 6; ++q) W[r][q] = {0, 0};
+            for (int q = 0; q < 6; ++q) {
+                W[q][q] = {1.0 / L[q][q].r, 0.0};
+                for (int r = q + 1; r < 6; ++r) {
+                    dcx s = {0, 0};
+                    for (int k = q; k < r; ++k) s = s + L[r][k] * W[k][q];
+                    W[r][q] = (-1.0 / L[r][r].r) * s;
+                }
+            }
+            // M^{-1} = W^+ W
+            for (int r = 0; r < 6; ++r)
+                for (int q = 0; q < 6; ++q) {
+                    dcx s = {0, 0};
+                    for (int k = (r > q ? r : q); k < 6; ++k) s = cmadc(s, W[k][r], W[k][q]);
+                    const int e = 36 * c + 6 * r + q;
+                    o64[(size_t)e * g.Vh] = make_double2(s.r, s.i);
+                    if (e & 1) o32[(size_t)(e / 2) * g.Vh] = make_float4((float)pending.r, (float)pending.i,
+                                                                         (float)s.r, (float)s.i);
+                    else pending = s;
+                }
+        }
+    }
+    const double b = block_sum(logdet);
+    grid_reduce(b, R.partials, R.counter, R.s, RED_STORE, slot);
+}
+
+cudaError_t clover_invert(const double2* C64, const Geom& g, int parity, double2* I64, float4* I32, const RedArgs& R,
+                          int slot, cudaStream_t st) {
+    if (parity != 0 && parity != 1) return cudaErrorInvalidValue;
+    if (grid_for(g.Vh) > R.capacity) return cudaErrorInvalidValue;
+    clover_invert_kernel<<<grid_for(g.Vh), NT, 0, st>>>(C64, g, parity, I64, I32, R, slot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// The determinant term -2 ln det M of one parity: its variation -2 tr(M^{-1} delta A)
+// has the form of -2 Re eta^+ delta A chi with chi eta^+ replaced by M^{-1}, so
+//   Lambda_ab += sum_{s,t} sigma_{st} (M^{-1})_{(t a),(s b)}
+// and M_munu += -i (kappa c_sw / 4) (Lambda + Lambda^+) on the sites of that parity.
+__global__ void __launch_bounds__(NT) clover_det_insertion_kernel(const double2* I64, Geom g, int parity,
+                                                                  CloverSigma S, double c, double2* Mout) {
+    const int i = blockIdx.x * NT + threadIdx.x;
+    if (i >= g.Vh) return;
+    const double2* ib = I64 + (size_t)parity * 72 * g.Vh + i;
+    double2* o = Mout + (size_t)parity * 54 * g.Vh + i;
+#pragma unroll 1
+    for (int pl = 0; pl < 6; ++pl) {
+        dmat Lam = zero3<double>();
+        for (int cb = 0; cb < 2; ++cb)
+            for (int s = 0; s < 2; ++s)
+                for (int u = 0; u < 2; ++u) {
+                    const double2 sg = S.s[pl][cb][s][u];
+                    if (sg.x == 0.0 && sg.y == 0.0) continue;
+                    const dcx w = {sg.x, sg.y};
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) {
+                            const double2 z = __ldg(ib + (size_t)(36 * cb + 6 * (3 * u + a) + 3 * s + b) * g.Vh);
+                            Lam.e[a][b] = cmad(Lam.e[a][b], w, dcx{z.x, z.y});
+                        }
+                }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                const dcx h = Lam.e[a][b] + conj(Lam.e[b][a]);
+                double2 v = o[(size_t)(pl * 9 + 3 * a + b) * g.Vh];
+                v.x += c * h.i;   // -i c h
+                v.y -= c * h.r;
+                o[(size_t)(pl * 9 + 3 * a + b) * g.Vh] = v;
+            }
+    }
+}
+
+cudaError_t clover_det_insertion(const double2* I64, const Geom& g, int parity, const CloverSigma& S, double kappa,
+                                 double csw, double2* M, cudaStream_t st) {
+    if (parity != 0 && parity != 1) return cudaErrorInvalidValue;
+    clover_det_insertion_kernel<<<grid_for(g.Vh), NT, 0, st>>>(I64, g, parity, S, 0.25 * kappa * csw, M);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace lgt

@@ -236,6 +236,14 @@ cudaError_t clover_apply(const void* C, const void* in, void* out, const Geom& g
 cudaError_t clover_insertion(const double2* X, const double2* Y, const Geom& g, const CloverSigma& S, double kappa,
                              double csw, double2* M, cudaStream_t st);
 // clover part of the force: form 0 Lie (out = keep*out + coef*F), form 1 G form
+// (1 + A)^{-1} on the sites of `parity` (0 / 1) in the layout of the clover field (I64
+// double2 [parity][72][Vh], I32 float4 [parity][36][Vh]; the other parity untouched), and
+// the sum over those sites of ln det (1 + A) into R.s->slot[slot]
+cudaError_t clover_invert(const double2* C64, const Geom& g, int parity, double2* I64, float4* I32, const RedArgs& R,
+                          int slot, cudaStream_t st);
+// adds the insertion of -2 ln det (1 + A) over the sites of `parity` to M (from I64)
+cudaError_t clover_det_insertion(const double2* I64, const Geom& g, int parity, const CloverSigma& S, double kappa,
+                                 double csw, double2* M, cudaStream_t st);
 cudaError_t clover_force(const double2* U, const double2* M, const Geom& g, double coef, int keep, int form,
                          double2* out, cudaStream_t st);
 
