@@ -266,6 +266,21 @@ def run_ours(args):
                            "force_rel_err_vs_fp64_path": (torch.linalg.norm(Fv - fd) / torch.linalg.norm(fd)).item()}
         del Fv
 
+    # the even-odd clover action (c_sw = 1.0) against the Wilson one on the same MD steps,
+    # at kappa = 0.13 (1 + A stays positive definite on this start at the couplings used)
+    clover = None
+    if not args.no_clover:
+        kc, cswc = 0.13, 1.0
+        res_c = {}
+        for name, csw in (("wilson_eo", 0.0), ("clover_eo", cswc)):
+            apc = lgt.action_params(beta=BETA, kappa=kc, even_odd=True, force_arith=FORCE_ARITH, csw=csw)
+            msc, stc, _, _, _ = timed(sp_mixed, K, W, a=apc)
+            res_c[name] = {"value": world * K / (max_over_ranks(msc) / 1e3), "ms_per_step": msc / K,
+                           "cg_iters_per_step": statistics.mean(x["iters"] for x in stc)}
+        clover = {"kappa": kc, "csw": cswc, **res_c,
+                  "clover_overhead": res_c["clover_eo"]["ms_per_step"] / res_c["wilson_eo"]["ms_per_step"]}
+        restore()   # the force comparison below is on the starting field
+
     # error of the headline mixed force against the FP64 path on the same field
     Fm, _ = lat.force(ap, phi, sp_mixed)
     force_err = (torch.linalg.norm(Fm - fd) / torch.linalg.norm(fd)).item()
@@ -424,6 +439,7 @@ def run_ours(args):
                         "traffic": traffic, "traffic_kernel": "plain FP32 hop (ncu capture)",
                         "algorithmic_bytes_per_launch": bytes32 / max(n32, 1),
                         "algorithmic_bytes_plain_hop": HOP_BYTES["fp32"] * lat.Vh},
+           "clover": clover,
            "multi_rhs": multi,
            "serving": serving,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches}
@@ -621,6 +637,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the several-sources measurement")
+    ap.add_argument("--no-clover", action="store_true", help="skip the even-odd clover measurement")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests per arrival rate in the serving measurement (0 skips it)")
     ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")

@@ -1655,7 +1655,10 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
             // even-odd: the odd-site determinant -2 ln det M_oo
             if (ap->even_odd)
                 CK(clover_det_insertion(ferm_lk.I64, L->g, 1, clover_sigma(), ap->kappa, ap->csw, L->cins, L->st));
-            CK(clover_force(ferm_lk.U, L->cins, L->g, coef, 1, form, out, L->st));
+            // double-float force arithmetic: the gather from the double-float links the
+            // fermion force just used (Udf holds ferm_lk.U)
+            if (dfa) CK(clover_force_df(L->Udf, L->cins, L->g, coef, 1, out, L->st));
+            else CK(clover_force(ferm_lk.U, L->cins, L->g, coef, 1, form, out, L->st));
         }
     }
     if (!keep) CK(cudaMemsetAsync(out, 0, form == 0 ? mom_bytes(L) : links64(L), L->st));

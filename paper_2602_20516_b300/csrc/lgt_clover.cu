@@ -16,6 +16,7 @@
 //   G += (A1 A2 A3 M_0 + M_1 A1 A2 A3 + A1 M_2 A2 A3 + A1 A2 M_3 A3)^+ ,
 // M_j the insertion at corner j with the sign of the plaquette's orientation
 // relative to mu -> nu (mu < nu).
+#include "lgt_df64.cuh"
 #include "lgt_internal.h"
 #include "lgt_su3.cuh"
 
@@ -112,35 +113,54 @@ template <typename R> struct CloverIO;
 template <> struct CloverIO<double> {
     static __device__ __forceinline__ void load(const void* f, int Vh, int i, dcx (&v)[12]) {
         const double2* b = (const double2*)f + i;
+#pragma unroll
         for (int k = 0; k < 12; ++k) { const double2 z = __ldg(b + (size_t)k * Vh); v[k] = {z.x, z.y}; }
     }
     static __device__ __forceinline__ void store(void* f, int Vh, int i, const dcx (&v)[12]) {
         double2* b = (double2*)f + i;
+#pragma unroll
         for (int k = 0; k < 12; ++k) b[(size_t)k * Vh] = make_double2(v[k].r, v[k].i);
-    }
-    static __device__ __forceinline__ dcx entry(const void* C, int Vh, int i, int k) {
-        const double2 z = __ldg((const double2*)C + (size_t)k * Vh + i);
-        return {z.x, z.y};
     }
 };
 template <> struct CloverIO<float> {
-    static __device__ __forceinline__ void load(const void* f, int Vh, int i, dcx (&v)[12]) {
+    static __device__ __forceinline__ void load(const void* f, int Vh, int i, fcx (&v)[12]) {
         const float4* b = (const float4*)f + i;
+#pragma unroll
         for (int k = 0; k < 6; ++k) {
             const float4 z = __ldg(b + (size_t)k * Vh);
             v[2 * k] = {z.x, z.y};
             v[2 * k + 1] = {z.z, z.w};
         }
     }
-    static __device__ __forceinline__ void store(void* f, int Vh, int i, const dcx (&v)[12]) {
+    static __device__ __forceinline__ void store(void* f, int Vh, int i, const fcx (&v)[12]) {
         float4* b = (float4*)f + i;
+#pragma unroll
         for (int k = 0; k < 6; ++k)
-            b[(size_t)k * Vh] = make_float4((float)v[2 * k].r, (float)v[2 * k].i, (float)v[2 * k + 1].r,
-                                            (float)v[2 * k + 1].i);
+            b[(size_t)k * Vh] = make_float4(v[2 * k].r, v[2 * k].i, v[2 * k + 1].r, v[2 * k + 1].i);
     }
-    static __device__ __forceinline__ dcx entry(const void* C, int Vh, int i, int k) {
-        const float4 z = __ldg((const float4*)C + (size_t)(k / 2) * Vh + i);
-        return (k & 1) ? dcx{z.z, z.w} : dcx{z.x, z.y};
+};
+
+// chiral block c (6 x 6, row-major) of the clover field at half-field site i
+template <typename R> struct CloverBlock;
+template <> struct CloverBlock<double> {
+    static __device__ __forceinline__ void load(const void* C, int Vh, int i, int c, dcx (&M)[6][6]) {
+        const double2* b = (const double2*)C + (size_t)(36 * c) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 36; ++k) {
+            const double2 z = __ldg(b + (size_t)k * Vh);
+            M[k / 6][k % 6] = {z.x, z.y};
+        }
+    }
+};
+template <> struct CloverBlock<float> {
+    static __device__ __forceinline__ void load(const void* C, int Vh, int i, int c, fcx (&M)[6][6]) {
+        const float4* b = (const float4*)C + (size_t)(18 * c) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {   // float4 k holds entries 2k, 2k+1 of the block
+            const float4 z = __ldg(b + (size_t)k * Vh);
+            M[(2 * k) / 6][(2 * k) % 6] = {z.x, z.y};
+            M[(2 * k + 1) / 6][(2 * k + 1) % 6] = {z.z, z.w};
+        }
     }
 };
 
@@ -153,14 +173,21 @@ __global__ void __launch_bounds__(NT) clover_apply_kernel(const void* C, const v
     const int p = parity == 2 ? (t >= g.Vh) : parity, i = parity == 2 ? t - p * g.Vh : t;
     const char* Cp = (const char*)C + p * cstride;
     const size_t fo = parity == 2 ? p * fstride : 0;
-    dcx v[12], w[12];
+    // arithmetic in the field's precision (FP64 FMAs issue at 1/64 of the FP32 rate)
+    cx<R> v[12], w[12];
     CloverIO<R>::load((const char*)in + fo, g.Vh, i, v);
-    for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        cx<R> M[6][6];
+        CloverBlock<R>::load(Cp, g.Vh, i, c, M);
+#pragma unroll
         for (int r = 0; r < 6; ++r) {
-            dcx s = {0, 0};
-            for (int q = 0; q < 6; ++q) s = cmad(s, CloverIO<R>::entry(Cp, g.Vh, i, 36 * c + 6 * r + q), v[6 * c + q]);
+            cx<R> s = {0, 0};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) s = cmad(s, M[r][q], v[6 * c + q]);
             w[6 * c + r] = s;
         }
+    }
     CloverIO<R>::store((char*)out + fo, g.Vh, i, w);
 }
 
@@ -298,6 +325,87 @@ __global__ void __launch_bounds__(NT) clover_force_kernel(const double2* U, cons
             }
         store_link(out, g.Vh, p, m, i, Go);
     }
+}
+
+// The same gather in double-float arithmetic (Lie form): links from their double-float
+// copy, the insertions split into double-float on load, products as in the gauge
+// force's double-float kernel; FP64 only in the final Lie components.
+__device__ __forceinline__ dfmat insertion_df_at(const double2* M, const Geom& g, const int x[4], int pl, double sgn) {
+    const int lex = lex_of(g, x);
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const double2* b = M + (size_t)par * 54 * g.Vh + (lex >> 1);
+    dfmat m;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double2 z = __ldg(b + (size_t)(pl * 9 + k) * g.Vh);
+        m.e[k / 3][k % 3] = {df_from(sgn * z.x), df_from(sgn * z.y)};
+    }
+    return m;
+}
+
+__global__ void __launch_bounds__(NT) clover_force_df_kernel(const float4* U, const double2* M, Geom g, double coef,
+                                                             int keep, double2* out) {
+    int m, p, i;
+    if (!link_index(g, m, p, i)) return;
+    int y[4];
+    eo_coords(g, p, i, y);
+    dfmat Gsum = df_zero3();
+    int ym[4] = {y[0], y[1], y[2], y[3]};
+    shift(g, ym, m, +1);
+#pragma unroll 1
+    for (int n = 0; n < 4; ++n) {
+        if (n == m) continue;
+        const int pl = plane_of(m, n);
+        const double s = m < n ? 1.0 : -1.0;
+        // above: A1 = U_n(y+m), A2 = U_m(y+n)^+, A3 = U_n(y)^+
+        {
+            int c2[4] = {ym[0], ym[1], ym[2], ym[3]};
+            shift(g, c2, n, +1);
+            int c3[4] = {y[0], y[1], y[2], y[3]};
+            shift(g, c3, n, +1);
+            const dfmat A1 = link_df_at(U, g, ym, n);
+            const dfmat Um = link_df_at(U, g, c3, m);
+            const dfmat Un = link_df_at(U, g, y, n);
+            const dfmat P12 = df_mul<false, true>(A1, Um);
+            const dfmat P23 = df_mul<true, true>(Um, Un);
+            const dfmat P123 = df_mul<false, true>(P12, Un);
+            df_mul_acc<false, false>(Gsum, P123, insertion_df_at(M, g, y, pl, s));
+            df_mul_acc<false, false>(Gsum, insertion_df_at(M, g, ym, pl, s), P123);
+            df_mul_acc<false, false>(Gsum, A1, df_mul<false, false>(insertion_df_at(M, g, c2, pl, s), P23));
+            df_mul_acc<false, true>(Gsum, df_mul<false, false>(P12, insertion_df_at(M, g, c3, pl, s)), Un);
+        }
+        // below: B1 = U_n(y+m-n)^+, B2 = U_m(y-n)^+, B3 = U_n(y-n)
+        {
+            int c2[4] = {ym[0], ym[1], ym[2], ym[3]};
+            shift(g, c2, n, -1);
+            int c3[4] = {y[0], y[1], y[2], y[3]};
+            shift(g, c3, n, -1);
+            const dfmat Un2 = link_df_at(U, g, c2, n);
+            const dfmat Um = link_df_at(U, g, c3, m);
+            const dfmat B3 = link_df_at(U, g, c3, n);
+            const dfmat P12 = df_mul<true, true>(Un2, Um);
+            const dfmat P23 = df_mul<true, false>(Um, B3);
+            const dfmat P123 = df_mul<false, false>(P12, B3);
+            df_mul_acc<false, false>(Gsum, P123, insertion_df_at(M, g, y, pl, -s));
+            df_mul_acc<false, false>(Gsum, insertion_df_at(M, g, ym, pl, -s), P123);
+            df_mul_acc<true, false>(Gsum, Un2, df_mul<false, false>(insertion_df_at(M, g, c2, pl, -s), P23));
+            df_mul_acc<false, false>(Gsum, df_mul<false, false>(P12, insertion_df_at(M, g, c3, pl, -s)), B3);
+        }
+    }
+    const dfmat UG = df_mul<false, false>(load_link_df(U, g.Vh, p, m, i), Gsum);
+    double c[8], f[8];
+    lie_im_tr_df(UG, c);
+    if (keep) load_mom(out, g.Vh, p, m, i, f);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) f[a] = (keep ? f[a] : 0.0) - 0.5 * coef * c[a];
+    store_mom(out, g.Vh, p, m, i, f);
+}
+
+cudaError_t clover_force_df(const float4* Udf, const double2* M, const Geom& g, double coef, int keep, double2* out,
+                            cudaStream_t st) {
+    clover_force_df_kernel<<<grid_for(8L * g.Vh), NT, 0, st>>>(Udf, M, g, coef, keep, out);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t clover_force(const double2* U, const double2* M, const Geom& g, double coef, int keep, int form,

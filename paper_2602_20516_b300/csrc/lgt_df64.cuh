@@ -12,6 +12,7 @@
 // intrinsics, which the compiler never contracts into an FMA.
 #pragma once
 #include "lgt_common.cuh"
+#include "lgt_su3.cuh"
 
 namespace lgt {
 
@@ -166,6 +167,25 @@ __device__ __forceinline__ void store_link_df(float4* __restrict__ U, int Vh, in
         const df r = df_from(m.e[k / 3][k % 3].r), im = df_from(m.e[k / 3][k % 3].i);
         b[(size_t)k * Vh] = make_float4(r.h, r.l, im.h, im.l);
     }
+}
+
+// the double-float link U_mu at coordinates x
+__device__ __forceinline__ dfmat link_df_at(const float4* U, const Geom& g, const int x[4], int mu) {
+    const int lex = lex_of(g, x);
+    return load_link_df(U, g.Vh, (x[0] + x[1] + x[2] + x[3]) & 1, mu, lex >> 1);
+}
+
+// Lie components c_a = Im tr(lambda^a M) of a double-float matrix, in FP64
+__device__ __forceinline__ void lie_im_tr_df(const dfmat& M, double c[8]) {
+    c[0] = df_to(df_add(M.e[0][1].i, M.e[1][0].i));
+    c[1] = df_to(df_sub(M.e[0][1].r, M.e[1][0].r));
+    c[2] = df_to(df_sub(M.e[0][0].i, M.e[1][1].i));
+    c[3] = df_to(df_add(M.e[0][2].i, M.e[2][0].i));
+    c[4] = df_to(df_sub(M.e[0][2].r, M.e[2][0].r));
+    c[5] = df_to(df_add(M.e[1][2].i, M.e[2][1].i));
+    c[6] = df_to(df_sub(M.e[1][2].r, M.e[2][1].r));
+    const df d = df_sub(df_add(M.e[0][0].i, M.e[1][1].i), df_add(M.e[2][2].i, M.e[2][2].i));
+    c[7] = df_to(d) * 0.57735026918962576451;
 }
 
 }  // namespace lgt

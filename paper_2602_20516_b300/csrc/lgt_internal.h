@@ -244,6 +244,9 @@ cudaError_t clover_invert(const double2* C64, const Geom& g, int parity, double2
 // adds the insertion of -2 ln det (1 + A) over the sites of `parity` to M (from I64)
 cudaError_t clover_det_insertion(const double2* I64, const Geom& g, int parity, const CloverSigma& S, double kappa,
                                  double csw, double2* M, cudaStream_t st);
+// the clover force gather (Lie form) in double-float arithmetic from the links' double-float copy
+cudaError_t clover_force_df(const float4* Udf, const double2* M, const Geom& g, double coef, int keep, double2* out,
+                            cudaStream_t st);
 cudaError_t clover_force(const double2* U, const double2* M, const Geom& g, double coef, int keep, int form,
                          double2* out, cudaStream_t st);
 
