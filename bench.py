@@ -60,8 +60,8 @@ HOP_FLOPS = 1320
 HOP_MIN_MS = 0.010
 # ncu DRAM traffic (read + write) of one FP32 hop launch at 32^3 x 64, and the hash of
 # the kernel sources it was taken from (traffic is reported as null once they change)
-NCU_TRAFFIC = {"bytes": 593212672,
-               "sources_sha256": "98a9a8a46d15b16a042097cc8c204e5021935358bed86d7560e0ef9327a45b0e"}
+NCU_TRAFFIC = {"bytes": 593337600,
+               "sources_sha256": "538073696f8c5ae43bd6ab2f31e5d6a4b04b56151b93b477a7430ed15ff8e2de"}
 HOP_SOURCES = ["paper_2602_20516_b300/csrc/lgt_dirac.cu", "paper_2602_20516_b300/csrc/lgt_spin.cuh",
                "paper_2602_20516_b300/csrc/lgt_common.cuh"]
 
