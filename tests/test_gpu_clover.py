@@ -191,3 +191,23 @@ def test_even_odd_clover_hmc_trajectory_matches_oracle(lgt, ora):
     assert abs(r["dH"] - ro["dH"]) < 1e-8 * max(1.0, abs(ro["dH"]))
     assert r["accepted"] == ro["accepted"]
     assert H.rel(_np(lat.get_links()), Uo) < 1e-10
+
+
+@pytest.mark.parametrize("recompute", [0, 1])
+def test_even_odd_clover_with_stout_force_vs_oracle(lgt, ora, recompute):
+    """Even-odd clover on 2-level stout links (the clover field, its odd-site inverse and
+    the determinant built from the top level): the force through the stout adjoint
+    against the oracle's MD force, with the smeared levels stored or recomputed."""
+    U = synth.random_links(DIMS, 0.5, 121)
+    phi = synth.gaussian_spinor(DIMS, 122, parity_mask=1)
+    lat = _lat(lgt, U)
+    pf = lat.pack_spinor(phi, lgt.EVEN, lgt.FP64)
+    ap = lgt.action_params(beta=5.7, kappa=KAPPA, csw=CSW, even_odd=True, n_stout=2, rho=0.1,
+                           stout_recompute=recompute)
+    F, _ = lat.force(ap, pf, lgt.solver("fp64", tol=1e-13))
+    p = ora.hmc_params(5.7, KAPPA, eo=True, tol_md=1e-13, n_stout=2, rho=0.1, csw=CSW)
+    Fo = ora.md_force(DIMS, U, p, phi)
+    assert H.rel(_np(lat.unpack_momenta(F)), Fo) < 1e-10
+    _, Sf, _ = lat.action(ap, pf, lgt.solver("fp64", tol=1e-13))
+    Hs = ora.hamiltonian(DIMS, U, np.zeros((int(np.prod(DIMS)), 4, 8)), phi, p) - ora.gauge_action(DIMS, U, 5.7)
+    assert abs(Sf - Hs) / abs(Hs) < 1e-11
