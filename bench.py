@@ -12,7 +12,7 @@ runs the CG in FP32 with FP64 reliable updates and the forces in double-float
 (FP32-pair) arithmetic accumulated in FP64; the FP64 path is FP64 throughout.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --kernel hop32|hop64|force_df [--reps R]   # a few launches, for ncu
+    python bench.py --kernel hop32|hop64|force_df|clover_md [--reps R]   # a few launches, for ncu
 
 Prints one JSON line (rank 0).  With torchrun each rank runs an independent
 replica (no collective in the data path; weak scaling).
@@ -615,6 +615,18 @@ def run_kernel(args):
         torch.cuda.synchronize()
         print(json.dumps({"kernel": args.kernel, "force_evals": args.reps, "lattice": list(DIMS)}))
         return
+    if args.kernel == "clover_md":
+        # mixed-precision MD steps with the even-odd clover action (kappa 0.13, c_sw 1.0)
+        phi = lat.gaussian_spinor(SEED, 0, lgt.FIELD_SOURCE, lgt.EVEN)
+        ap = lgt.action_params(beta=BETA, kappa=0.13, even_odd=True, force_arith=FORCE_ARITH, csw=1.0)
+        sp = lgt.solver("mixed", tol=TOL, delta=DELTA)
+        mom = lat.momentum_field()
+        for _ in range(args.reps):
+            st = lat.md_update(mom, EPS, lgt.UPDATE_P, ap, phi, sp)
+            lat.md_update(mom, EPS, lgt.UPDATE_U)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": args.kernel, "md_steps": args.reps, "lattice": list(DIMS), "last_solve": st}))
+        return
     prec = lgt.FP32 if args.kernel == "hop32" else lgt.FP64
     src = lat.pack_spinor(lat.unpack_spinor(lat.gaussian_spinor(SEED, 0, lgt.FIELD_SOURCE, lgt.ODD),
                                             lgt.ODD, lgt.FP64), lgt.ODD, prec)
@@ -647,7 +659,7 @@ def main():
     ap.add_argument("--checkpoint", default="", help="HMC mode: write the chain's checkpoint here after every trajectory")
     ap.add_argument("--chrono", type=int, default=0,
                     help="HMC mode: MD solves start from the last N solutions (chronological guess)")
-    ap.add_argument("--kernel", choices=["hop32", "hop64", "force_df"])
+    ap.add_argument("--kernel", choices=["hop32", "hop64", "force_df", "clover_md"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "ours" and not args.kernel:
