@@ -160,6 +160,26 @@ def oracle_sample(cg_iters, reps=1):
     return est, cores, sample
 
 
+# ---------------------------------------------------------------- ranks
+# One process per GPU (replicas: every rank runs the whole step on its own lattice,
+# with no collective on the data path).  The timing is the slowest rank's, and the
+# whole-job throughput counts the units of all ranks.
+def max_over_ranks(v, world, device="cuda"):
+    """The maximum of v over the ranks (v itself for one rank)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(world, units_per_rank, seconds_max):
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -177,12 +197,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+    def max_ranks(v):
+        return max_over_ranks(v, world)
 
     lat = lgt.Lattice(DIMS)
     lat.random_links(SEED + rank, ALPHA)
@@ -239,15 +255,15 @@ def run_ours(args):
     sp_mixed = lgt.solver("mixed", tol=TOL, delta=DELTA)
     sampler = ClockSampler(local)
     ms, st, launches, kt, clk = timed(sp_mixed, K, W, kernel_timing=True, clocks=sampler)
-    ms_max = max_over_ranks(ms)
-    value = world * K / (ms_max / 1e3)
+    ms_max = max_ranks(ms)
+    value = whole_job_rate(world, K, ms_max / 1e3)
     iters = statistics.mean(s["iters"] for s in st)
     rel = statistics.mean(s["reliable_updates"] for s in st)
 
     # FP64 path, same workload
     K64 = max(1, min(K, args.fp64_steps))
     ms64, st64, _, kt64, _ = timed(lgt.solver("fp64", tol=TOL), K64, W, kernel_timing=True)
-    ms64 = max_over_ranks(ms64)
+    ms64 = max_ranks(ms64)
     value64 = world * K64 / (ms64 / 1e3)
     iters64 = statistics.mean(s["iters"] for s in st64)
 
@@ -262,7 +278,7 @@ def run_ours(args):
         Fv, _ = lat.force(apv, phi, sp_mixed)
         if fd is None:
             fd, _ = lat.force(ap, phi, lgt.solver("fp64", tol=TOL))
-        variants[arith] = {"value": world * K / (max_over_ranks(msv) / 1e3), "ms_per_step": msv / K, "steps": K,
+        variants[arith] = {"value": world * K / (max_ranks(msv) / 1e3), "ms_per_step": msv / K, "steps": K,
                            "force_rel_err_vs_fp64_path": (torch.linalg.norm(Fv - fd) / torch.linalg.norm(fd)).item()}
         del Fv
 
@@ -275,7 +291,7 @@ def run_ours(args):
         for name, csw in (("wilson_eo", 0.0), ("clover_eo", cswc)):
             apc = lgt.action_params(beta=BETA, kappa=kc, even_odd=True, force_arith=FORCE_ARITH, csw=csw)
             msc, stc, _, _, _ = timed(sp_mixed, K, W, a=apc)
-            res_c[name] = {"value": world * K / (max_over_ranks(msc) / 1e3), "ms_per_step": msc / K,
+            res_c[name] = {"value": world * K / (max_ranks(msc) / 1e3), "ms_per_step": msc / K,
                            "cg_iters_per_step": statistics.mean(x["iters"] for x in stc)}
         clover = {"kappa": kc, "csw": cswc, **res_c,
                   "clover_overhead": res_c["clover_eo"]["ms_per_step"] / res_c["wilson_eo"]["ms_per_step"]}
@@ -378,7 +394,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         pipeline(Ke)
         barrier()
-        te = max_over_ranks(time.perf_counter() - t0)
+        te = max_ranks(time.perf_counter() - t0)
 
         # the host link alone: one upload and one download of a step's bytes
         def copy_time(fn):
