@@ -347,6 +347,56 @@ def test_stout_unitary_and_covariant(ora):
     assert H.rel(lhs, H.gauge_transform_links(d, S, g)) < 1e-13
 
 
+def test_stout_rho_derivative_is_gauge_flow(ora):
+    """One stout level is U' = exp(rho P[(U V)^+]) U with V the force staple, i.e. a
+    step of the gradient flow of S_G: dS_G(smear_rho U)/drho at rho = 0 equals
+    sum_{x,mu,a} F_a (-2 Im tr T^a U V) = -(6 / beta) sum F_a^2, with F the gauge
+    force (itself pinned by finite differences).  A central difference in rho checks
+    the sign and scale of Q, the staple orientation and the projection."""
+    d = (4, 4, 4, 4)
+    beta = 5.8
+    U = synth.random_links(d, 0.5, 39)
+    F = ora.gauge_force(d, U, beta)
+    want = -(6.0 / beta) * float(np.sum(F * F))
+    h = 1e-4
+    fd = (ora.gauge_action(d, ora.stout_forward(d, U, h), beta)
+          - ora.gauge_action(d, ora.stout_forward(d, U, -h), beta)) / (2 * h)
+    assert abs(fd - want) < 1e-6 * abs(want), (fd, want)
+    # a flow step lowers the action
+    assert ora.gauge_action(d, ora.stout_forward(d, U, 0.01), beta) < ora.gauge_action(d, U, beta)
+
+
+def test_stout_closed_form_abelian_field(ora):
+    """Diagonal (abelian) links U_mu(x) = diag(exp(i th_mu,k(x))), sum_k th = 0: every
+    product is diagonal, so one stout level moves each phase by
+    rho sum_nu [sin phi_munu,k(x - nu) - sin phi_munu,k(x)] minus its colour mean,
+    phi_munu(x) = th_mu(x) + th_nu(x + mu) - th_mu(x + nu) - th_nu(x) the plaquette
+    angle (scalar trigonometry; no matrix code)."""
+    d = (4, 6, 4, 8)
+    V = synth.volume(d)
+    rng = np.random.default_rng(41)
+    th = rng.uniform(-1.2, 1.2, size=(V, 4, 3))
+    th -= th.mean(axis=2, keepdims=True)
+    U = np.zeros((V, 4, 3, 3), np.complex128)
+    for k in range(3):
+        U[:, :, k, k] = np.exp(1j * th[:, :, k])
+    rho = 0.13
+    shift = np.zeros_like(th)
+    for mu in range(4):
+        xpmu = H.neighbour(d, mu, +1)
+        for nu in range(4):
+            if nu == mu:
+                continue
+            xpnu, xmnu = H.neighbour(d, nu, +1), H.neighbour(d, nu, -1)
+            phi = th[:, mu] + th[xpmu, nu] - th[xpnu, mu] - th[:, nu]
+            shift[:, mu] += rho * (np.sin(phi[xmnu]) - np.sin(phi))
+    shift -= shift.mean(axis=2, keepdims=True)
+    want = np.zeros_like(U)
+    for k in range(3):
+        want[:, :, k, k] = np.exp(1j * (th[:, :, k] + shift[:, :, k]))
+    assert H.rel(ora.stout_forward(d, U, rho), want) < 1e-14
+
+
 def test_stout_backward_finite_difference(ora):
     """L(U) = Re tr sum A^+ smear(U): its gradient is the backward of G' = A."""
     d = (4, 4, 4, 4)
