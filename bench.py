@@ -1,26 +1,36 @@
 #!/usr/bin/env python
 """Benchmark: molecular-dynamics force evaluations per second on a 32^3 x 64
 lattice (two-flavour Wilson fermions, even-odd pseudofermion action, beta 5.8,
-kappa 0.156, seeded links exp(i 0.5 H)), mixed-precision path vs FP64 path,
-Wilson-hop HBM bandwidth, end-to-end rate with host buffers, and the FP64 CPU
-oracle as the baseline.
+kappa 0.156), mixed-precision path vs FP64 path, Wilson-hop HBM bandwidth,
+end-to-end rate with host buffers, and the FP64 CPU oracle as the baseline.
 
-One step = one MD update: a force evaluation from scratch (CG on Dhat^+ Dhat from a
-zero guess to tol 1e-10, X/Y vectors, fermion and gauge force fused into the
-momentum kick) followed by the link update U <- exp(i eps P) U.  The mixed path
-runs the CG in FP32 with FP64 reliable updates and the forces in double-float
-(FP32-pair) arithmetic accumulated in FP64; the FP64 path is FP64 throughout.
+Workload: four fixed gauge fields, the links (and momenta) at MD steps 0, 10, 20
+and 30 of the seeded MD sequence from the exp(i 0.5 H) start (eps = 1/20, built
+untimed before the measurement and kept on the device).  Along that sequence the
+plaquette swings 0.50 -> 0.61 -> 0.47 and the field at step 20 has a nearly
+singular Dhat (about 600 FP64 CG iterations against 110-190 for the others), so
+the four span the cost range of the sequence.  One step = one force evaluation
+on each of the four fields from a zero CG guess (CG on Dhat^+ Dhat to tol 1e-10,
+X/Y vectors, fermion and gauge force fused into the momentum kick) followed by
+the link update U <- exp(i eps P) U: the same work whatever --steps is.  The
+mixed path runs the CG in FP32 with FP64 reliable updates and the forces in
+double-float (FP32-pair) arithmetic accumulated in FP64; the FP64 path is FP64
+throughout and is timed on the same four fields.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--detail PATH]
     python bench.py --kernel hop32|hop64|force_df|clover_md [--reps R]   # a few launches, for ncu
+    python bench.py --hmc N [--hmc-fp64 M] [--log PATH]                  # config-4 HMC record
+    python bench.py --cpu-table1                                         # oracle force at 24^4, 1 and all threads
 
-Prints one JSON line (rank 0).  With torchrun each rank runs an independent
-replica (no collective in the data path; weak scaling).
+Prints one JSON line (rank 0); --detail also writes the per-field and per-phase
+figures to a file.  With torchrun each rank runs an independent replica (no
+collective in the data path; weak scaling).
 """
 import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -34,19 +44,27 @@ METRIC = "force evals/s + Dslash HBM GB/s at 32^3×64, mixed vs FP64; p99 solve 
 UNIT = "force evals/s"
 DIMS = (32, 32, 32, 64)
 # DELTA: reliable-update threshold of the mixed CG (|r| < DELTA max|r| triggers an FP64
-# residual replacement).  Measured on this workload (force from a zero guess at the
-# seeded start): 146 inner iterations for every DELTA from 1e-3 to 3e-5 with 4 -> 3 FP64
-# updates; 3e-6 needs 147 iterations and 2 updates (the fastest); 1e-6 needs 158
+# residual replacement).  Measured on the seeded start: 146 inner iterations for every
+# DELTA from 1e-3 to 3e-5 with 4 -> 3 FP64 updates; 3e-6 needs 147 iterations and 2
+# updates (the fastest); 1e-6 needs 158
 BETA, KAPPA, ALPHA, TOL, DELTA = 5.8, 0.156, 0.5, 1e-10, 3e-6
 # force arithmetic of the mixed path: double-float (FP32 pairs, ~48 bits) accumulated
 # in FP64; FP64 and FP32 force arithmetic are timed beside it
 FORCE_ARITH = "df64"
 EPS = 1.0 / 20
 SEED = 4
-# FP64 CG iterations of this workload (Dhat^+Dhat, tol 1e-10, zero guess): used only to
-# scale the oracle's capped-CG sample in the reference arm (the default arm uses the
-# count it measures in the same run)
-CG_ITERS_FP64 = 146
+# the workload's gauge fields: MD steps of the seeded sequence
+FIELD_STEPS = (0, 10, 20, 30)
+# FP64 CG iterations (Dhat^+Dhat, tol 1e-10, zero guess) on those four fields, measured
+# on a B300 with this build; the reference arm scales its capped-CG sample with them (the
+# default arm uses the counts it measures in the same run, reported beside them)
+CG_ITERS_FP64 = {0: 146, 10: 111, 20: 592, 30: 188}
+# one oracle force evaluation run to completion (no extrapolation) beside Table I of
+# the paper (24^4, Wilson fermions, no smearing; its beta, kappa and tolerance are not
+# stated, so these are config 4's)
+TABLE1_DIMS = (24, 24, 24, 24)
+TABLE1_PAPER_S = {"single_thread_cpu_handwritten": 195.53, "single_thread_cpu_ad": 162.50,
+                  "h100_handwritten": 4.61, "h100_ad": 3.39}
 # algorithmic (compulsory) bytes per output site of one even-odd hop:
 # 8 links + 1 input spinor + 1 output spinor (each array touched once)
 HOP_BYTES = {"fp32": 8 * 48 + 96 + 96, "fp64": 8 * 144 + 192 + 192}
@@ -82,12 +100,12 @@ def measured_peaks():
 
 
 def config_block(args):
-    return {"workload": "32^3x64 Nf=2 Wilson even-odd MD step: mixed CG (FP32 inner, FP64 reliable "
-                        "updates) tol 1e-10 from zero guess + fermion/gauge force (double-float arithmetic, "
-                        "FP64 accumulation) into the momentum kick + FP64 link update",
+    return {"workload": "32^3x64 Nf=2 Wilson eo; step = force eval (CG from 0, tol 1e-10) + kick + link update "
+                        "on each of 4 fixed fields (MD steps 0,10,20,30 of the seeded sequence)",
+            "force_evals_per_step": len(FIELD_STEPS), "field_md_steps": list(FIELD_STEPS),
             "lattice": list(DIMS), "beta": BETA, "kappa": KAPPA, "alpha": ALPHA, "tol": TOL,
             "delta": DELTA, "seed": SEED, "eps": EPS,
-            "l2": "inputs larger than L2 (FP64 links 1.21 GB + FP32 links 0.40 GB per replica)",
+            "l2": "inputs > L2 (1.61 GB of links per field)",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -128,36 +146,88 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(cg_iters, reps=1):
-    """Time the FP64 oracle on a bounded sample of one MD step at 32^3 x 64 and
-    scale it to one force evaluation: CG capped at 2 iterations (3 operator
-    applications with its residual check; per-iteration cost = t/3), the X/Y hops,
-    gauge force, fermion force and link update."""
-    import numpy as np
+# ---------------------------------------------------------------- CPU oracle
+def cpu_info():
+    model = platform.processor() or ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"model": model, "nproc": os.cpu_count(),
+            "threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+
+
+_ORACLE_FIELDS = {}
+
+
+def oracle_step_estimate(iters_by_field):
+    """An ESTIMATE of one step of the workload on the FP64 oracle at 32^3 x 64, from a
+    bounded sample on the seeded start field: CG capped at 1 iteration (2 operator
+    applications with its residual check; per-iteration cost = t/2) plus the X/Y hops,
+    gauge force, fermion force and link update, timed once.  One step is estimated as
+    sum over the four fields of t_iter (iters + 1) + t_rest with the FP64 CG iteration
+    counts of those fields.  Returns (seconds per step, sample description)."""
     import oracle as O
     d = DIMS
-    U = O.random_links(d, SEED, ALPHA)
-    phi = O.gaussian_spinor(d, SEED, 0, O.FIELD_SOURCE, 1)
-    mom = O.gaussian_momenta(d, SEED, 0)
-    est = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        O.cg(d, U, KAPPA, phi, eo=True, tol=TOL, max_iter=2)
-        t_cg = time.perf_counter() - t0
-        t1 = time.perf_counter()
-        X = O.hop(d, U, phi, out_mask=2)
-        Y = O.hop(d, U, X, out_mask=1)
-        O.hop(d, U, Y, out_mask=2, dagger=True)
-        O.gauge_force(d, U, BETA)
-        O.fermion_force_xy(d, U, KAPPA, X, Y)
-        O.update_links(d, U, mom, EPS)
-        t_rest = time.perf_counter() - t1
-        est.append(t_cg / 3.0 * (cg_iters + 1) + t_rest)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = (f"oracle (C, OpenMP) on 32^3x64: CG capped at 2 iterations scaled to {cg_iters} "
-              f"iterations (+1 residual apply), plus X/Y hops, gauge force, fermion force, link update")
-    return est, cores, sample
+    if not _ORACLE_FIELDS:   # generated once per process, outside the sample
+        _ORACLE_FIELDS["U"] = O.random_links(d, SEED, ALPHA)
+        _ORACLE_FIELDS["phi"] = O.gaussian_spinor(d, SEED, 0, O.FIELD_SOURCE, 1)
+        _ORACLE_FIELDS["mom"] = O.gaussian_momenta(d, SEED, 0)
+    U, phi, mom = _ORACLE_FIELDS["U"], _ORACLE_FIELDS["phi"], _ORACLE_FIELDS["mom"]
+    t0 = time.perf_counter()
+    O.cg(d, U, KAPPA, phi, eo=True, tol=TOL, max_iter=1)
+    t_iter = (time.perf_counter() - t0) / 2.0
+    t1 = time.perf_counter()
+    X = O.hop(d, U, phi, out_mask=2)
+    Y = O.hop(d, U, X, out_mask=1)
+    O.hop(d, U, Y, out_mask=2, dagger=True)
+    O.gauge_force(d, U, BETA)
+    O.fermion_force_xy(d, U, KAPPA, X, Y)
+    O.update_links(d, U, mom, EPS)
+    t_rest = time.perf_counter() - t1
+    step = sum(t_iter * (iters_by_field[f] + 1) + t_rest for f in FIELD_STEPS)
+    sample = (f"ESTIMATE from a sample: oracle (C, OpenMP) on the 32^3x64 start field, CG capped at 1 "
+              f"iteration ({t_iter:.2f} s per iteration) scaled to the FP64 iteration counts of the 4 fields "
+              f"{[iters_by_field[f] for f in FIELD_STEPS]} (+1 residual apply each), plus X/Y hops, gauge force, "
+              f"fermion force and link update ({t_rest:.2f} s) per field")
+    return step, sample
+
+
+def oracle_full_force(dims=TABLE1_DIMS):
+    """One complete FP64 oracle force evaluation (no extrapolation): CG on Dhat^+ Dhat
+    from zero to tol 1e-10, fermion force, gauge force, at config 4's couplings on
+    the seeded exp(i 0.5 H) field of the given lattice.  Threads: OMP_NUM_THREADS."""
+    import oracle as O
+    U = O.random_links(dims, SEED, ALPHA)
+    phi = O.gaussian_spinor(dims, SEED, 0, O.FIELD_SOURCE, 1)
+    t0 = time.perf_counter()
+    Ff, it = O.pf_force(dims, U, KAPPA, phi, eo=True, tol=TOL)
+    Fg = O.gauge_force(dims, U, BETA)
+    sec = time.perf_counter() - t0
+    del Ff, Fg
+    return {"lattice": list(dims), "seconds": sec, "cg_iters": int(it), **cpu_info()}
+
+
+def cpu_table1(threads_list=(1, None)):
+    """The full oracle force at 24^4 with 1 thread and with every core, each in a
+    process of its own (OpenMP reads its thread count at start)."""
+    out = []
+    for th in threads_list:
+        env = dict(os.environ)
+        if th is None:
+            env.pop("OMP_NUM_THREADS", None)
+        else:
+            env["OMP_NUM_THREADS"] = str(th)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-force-once"], env=env,
+                           capture_output=True, text=True, check=True)
+        out.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    return {"oracle_force_24x4": out, "paper_table1_s": TABLE1_PAPER_S,
+            "note": "paper: 24^4 Wilson fermions, no smearing, beta/kappa/tolerance not stated, CPU model not "
+                    "stated; here config 4's couplings (beta 5.8, kappa 0.156, tol 1e-10) on the seeded "
+                    "exp(i 0.5 H) field"}
 
 
 # ---------------------------------------------------------------- ranks
@@ -181,6 +251,29 @@ def whole_job_rate(world, units_per_rank, seconds_max):
 
 
 # ---------------------------------------------------------------- our arm
+STAT_KEYS = ("iters", "reliable_updates", "breakdowns", "diverged", "handovers", "fp64_iters", "restarts")
+
+
+def _round(v, sig=4):
+    if isinstance(v, float):
+        return float(f"{v:.{sig}g}")
+    if isinstance(v, dict):
+        return {k: _round(x, sig) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [_round(x, sig) for x in v]
+    return v
+
+
+def summarize_stats(st):
+    """Per-field solver counts of one step (the steps repeat the same four solves) and
+    their mean over the step."""
+    n = len(FIELD_STEPS)
+    first = st[:n]
+    per_field = {str(f): {k: s[k] for k in STAT_KEYS} for f, s in zip(FIELD_STEPS, first)}
+    sums = {k: sum(s[k] for s in st) / (len(st) / n) for k in STAT_KEYS}
+    return per_field, sums
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -204,27 +297,36 @@ def run_ours(args):
     lat.random_links(SEED + rank, ALPHA)
     phi = lat.gaussian_spinor(SEED + rank, 0, lgt.FIELD_SOURCE, lgt.EVEN)
     mom = lat.gaussian_momenta(SEED + rank, 0)
-    # every phase (mixed, FP64, FP32 forces, e2e) starts from this same state, so
-    # they run the same MD steps on the same fields
-    U_start = lat.get_links()
-    mom_start = mom.clone()
-
-    def restore():
-        lat.set_links(U_start)
-        mom.copy_(mom_start)
     # headline mixed path: FP32 CG with FP64 reliable updates, forces in double-float
     # (FP32-pair) arithmetic accumulated in FP64; the FP64 path ignores force_arith
     ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith=FORCE_ARITH)
+    sp_mixed = lgt.solver("mixed", tol=TOL, delta=DELTA)
+    sp64 = lgt.solver("fp64", tol=TOL)
     stream = torch.cuda.current_stream()
 
+    # the workload's fields: links and momenta at the MD steps FIELD_STEPS of the seeded
+    # sequence (untimed; every phase below starts each force evaluation from one of them)
+    fields = []
+    for k in range(max(FIELD_STEPS) + 1):
+        if k in FIELD_STEPS:
+            fields.append((lat.get_links(), mom.clone()))
+        if k < max(FIELD_STEPS):
+            lat.md_update(mom, EPS, lgt.UPDATE_P, ap, phi, sp_mixed)
+            lat.md_update(mom, EPS, lgt.UPDATE_U)
+    plaq = []
+    for U, _ in fields:
+        lat.set_links(U)
+        plaq.append(lat.plaquette())
+
     def step(sp, stats, a=ap):
-        s = lat.md_update(mom, EPS, lgt.UPDATE_P, a, phi, sp)
-        lat.md_update(mom, EPS, lgt.UPDATE_U)
-        stats.append(s)
+        for U, m in fields:
+            lat.set_links(U)
+            mom.copy_(m)
+            stats.append(lat.md_update(mom, EPS, lgt.UPDATE_P, a, phi, sp))
+            lat.md_update(mom, EPS, lgt.UPDATE_U)
 
     def timed(sp, K, W, kernel_timing=False, clocks=None, a=ap):
         st = []
-        restore()
         for _ in range(W):
             step(sp, st, a)
         st.clear()
@@ -235,7 +337,7 @@ def run_ours(args):
             clocks.start()
         lgt.launch_count(reset=True)
         if kernel_timing:
-            lgt.kernel_timing_start(65536)
+            lgt.kernel_timing_start(1 << 18)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(K):
@@ -251,56 +353,58 @@ def run_ours(args):
         ms = e0.elapsed_time(e1)
         return ms, st, launches, kt, clk
 
+    nf = len(FIELD_STEPS)
     K, W = args.steps, args.warmup
-    sp_mixed = lgt.solver("mixed", tol=TOL, delta=DELTA)
     sampler = ClockSampler(local)
     ms, st, launches, kt, clk = timed(sp_mixed, K, W, kernel_timing=True, clocks=sampler)
     ms_max = max_ranks(ms)
-    value = whole_job_rate(world, K, ms_max / 1e3)
-    iters = statistics.mean(s["iters"] for s in st)
-    rel = statistics.mean(s["reliable_updates"] for s in st)
+    value = whole_job_rate(world, nf * K, ms_max / 1e3)
+    per_field, sums = summarize_stats(st)
 
-    # FP64 path, same workload
+    # FP64 path on the same four fields (each step the same work as a mixed step)
     K64 = max(1, min(K, args.fp64_steps))
-    ms64, st64, _, kt64, _ = timed(lgt.solver("fp64", tol=TOL), K64, W, kernel_timing=True)
+    ms64, st64, _, kt64, _ = timed(sp64, K64, 1, kernel_timing=True)
     ms64 = max_ranks(ms64)
-    value64 = world * K64 / (ms64 / 1e3)
-    iters64 = statistics.mean(s["iters"] for s in st64)
+    value64 = whole_job_rate(world, nf * K64, ms64 / 1e3)
+    per_field64, sums64 = summarize_stats(st64)
 
-    # the same workload with the other force arithmetics of the mixed path: FP64, and
-    # FP32 (~1e-7 force error, moves Delta H by ~1e-4 relative)
+    # the other force arithmetics of the mixed path: FP64, and FP32 (~1e-7 force error,
+    # moves Delta H by ~1e-4 relative)
+    Kv = max(1, min(K, args.variant_steps))
     variants = {}
-    fd = None
     for arith in ("fp64", "fp32"):
         apv = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith=arith)
-        msv, _, _, _, _ = timed(sp_mixed, K, W, a=apv)
-        restore()
-        Fv, _ = lat.force(apv, phi, sp_mixed)
-        if fd is None:
-            fd, _ = lat.force(ap, phi, lgt.solver("fp64", tol=TOL))
-        variants[arith] = {"value": world * K / (max_ranks(msv) / 1e3), "ms_per_step": msv / K, "steps": K,
-                           "force_rel_err_vs_fp64_path": (torch.linalg.norm(Fv - fd) / torch.linalg.norm(fd)).item()}
-        del Fv
+        msv, _, _, _, _ = timed(sp_mixed, Kv, 1, a=apv)
+        variants[arith] = {"value": whole_job_rate(world, nf * Kv, max_ranks(msv) / 1e3),
+                           "ms_per_step": msv / Kv, "steps": Kv}
 
-    # the even-odd clover action (c_sw = 1.0) against the Wilson one on the same MD steps,
-    # at kappa = 0.13 (1 + A stays positive definite on this start at the couplings used)
+    # force of every arithmetic against the FP64 path's, field by field
+    ferr = {"df64": [], "fp64": [], "fp32": []}
+    for U, _ in fields:
+        lat.set_links(U)
+        fd, _ = lat.force(ap, phi, sp64)
+        for arith in ferr:
+            Fv, _ = lat.force(lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith=arith),
+                              phi, sp_mixed)
+            ferr[arith].append((torch.linalg.norm(Fv - fd) / torch.linalg.norm(fd)).item())
+            del Fv
+        del fd
+    for arith in ("fp64", "fp32"):
+        variants[arith]["force_rel_err_vs_fp64_path_max"] = max(ferr[arith])
+
+    # the even-odd clover action (c_sw = 1.0) against the Wilson one on the same fields,
+    # at kappa = 0.13 (1 + A stays positive definite on them at the couplings used)
     clover = None
     if not args.no_clover:
         kc, cswc = 0.13, 1.0
         res_c = {}
         for name, csw in (("wilson_eo", 0.0), ("clover_eo", cswc)):
             apc = lgt.action_params(beta=BETA, kappa=kc, even_odd=True, force_arith=FORCE_ARITH, csw=csw)
-            msc, stc, _, _, _ = timed(sp_mixed, K, W, a=apc)
-            res_c[name] = {"value": world * K / (max_ranks(msc) / 1e3), "ms_per_step": msc / K,
-                           "cg_iters_per_step": statistics.mean(x["iters"] for x in stc)}
+            msc, stc, _, _, _ = timed(sp_mixed, Kv, 1, a=apc)
+            res_c[name] = {"value": whole_job_rate(world, nf * Kv, max_ranks(msc) / 1e3), "ms_per_step": msc / Kv,
+                           "cg_iters_per_step": sum(x["iters"] for x in stc) / Kv}
         clover = {"kappa": kc, "csw": cswc, **res_c,
                   "clover_overhead": res_c["clover_eo"]["ms_per_step"] / res_c["wilson_eo"]["ms_per_step"]}
-        restore()   # the force comparison below is on the starting field
-
-    # error of the headline mixed force against the FP64 path on the same field
-    Fm, _ = lat.force(ap, phi, sp_mixed)
-    force_err = (torch.linalg.norm(Fm - fd) / torch.linalg.norm(fd)).item()
-    del Fm, fd
 
     # dominant kernel: the FP32 hop, timed with CUDA events on its stream inside the
     # timed region; each epilogue variant counts its own algorithmic bytes
@@ -308,11 +412,13 @@ def run_ours(args):
     bytes32 = sum(HOP_BYTES_EPI["fp32"][e] * lat.Vh * n for (p, e), (ms_, n) in kinds.items() if p == "fp32")
     ms32_sum = sum(ms_ for (p, e), (ms_, n) in kinds.items() if p == "fp32")
     n32 = sum(n for (p, e), (ms_, n) in kinds.items() if p == "fp32")
-    hop32_ms = ms32_sum / max(n32, 1)
     achieved = bytes32 / (ms32_sum * 1e-3) / 1e9
     per_variant = {e: {"launches": n, "avg_us": 1e3 * ms_ / n,
                        "GBs": HOP_BYTES_EPI["fp32"][e] * lat.Vh / (ms_ / n * 1e-3) / 1e9}
                    for (p, e), (ms_, n) in kinds.items() if p == "fp32"}
+    hop_share = ms32_sum / ms   # FP32 hop launches' share of the timed region
+    fp64_kinds = {e: {"launches": n, "avg_us": 1e3 * ms_ / n}
+                  for (p, e), (ms_, n) in kinds.items() if p == "fp64"}
     kinds64, _ = kt64
     plain64 = kinds64.get(("fp64", "hop"), (0.0, 0))
     hop64_ms = plain64[0] / max(plain64[1], 1)
@@ -320,145 +426,155 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources_sha256"] == hop_sources_hash() else None
 
-    # end to end through the public API with host buffers: every step uploads the
-    # canonical links and phi from pinned host memory and downloads the canonical
-    # force; the upload of step k+1 and the download of step k run on a copy stream
-    # while step k / k+1 compute (two device staging slots)
+    # end to end through the public API with host buffers: for every force evaluation the
+    # canonical links, momenta and phi are uploaded from pinned host memory, the MD update
+    # (force + kick, link update) runs, and the kicked canonical momenta are downloaded;
+    # the upload of evaluation j+1 and the download of j run on copy streams of their own
+    # while j / j+1 compute (two device staging slots)
     e2e = None
     if not args.no_e2e:
-        Ke = max(2, min(K, args.e2e_steps))
-        # the gauge configurations of the headline's first timed MD steps (an untimed
-        # replay of the same sequence), so that every end-to-end force evaluation is
-        # one the headline also timed; at most 4 kept in pinned host memory, cycled
-        n_cfg = min(Ke, 4)
-        Uhs = []
-        restore()
-        st_replay = []
-        for _ in range(W):
-            step(sp_mixed, st_replay)
-        for _ in range(n_cfg):
-            Uhs.append(lat.get_links().cpu().pin_memory())
-            step(sp_mixed, st_replay)
-        Uh = Uhs[0]
+        Ke = max(1, min(K, args.e2e_steps))
+        Uhs = [U.cpu().pin_memory() for U, _ in fields]
+        Mhs = [lat.unpack_momenta(m).cpu().pin_memory() for _, m in fields]
         phic = lat.unpack_spinor(phi, lgt.EVEN, lgt.FP64).cpu().pin_memory()
-        Fh = [torch.empty((lat.V, 4, 8), dtype=torch.float64).pin_memory() for _ in range(2)]
-        Ud = [torch.empty_like(Uh, device="cuda") for _ in range(2)]
+        Mout = [torch.empty_like(Mhs[0]).pin_memory() for _ in range(2)]
+        Ud = [torch.empty_like(Uhs[0], device="cuda") for _ in range(2)]
+        Md = [torch.empty_like(Mhs[0], device="cuda") for _ in range(2)]
         phid = [torch.empty_like(phic, device="cuda") for _ in range(2)]
-        Fd = [torch.empty((lat.V, 4, 8), dtype=torch.float64, device="cuda") for _ in range(2)]
-        # uploads and downloads on streams of their own (the two copy engines run both
-        # directions at once, and an upload never queues behind a download)
-        copy = torch.cuda.Stream()
+        Mres = [torch.empty_like(Mhs[0], device="cuda") for _ in range(2)]
+        copy_in = torch.cuda.Stream()
         copy_out = torch.cuda.Stream()
         ev_in = [torch.cuda.Event() for _ in range(2)]
         ev_free = [torch.cuda.Event() for _ in range(2)]
         ev_out = [torch.cuda.Event() for _ in range(2)]
-        e2e_iters = []
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        e2e_st = []
 
-        def upload(k):
-            q = k % 2
-            with torch.cuda.stream(copy):
-                copy.wait_event(ev_free[q])
-                Ud[q].copy_(Uhs[k % n_cfg], non_blocking=True)
+        def upload(j):
+            q = j % 2
+            with torch.cuda.stream(copy_in):
+                copy_in.wait_event(ev_free[q])
+                Ud[q].copy_(Uhs[j % nf], non_blocking=True)
+                Md[q].copy_(Mhs[j % nf], non_blocking=True)
                 phid[q].copy_(phic, non_blocking=True)
-                ev_in[q].record(copy)
+                ev_in[q].record(copy_in)
 
-        def compute(k):
-            q = k % 2
+        def compute(j):
+            q = j % 2
             stream.wait_event(ev_in[q])
+            stream.wait_event(ev_done[q])   # the slot's previous download has finished
             lat.set_links(Ud[q])
             pf = lat.pack_spinor(phid[q], lgt.EVEN, lgt.FP64)
+            m = lat.pack_momenta(Md[q])
             ev_free[q].record(stream)
-            F, fs = lat.force(ap, pf, sp_mixed)
-            e2e_iters.append(fs["iters"])
-            Fd[q].copy_(lat.unpack_momenta(F))
+            e2e_st.append(lat.md_update(m, EPS, lgt.UPDATE_P, ap, pf, sp_mixed))
+            lat.md_update(m, EPS, lgt.UPDATE_U)
+            Mres[q].copy_(lat.unpack_momenta(m))
             ev_out[q].record(stream)
 
-        def download(k):
-            q = k % 2
+        def download(j):
+            q = j % 2
             with torch.cuda.stream(copy_out):
                 copy_out.wait_event(ev_out[q])
-                Fh[q].copy_(Fd[q], non_blocking=True)
+                Mout[q].copy_(Mres[q], non_blocking=True)
+                ev_done[q].record(copy_out)
 
         def pipeline(n):
             upload(0)
-            for k in range(n):
-                if k + 1 < n:
-                    upload(k + 1)
-                compute(k)
-                download(k)
+            for j in range(n):
+                if j + 1 < n:
+                    upload(j + 1)
+                compute(j)
+                download(j)
             torch.cuda.synchronize()
 
-        pipeline(2)
+        pipeline(nf)   # warm-up: one step
         barrier()
-        e2e_iters.clear()
+        e2e_st.clear()
         t0 = time.perf_counter()
-        pipeline(Ke)
+        pipeline(nf * Ke)
         barrier()
         te = max_ranks(time.perf_counter() - t0)
-
-        # the host link alone: one upload and one download of a step's bytes
-        def copy_time(fn):
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            b.record()
-            torch.cuda.synchronize()
-            return a.elapsed_time(b) * 1e-3
-        h2d_b, d2h_b = Uh.numel() * 16 + phic.numel() * 16, Fh[0].numel() * 8
-        t_up = copy_time(lambda: (Ud[0].copy_(Uh, non_blocking=True), phid[0].copy_(phic, non_blocking=True)))
-        t_down = copy_time(lambda: Fh[0].copy_(Fd[0], non_blocking=True))
-        e2e = {"value": world * Ke / te, "unit": UNIT,
-               "h2d_bytes_per_step": h2d_b,
-               "d2h_bytes_per_step": d2h_b,
-               "h2d_GBs": h2d_b / t_up / 1e9, "d2h_GBs": d2h_b / t_down / 1e9,
-               "cg_iters_per_step": statistics.mean(e2e_iters),
-               "steps": Ke, "step": "upload canonical links (the configurations of the headline's first "
-                                   "timed MD steps) + phi from pinned host memory, force (mixed CG), "
-                                   "download canonical force; uploads and downloads overlap the "
-                                   "neighbouring steps' compute on copy streams"}
-        del Uhs, Uh
+        h2d_b = Uhs[0].numel() * 16 + Mhs[0].numel() * 8 + phic.numel() * 16
+        d2h_b = Mout[0].numel() * 8
+        e2e = {"value": whole_job_rate(world, nf * Ke, te), "unit": UNIT,
+               "h2d_bytes_per_step": nf * h2d_b, "d2h_bytes_per_step": nf * d2h_b, "steps": Ke,
+               "cg_iters_per_step": sum(x["iters"] for x in e2e_st) / Ke,
+               "step": "per field: upload canonical links, momenta and phi from pinned host memory, MD update "
+                       "through the public API (force + kick, link update), download the kicked canonical "
+                       "momenta; copies overlap the neighbouring evaluations on copy streams"}
+        del Uhs, Mhs, Ud, Md, Mres
 
     multi = run_multi_rhs(lat, stream) if not args.no_multi else None
 
     serving = None
     if args.serve_requests > 0:
         free, total = torch.cuda.mem_get_info()
-        serving = {"full": run_serving(args.serve_requests, int(0.8 * free)),
-                   "tight_8GB": run_serving(args.serve_requests, 8 << 30) if args.serve_tight else None}
+        serving = {"full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup),
+                   "tight_8GB": run_serving(args.serve_requests, 8 << 30, warmup=args.serve_warmup)
+                   if args.serve_tight else None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        est, cores, sample = oracle_sample(int(round(iters64)), reps=1)
-        cpu = {"value": 1.0 / statistics.mean(est), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": sample}
+        iters64 = {f: per_field64[str(f)]["iters"] for f in FIELD_STEPS}
+        est, sample = oracle_step_estimate(iters64)
+        full = oracle_full_force()
+        cpu = {"value": len(FIELD_STEPS) / est, "unit": UNIT, "kind": "oracle", "cores": full["threads"],
+               "sample": sample, "cpu_model": full["model"],
+               "full_force_24x4": {"seconds": full["seconds"], "cg_iters": full["cg_iters"],
+                                   "threads": full["threads"],
+                                   "paper_table1_single_thread_s": TABLE1_PAPER_S["single_thread_cpu_handwritten"]}}
+
+    detail = {"plaquette_per_field": dict(zip(map(str, FIELD_STEPS), plaq)),
+              "solver_per_field_mixed": per_field, "solver_per_field_fp64": per_field64,
+              "force_rel_err_vs_fp64_path_per_field": ferr, "force_arith_variants": variants,
+              "dslash_fp32_variants": per_variant, "fp64_kernels_in_mixed_region": fp64_kinds,
+              "clover": clover, "multi_rhs": multi, "serving": serving, "e2e": e2e, "cpu_baseline": cpu}
+
+    def serve_summary(sv):
+        if not sv:
+            return None
+        return {"saturated_req_s": sv["saturated_requests_per_s"], "requests_per_rate": sv["requests_per_rate"],
+                **{r: [v["p50_ms"], v["p99_ms"], v["failed"]] for r, v in sv["rates"].items()}}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32 CG + f64 reliable updates + df64 forces (mixed)", "data": "synthetic: seeded links exp(i 0.5 H), Gaussian pseudofermion",
+           "dtype": "f32 CG + f64 reliable updates + df64 forces (mixed)",
+           "data": "synthetic: seeded exp(i 0.5 H) links evolved by seeded MD, Gaussian phi",
            "config": config_block(args),
-           "cg_iters_per_step": iters, "reliable_updates_per_step": rel,
-           "fp64": {"value": value64, "ms_per_step": ms64 / K64, "steps": K64, "cg_iters_per_step": iters64,
+           "cg": {"iters_per_step": sums["iters"], "iters_per_field": [per_field[str(f)]["iters"] for f in FIELD_STEPS],
+                  "reliable_updates_per_step": sums["reliable_updates"], "breakdowns_per_step": sums["breakdowns"],
+                  "diverged_per_step": sums["diverged"], "handovers_per_step": sums["handovers"],
+                  "fp64_iters_per_step": sums["fp64_iters"]},
+           "fp64": {"value": value64, "ms_per_step": ms64 / K64, "steps": K64,
+                    "iters_per_field": [per_field64[str(f)]["iters"] for f in FIELD_STEPS],
                     "mixed_speedup": value / value64,
-                    "mixed_force_rel_err_vs_fp64_path": force_err},
-           "force_arith": FORCE_ARITH, "force_arith_variants": variants,
-           "dslash": {"fp32_hop_avg_us": hop32_ms * 1e3, "fp32_hop_GBs_algorithmic": achieved,
-                      "fp32_variants": per_variant,
-                      "fp32_hop_launches": n32, "skipped_hop_launches": n32_short,
-                      "fp64_plain_hop_us": hop64_ms * 1e3,
-                      "fp64_hop_TFLOPs": HOP_FLOPS * lat.Vh / (hop64_ms * 1e-3) / 1e12,
-                      "fp64_peak_TFLOPs_measured": fp64_peak / 1e12,
-                      "fp64_hop_frac_of_fp64_peak": HOP_FLOPS * lat.Vh / (hop64_ms * 1e-3) / fp64_peak},
+                    "mixed_force_rel_err_vs_fp64_path_max": max(ferr["df64"])},
            "roofline": {"bound": "hbm", "kernel": "hop_kernel<float> (FP32 Wilson hop, two-row links)",
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "peak_source": peak_kind,
-                        "traffic": traffic, "traffic_kernel": "plain FP32 hop (ncu capture)",
-                        "algorithmic_bytes_per_launch": bytes32 / max(n32, 1),
-                        "algorithmic_bytes_plain_hop": HOP_BYTES["fp32"] * lat.Vh},
-           "clover": clover,
-           "multi_rhs": multi,
-           "serving": serving,
-           "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches}
+                        "peak_source": peak_kind, "traffic": traffic,
+                        "algorithmic_bytes_per_launch": bytes32 / max(n32, 1), "launches": n32,
+                        "share_of_step": hop_share},
+           "dslash": {"fp32_plain_hop_us": per_variant.get("hop", {}).get("avg_us"),
+                      "fp64_plain_hop_us": hop64_ms * 1e3,
+                      "fp64_hop_frac_of_fp64_peak": HOP_FLOPS * lat.Vh / (hop64_ms * 1e-3) / fp64_peak},
+           "force_arith_variants": {k: round(v["value"], 3) for k, v in variants.items()},
+           "clover_overhead": clover["clover_overhead"] if clover else None,
+           "multi_rhs_solve4_speedup": multi["solve4"]["speedup"] if multi else None,
+           "serving": serve_summary(serving["full"]) if serving else None,
+           "serving_tight_8GB": serve_summary(serving["tight_8GB"]) if serving else None,
+           "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "kind", "cores", "cpu_model")} |
+                            {"sample": "estimate from a capped-CG sample (see detail)",
+                             "full_force_24x4_s": cpu["full_force_24x4"]["seconds"]}) if cpu else None,
+           "e2e": ({k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "steps")}
+                   if e2e else None),
+           "clocks": clk, "gpu_launches": launches}
+    # nested figures to 4 significant digits (the line must fit a 3 kB log tail)
+    out = {k: (v if k in ("value", "ms_per_step", "config", "metric") else _round(v)) for k, v in out.items()}
+    if args.detail and rank == 0:
+        os.makedirs(os.path.dirname(os.path.abspath(args.detail)), exist_ok=True)
+        with open(args.detail, "w") as f:
+            json.dump({"line": out, "detail": detail}, f, indent=1)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -514,31 +630,38 @@ def run_multi_rhs(lat, stream, reps=50):
 SERVE_VOLUMES = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 48)]
 
 
-def run_serving(n_per_rate, budget_bytes, seed=10):
+def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9, 1.2)):
     """Resident pool of 2 gauge fields per volume (alpha ~ U[0.3, 0.6]); requests:
     70% Dirac solves, 30% force evaluations, kappa ~ U[0.14, 0.157], FP64 / mixed
     50/50, tol 1e-10.  Saturated throughput, then open-loop Poisson arrivals at
-    0.5, 0.9 and 1.2 x that rate; latency = completion - scheduled arrival."""
+    0.5, 0.9 and 1.2 x that rate (1.2 x is overload: no steady state); latency =
+    completion - scheduled arrival, over the requests after the first `warmup`."""
     import numpy as np
     from paper_2602_20516_b300 import serve
     rng = np.random.default_rng(seed)
     srv = serve.Server(budget_bytes, max_active=64, batch_iters=8, delta=DELTA)
-    gids = []
+    gids, vol = [], {}
     for k, d in enumerate(SERVE_VOLUMES):
         for j in range(2):
-            gids.append(srv.add_gauge(d, 1000 + 10 * k + j, float(rng.uniform(0.3, 0.6))))
-    warm = max(10, n_per_rate // 10)
+            g = srv.add_gauge(d, 1000 + 10 * k + j, float(rng.uniform(0.3, 0.6)))
+            gids.append(g)
+            vol[g] = "x".join(map(str, d))
+    warm = max(10, n_per_rate // 10) if warmup is None else warmup
     serve.saturated(srv, serve.workload(gids, warm, seed=seed))          # warm-up
     thr, done = serve.saturated(srv, serve.workload(gids, n_per_rate, seed=seed + 1))
     out = {"saturated_requests_per_s": thr, "budget_bytes": budget_bytes,
            "requests_per_rate": n_per_rate, "warmup_per_rate": warm, "rates": {}}
-    for j, f in enumerate((0.5, 0.9, 1.2)):
+
+    def label(c):
+        return f"{vol[c['gauge_id']]}/{'solve' if c['kind'] == serve.SOLVE else 'force'}/{c['precision']}"
+    for j, f in enumerate(rates):
         reqs = serve.workload(gids, n_per_rate + warm, seed=seed + 2 + j)
         d = serve.poisson(srv, reqs, f * thr, seed=seed + 20 + j, warmup=warm)
         st = serve.latency_stats(d)
-        solves = [c for c in d if c["status"] == 0]
         st["offered_per_s"] = f * thr
-        st["completed"] = len(solves)
+        st["completed"] = len(d)
+        st["overload"] = f > 1.0
+        st["by_class"] = serve.latency_breakdown(d, label)
         out["rates"][f"{f}x"] = st
     srv.close()
     return out
@@ -600,19 +723,44 @@ def run_hmc(args):
 
 # ---------------------------------------------------------------- reference arm (the oracle)
 def run_reference(args):
+    """The oracle on the host cores, on this arm's workload: each step is the
+    estimate of one step (four force evaluations with their link updates) from a
+    bounded capped-CG sample, scaled with the same FP64 iteration counts of the four
+    fields that the default arm measures on the GPU."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     K, W = args.steps, args.warmup
-    est, cores, sample = oracle_sample(CG_ITERS_FP64, reps=W + K)
+    est = []
+    for _ in range(W + K):
+        t, sample = oracle_step_estimate(CG_ITERS_FP64)
+        est.append(t)
     timed = est[W:]
-    value = len(timed) / sum(timed)
+    value = len(FIELD_STEPS) * len(timed) / sum(timed)
+    info = cpu_info()
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": K, "warmup": W, "ms_per_step": 1e3 * statistics.mean(timed), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (same seeds)",
            "config": config_block(args),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
+                            "cpu_model": info["model"], "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- serving record (config 5 as stated)
+def run_serve_only(args):
+    """The serving measurement alone, under the full budget and under 8 GB:
+    --serve-requests per arrival rate after --serve-warmup (config 5: 5000 after 200)."""
+    import torch
+    torch.cuda.set_device(0)
+    free, _ = torch.cuda.mem_get_info()
+    out = {"metric": "serving: p50/p99 latency (arrival -> completion) and requests/s",
+           "full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup),
+           "tight_8GB": run_serving(args.serve_requests, 8 << 30, warmup=args.serve_warmup)}
+    if args.detail:
+        with open(args.detail, "w") as f:
+            json.dump(out, f, indent=1)
     print(json.dumps(out), flush=True)
 
 
@@ -659,16 +807,23 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=10,
-                    help="timed steps of the FP64 path (the first ones of the same MD sequence)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--detail", default="", help="also write the per-field and per-phase figures to this file")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the FP64 path (same four fields; each step the same work)")
+    ap.add_argument("--variant-steps", type=int, default=3,
+                    help="timed steps of the force-arithmetic and clover variants")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the several-sources measurement")
     ap.add_argument("--no-clover", action="store_true", help="skip the even-odd clover measurement")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests per arrival rate in the serving measurement (0 skips it)")
+    ap.add_argument("--serve-warmup", type=int, default=None,
+                    help="warm-up requests per rate (default: a tenth of --serve-requests)")
     ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving measurement (full budget and 8 GB) and print it")
     ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
     ap.add_argument("--hmc-fp64", type=int, default=2, help="trajectories replayed on the FP64 path")
     ap.add_argument("--log", default="", help="HMC mode: append one JSON line per trajectory to this file")
@@ -677,13 +832,22 @@ def main():
                     help="HMC mode: MD solves start from the last N solutions (chronological guess)")
     ap.add_argument("--kernel", choices=["hop32", "hop64", "force_df", "clover_md"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--cpu-table1", action="store_true",
+                    help="one complete oracle force evaluation at 24^4 with 1 thread and with every core")
+    ap.add_argument("--cpu-force-once", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.impl == "ours" and not args.kernel:
         args.warmup = max(3, args.warmup)   # timing rule: at least 3 untimed steps
-    if args.kernel:
+    if args.cpu_force_once:
+        print(json.dumps(oracle_full_force()))
+    elif args.cpu_table1:
+        print(json.dumps(cpu_table1()))
+    elif args.kernel:
         run_kernel(args)
     elif args.hmc > 0:
         run_hmc(args)
+    elif args.serve_only:
+        run_serve_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -156,6 +156,18 @@ typedef struct {
     int reliable_updates;    /* FP64 residual replacements */
     double true_rel_residual;
     double seconds;          /* host wall time of the call */
+    /* how the mixed solver got there (all 0 for a clean mixed solve; summed where
+     * stats of several solves are accumulated): */
+    int breakdowns;          /* FP32 recursions restarted from the FP64 residual after a
+                                non-finite or non-positive <p, A p> */
+    int diverged;            /* FP32 cycles dropped because their recursion residual grew
+                                1e3-fold (in |r|^2) above the true residual they started from */
+    int handovers;           /* solves whose FP32 iterations stopped reducing the true residual
+                                (two reliable updates in a row short of halving it) and that
+                                were finished by CG in FP64 */
+    int fp64_iters;          /* iterations of CG in FP64 (every iteration of an LGT_FP64 solve;
+                                the iterations after a hand-over in a mixed solve) */
+    int restarts;            /* solves from a chronological guess redone from x = 0 */
 } lgt_solve_stats;
 
 typedef struct {

@@ -5,6 +5,7 @@ dims[0] | dims[1] << 32, dims[2] | dims[3] << 32, seed, next trajectory, payload
 the canonical links (complex128 [V][4][3][3]), then the FNV-1a hash of header and
 payload over 64-bit words.  The hash is a sequential recurrence, computed here in
 Python: fine for small lattices and tests, slow (minutes) for 32^3 x 64 files."""
+import os
 import struct
 
 import numpy as np
@@ -39,10 +40,16 @@ def write(path, dims, seed, next_traj, links):
     payload = links.view("<u8").reshape(-1)
     head = _header(dims, int(seed), int(next_traj), payload.nbytes)
     h = fnv1a_words(payload, fnv1a_words(head))
-    with open(path, "wb") as f:
+    # written beside the target, flushed to disk and renamed over it, so an
+    # interrupted write leaves the previous checkpoint intact
+    tmp = str(path) + ".tmp"
+    with open(tmp, "wb") as f:
         f.write(head.tobytes())
         f.write(payload.tobytes())
         f.write(struct.pack("<Q", h))
+        f.flush()
+        os.fsync(f.fileno())
+    os.replace(tmp, path)
 
 
 def read(path, verify=True):

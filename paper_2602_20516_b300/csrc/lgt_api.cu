@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unistd.h>
 #include <vector>
 
 #include "../../include/lgt.h"
@@ -37,7 +38,7 @@ int set_error(int code, const char* msg) {
     return code;
 }
 bool kernel_timing_slot(int kind, cudaEvent_t* a, cudaEvent_t* b) {
-    if (!g_kt.on || g_kt.used + 2 > g_kt.ev.size()) return false;
+    if (!g_kt.on || g_kt.used + 2 > g_kt.ev.size() || g_kt.used / 2 >= g_kt.kind.size()) return false;
     *a = g_kt.ev[g_kt.used];
     *b = g_kt.ev[g_kt.used + 1];
     g_kt.kind[g_kt.used / 2] = kind;
@@ -547,10 +548,22 @@ extern "C" int lgt_save_checkpoint(lgt_lattice_t L, const char* path, uint64_t s
     CK(cudaMemcpyAsync(h + 7, L->ckpt, bytes, cudaMemcpyDeviceToHost, L->st));
     CK(cudaStreamSynchronize(L->st));
     const uint64_t sum = fnv1a_words(0xcbf29ce484222325ull, buf.data(), buf.size());
-    FILE* f = fopen(path, "wb");
-    if (!f) return fail(LGT_EINVAL, "cannot open %s for writing", path);
-    const bool ok = fwrite(buf.data(), 8, buf.size(), f) == buf.size() && fwrite(&sum, 8, 1, f) == 1;
-    if (fclose(f) != 0 || !ok) return fail(LGT_EINVAL, "writing %s failed", path);
+    // written beside the target and renamed over it once complete and flushed to disk,
+    // so a crash or a full disk mid-write leaves the previous checkpoint intact
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return fail(LGT_EINVAL, "cannot open %s for writing", tmp.c_str());
+    bool ok = fwrite(buf.data(), 8, buf.size(), f) == buf.size() && fwrite(&sum, 8, 1, f) == 1;
+    ok = fflush(f) == 0 && ok;
+    ok = fsync(fileno(f)) == 0 && ok;
+    if (fclose(f) != 0 || !ok) {
+        remove(tmp.c_str());
+        return fail(LGT_EINVAL, "writing %s failed", tmp.c_str());
+    }
+    if (rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return fail(LGT_EINVAL, "renaming %s to %s failed", tmp.c_str(), path);
+    }
     return LGT_OK;
 }
 
@@ -1046,7 +1059,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     const int K = sp->check_every > 0 ? sp->check_every : 16;
     const bool mixed = sp->precision == LGT_MIXED;
     const size_t b64 = (size_t)n * 12 * sizeof(double2), b32 = (size_t)n * 6 * sizeof(float4);
-    lgt_solve_stats st = {0, 0, 0.0, 0.0};
+    lgt_solve_stats st = {};
 
     CK(blas_norm2(b, n, L->g.Vh, true, red(L), 0, L->st));
     TRY(sync_scalars(L));
@@ -1108,7 +1121,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     // continues in FP64 CG from the current x and residual.
     bool use32 = mixed;
     bool guessed = guess;   // still iterating from a chronological guess
-    int breakdowns = 0, poor = 0, iters_at_update = 0;
+    int breakdowns = 0, poor = 0, iters_at_update = 0, iters_handover = 0;
     double rr_prev = rr0;
     // an FP32 cycle that runs this long without its stop test firing is ended by a
     // reliable update as well (its progress is then judged like any other); a solve from
@@ -1131,6 +1144,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
         rr_true = rr_prev = bb;
         poor = breakdowns = 0;
         guessed = false;
+        st.restarts += 1;
         hs->rr = hs->rr_max = bb;
         hs->done = 0;
         hs->nan = 0;
@@ -1164,6 +1178,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
                 break;
             }
             iters_at_update = hs->iters;
+            st.diverged += 1;
             CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
             CK(blas_d2f(L->r32, L->r, n, L->g.Vh, L->st));
             CK(cudaMemcpyAsync(L->p32, L->r32, b32, cudaMemcpyDeviceToDevice, L->st));
@@ -1189,6 +1204,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
         }
         if (hs->done || hit_cap || breakdown || long_cycle) {
             iters_at_update = hs->iters;
+            if (breakdown) st.breakdowns += 1;
             if (use32) {
                 CK(blas_add_f2d(x, L->x32, n, L->g.Vh, L->st));
                 CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
@@ -1218,6 +1234,8 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
                 poor = slow ? poor + 1 : 0;
                 if (poor >= 2) {   // the FP32 iterations stopped making progress: FP64 from here
                     use32 = false;
+                    st.handovers = 1;
+                    iters_handover = hs->iters;
                     CK(cudaMemcpyAsync(L->p, L->r, b64, cudaMemcpyDeviceToDevice, L->st));
                 }
             }
@@ -1236,6 +1254,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     }
     CK(cudaStreamSynchronize(L->st));
     st.iters = hs->iters;
+    st.fp64_iters = mixed ? (st.handovers ? hs->iters - iters_handover : 0) : hs->iters;
     st.true_rel_residual = std::sqrt(rr_true / bb);
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = st;
@@ -1245,6 +1264,11 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
 static void add_stats(lgt_solve_stats* acc, const lgt_solve_stats& s) {
     acc->iters += s.iters;
     acc->reliable_updates += s.reliable_updates;
+    acc->breakdowns += s.breakdowns;
+    acc->diverged += s.diverged;
+    acc->handovers += s.handovers;
+    acc->fp64_iters += s.fp64_iters;
+    acc->restarts += s.restarts;
     acc->true_rel_residual = s.true_rel_residual > acc->true_rel_residual ? s.true_rel_residual : acc->true_rel_residual;
     acc->seconds += s.seconds;
 }
@@ -1339,7 +1363,7 @@ static int cg_multi(lgt_lattice* L, int nrhs, const double2* const* b, double2* 
     for (int k = 0; k < nrhs; ++k) CK(blas_norm2(b[k], n, L->g.Vh, true, red(L), k, L->st));
     TRY(sync_scalars(L));
     double bb[KMAX_RHS], rr_true[KMAX_RHS];
-    int rel[KMAX_RHS];
+    int rel[KMAX_RHS], div[KMAX_RHS] = {};
     bool fin[KMAX_RHS];
     int rc = LGT_OK;
     memset(W.hs, 0, sizeof(Scalars) * KMAX_RHS);
@@ -1375,6 +1399,7 @@ static int cg_multi(lgt_lattice* L, int nrhs, const double2* const* b, double2* 
             Scalars& h = W.hs[k];
             // a diverged FP32 cycle restarts from its last true residual (as cg_core)
             if (!h.nan && h.rr_max > 1e3 * rr_true[k]) {
+                div[k] += 1;
                 CK(cudaMemsetAsync(W.x32[k], 0, b32, L->st));
                 CK(blas_d2f(W.r32[k], W.r64[k], n, L->g.Vh, L->st));
                 CK(cudaMemcpyAsync(W.p32[k], W.r32[k], b32, cudaMemcpyDeviceToDevice, L->st));
@@ -1417,7 +1442,8 @@ static int cg_multi(lgt_lattice* L, int nrhs, const double2* const* b, double2* 
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats)
         for (int k = 0; k < nrhs; ++k)
-            stats[k] = lgt_solve_stats{W.hs[k].iters, rel[k], bb[k] > 0 ? std::sqrt(rr_true[k] / bb[k]) : 0.0, secs};
+            stats[k] = lgt_solve_stats{W.hs[k].iters, rel[k], bb[k] > 0 ? std::sqrt(rr_true[k] / bb[k]) : 0.0, secs,
+                                       0, div[k], 0, 0, 0};
     return rc;
 }
 
@@ -1535,7 +1561,7 @@ extern "C" int lgt_action(lgt_lattice_t L, const lgt_action_params* ap, const do
                           const lgt_solver_params* sp, double* S_g, double* S_f, lgt_solve_stats* stats) {
     if (!L) return fail(LGT_EINVAL, "null lattice");
     TRY(check_action(ap));
-    if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
+    if (stats) *stats = lgt_solve_stats{};
     if (S_g) {
         double s;
         TRY(gauge_action_value(L, ap, &s));
@@ -1781,7 +1807,7 @@ extern "C" int lgt_force(lgt_lattice_t L, const lgt_action_params* ap, const dou
     if (!L || !F_out) return fail(LGT_EINVAL, "null argument");
     TRY(check_action(ap));
     if (form != LGT_FORCE_LIE && form != LGT_GRAD_G) return fail(LGT_EINVAL, "form %d", form);
-    if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
+    if (stats) *stats = lgt_solve_stats{};
     if (ap->n_stout == 0) {
         Links fl;
         TRY(fermion_links(L, ap, &fl));
@@ -1817,14 +1843,14 @@ extern "C" int lgt_md_update(lgt_lattice_t L, double* mom, double eps, int which
                              const double* phi, const lgt_solver_params* sp, lgt_solve_stats* stats) {
     if (!L || !mom) return fail(LGT_EINVAL, "null argument");
     NvtxRange nvtx(which == LGT_UPDATE_U ? "lgt update U" : "lgt update P");
-    if (stats) *stats = lgt_solve_stats{0, 0, 0.0, 0.0};
+    if (stats) *stats = lgt_solve_stats{};
     if (which == LGT_UPDATE_U) {
         CK(gauge_update_links(L->thin.U, L->thin.U12, (const double2*)mom, eps, L->g, L->st));
         return LGT_OK;
     }
     if (which != LGT_UPDATE_P) return fail(LGT_EINVAL, "which = %d", which);
     TRY(check_action(ap));
-    lgt_solve_stats s = {0, 0, 0.0, 0.0};
+    lgt_solve_stats s = {};
     TRY(kick(L, (double2*)mom, eps, ap, (const double2*)phi, sp, &s));
     CK(cudaStreamSynchronize(L->st));
     if (stats) *stats = s;
@@ -1851,7 +1877,7 @@ static int integrate(lgt_lattice* L, const lgt_action_params* ap, const lgt_hmc_
     const double eps = hp->tau / hp->n_steps;
     lgt_solve_stats s;
     auto K = [&](double e) -> int {
-        s = lgt_solve_stats{0, 0, 0.0, 0.0};
+        s = lgt_solve_stats{};
         int r = kick(L, L->mom, e, ap, phi, &hp->md_solver, &s);
         add_stats(tot, s);
         ++*evals;
@@ -1885,7 +1911,7 @@ static int integrate(lgt_lattice* L, const lgt_action_params* ap, const lgt_hmc_
         const int m = hp->n_inner > 0 ? hp->n_inner : 1;
         const double ein = eps / m;
         auto KP = [&](const lgt_action_params* a, double e) -> int {
-            s = lgt_solve_stats{0, 0, 0.0, 0.0};
+            s = lgt_solve_stats{};
             int r = kick(L, L->mom, e, a, phi, &hp->md_solver, &s);
             add_stats(tot, s);
             ++*evals;
@@ -1943,7 +1969,7 @@ extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, 
     if (ap->fermions) {
         Links lk;
         TRY(fermion_links(L, ap, &lk));
-        lgt_solve_stats s = {0, 0, 0.0, 0.0};
+        lgt_solve_stats s = {};
         TRY(pf_action_on(L, lk, ap, L->phi, &hp->action_solver, &res->Sf_new, &s));
         add_stats(&res->total, s);
     }

@@ -100,13 +100,15 @@ __global__ void __launch_bounds__(NT) plaquette_noalloc_kernel(const double2* __
 extern "C" int lgt_plaquette_noalloc(const double* links_canonical, const int dims[4], double* plaq_dev,
                                      void* stream) {
     if (!links_canonical || !dims || !plaq_dev) return lgt::set_error(LGT_EINVAL, "null argument");
+    // the limit is checked after every factor, so the product never exceeds
+    // kMaxSites * INT_MAX and cannot overflow
     long V = 1;
     for (int m = 0; m < 4; ++m) {
         if (dims[m] < 2 || dims[m] % 2) return lgt::set_error(LGT_EINVAL, "every extent must be even and >= 2");
         V *= dims[m];
+        if (V > kMaxSites)
+            return lgt::set_error(LGT_EINVAL, "volume exceeds the 8388608-site limit of the static scratch array");
     }
-    if (V > kMaxSites)
-        return lgt::set_error(LGT_EINVAL, "volume exceeds the 8388608-site limit of the static scratch array");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return lgt::set_error(LGT_ECUDA, "no usable current CUDA device");

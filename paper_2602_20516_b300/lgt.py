@@ -40,7 +40,9 @@ class SolverParams(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("reliable_updates", C.c_int),
-                ("true_rel_residual", C.c_double), ("seconds", C.c_double)]
+                ("true_rel_residual", C.c_double), ("seconds", C.c_double),
+                ("breakdowns", C.c_int), ("diverged", C.c_int), ("handovers", C.c_int),
+                ("fp64_iters", C.c_int), ("restarts", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -171,17 +171,47 @@ def poisson(server, reqs, rate, seed, warmup=0):
             continue
         c = dict(c)
         c["latency"] = c["t_done"] - arrival[i]
+        c["queued"] = c["t_admit"] - arrival[i]
         c["index"] = i
+        c["gauge_id"] = reqs[i]["gauge_id"]
+        c["kind"] = reqs[i]["kind"]
+        c["precision"] = reqs[i]["precision"]
         out.append(c)
     return out
 
 
+def _pct(a, q):
+    return 1e3 * float(np.percentile(a, q)) if len(a) else None
+
+
 def latency_stats(done):
-    lat = np.array([c["latency"] for c in done if c["status"] == 0])
-    if lat.size == 0:
-        return {"p50_ms": None, "p99_ms": None, "n": 0}
-    return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "mean_ms": 1e3 * float(lat.mean()), "n": int(lat.size),
+    """p50 / p99 / mean latency of the successful completions (failed requests are
+    excluded from these and counted apart), and p99 over every completion."""
+    ok = np.array([c["latency"] for c in done if c["status"] == 0])
+    allc = np.array([c["latency"] for c in done])
+    if ok.size == 0:
+        return {"p50_ms": None, "p99_ms": None, "n": 0, "failed": len(done)}
+    return {"p50_ms": _pct(ok, 50), "p99_ms": _pct(ok, 99),
+            "mean_ms": 1e3 * float(ok.mean()), "n": int(ok.size),
+            "p99_all_completions_ms": _pct(allc, 99), "failures_excluded_from_percentiles": True,
             "failed": int(sum(1 for c in done if c["status"] != 0)),
             "failed_by_status": {str(k): v for k, v in
                                  collections.Counter(c["status"] for c in done if c["status"] != 0).items()}}
+
+
+def latency_breakdown(done, label):
+    """Latency percentiles per class label(c) (e.g. volume, kind, precision), with the
+    time spent queued (arrival -> admission) and served (admission -> completion)."""
+    groups = collections.defaultdict(list)
+    for c in done:
+        if c["status"] == 0:
+            groups[label(c)].append(c)
+    out = {}
+    for k, cs in sorted(groups.items()):
+        lat = np.array([c["latency"] for c in cs])
+        q = np.array([c.get("queued", 0.0) for c in cs])
+        out[k] = {"n": len(cs), "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                  "queued_p50_ms": _pct(q, 50), "served_p50_ms": _pct(lat - q, 50),
+                  "served_p99_ms": _pct(lat - q, 99),
+                  "iters_mean": float(np.mean([c["iters"] for c in cs]))}
+    return out

@@ -56,3 +56,16 @@ def test_invalid_arguments_rejected_on_host(liblgt):
     assert liblgt.lgt_force(None, None, None, None, None, 0, C.byref(st)) == 1
     assert liblgt.lgt_cg_solve_multi(None, 2, None, None, None, None, None) == 1
     assert liblgt.lgt_hop_multi(None, 2, None, None, 0, 0) == 1
+
+
+def test_noalloc_volume_limit_checked_without_overflow(liblgt):
+    """Extents whose product exceeds 2^63 are rejected by the volume limit on the host
+    (the check runs after every factor, before any device call)."""
+    buf = (C.c_double * 4)()
+    big = (C.c_int * 4)(1 << 30, 1 << 30, 1 << 30, 1 << 30)
+    assert liblgt.lgt_plaquette_noalloc(buf, big, buf, None) == 1
+    assert b"limit" in liblgt.lgt_last_error()
+    # a product that wraps to a small value modulo 2^64 (2^62 * 2^2 = 2^64 -> 0)
+    wrap = (C.c_int * 4)(1 << 30, 1 << 30, 1 << 2, 1 << 2)
+    assert liblgt.lgt_plaquette_noalloc(buf, wrap, buf, None) == 1
+    assert b"limit" in liblgt.lgt_last_error()

@@ -58,3 +58,16 @@ def test_corruption_is_detected(tmp_path):
     (tmp_path / "version.lgt").write_bytes(bytes(bad))
     with pytest.raises(ValueError, match="version"):
         ck.read(tmp_path / "version.lgt")
+
+
+def test_write_replaces_atomically(tmp_path):
+    """The writer goes through a temporary file renamed over the target: no .tmp is
+    left behind and an existing checkpoint is replaced whole."""
+    dims = (2, 2, 2, 2)
+    p = tmp_path / "c.lgt"
+    ck.write(p, dims, 1, 1, _links(dims, 5))
+    ck.write(p, dims, 2, 7, _links(dims, 6))
+    assert not (tmp_path / "c.lgt.tmp").exists()
+    r = ck.read(p)
+    assert r["seed"] == 2 and r["next_traj"] == 7
+    assert np.array_equal(r["links"], _links(dims, 6))
