@@ -31,6 +31,7 @@
  *   FP64 spinor field double2 [parity][12][Vh]  component k = 3*spin + colour;
  *                     a half field is the [12][Vh] block of one parity
  *   FP32 spinor field float4  [parity][6][Vh]   float4 k holds components 2k, 2k+1
+ *   DF64 spinor field float4  [parity][12][Vh]  component k as (re.hi, re.lo, im.hi, im.lo)
  *   momenta / forces  double2 [parity][4 mu][4][Vh]  double2 k holds pi_{2k}, pi_{2k+1}
  *   G-form gradient   double2 [parity][4 mu][9][Vh]  entry 3*row + col
  * The handle stores the gauge field as FP64 double2 [parity][4][9][Vh] plus an
@@ -62,7 +63,11 @@ typedef enum {
     LGT_EKERNEL = 6   /* a kernel reported an internal error through its status word */
 } lgt_status;
 
-enum { LGT_FP64 = 0, LGT_MIXED = 1, LGT_FP32 = 2 };      /* precision */
+/* precision.  LGT_DF64 (double-float: a value is an unevaluated pair of FP32 numbers,
+ * about 48 significant bits) is a field layout and operator arithmetic of
+ * lgt_pack_spinor / lgt_unpack_spinor / lgt_dslash (LGT_OP_HOP only): float4
+ * [parity][12][Vh], each float4 = (re.hi, re.lo, im.hi, im.lo), the bytes of FP64. */
+enum { LGT_FP64 = 0, LGT_MIXED = 1, LGT_FP32 = 2, LGT_DF64 = 3 };
 enum { LGT_EVEN = 0, LGT_ODD = 1, LGT_FULL = 2 };         /* parity selector */
 /* operators of lgt_dslash */
 enum { LGT_OP_HOP = 0,       /* out_p = H_{p,1-p} in_{1-p}, p = out_parity (EVEN|ODD) */
@@ -268,8 +273,10 @@ int lgt_set_clover(lgt_lattice_t lat, double csw, double kappa);
 
 /* Apply a Wilson-Dirac operator (Sec. III: "Wilson-Dirac operator"; D of
  * Eq. S3.1) to `in`, writing `out` (distinct buffers, device layout of
- * `precision`, LGT_FP64 or LGT_FP32).  op/out_parity as in the LGT_OP_* enum;
- * dagger != 0 applies the adjoint (H^+ = g5 H g5).  Asynchronous. */
+ * `precision`, LGT_FP64 or LGT_FP32; LGT_DF64 for LGT_OP_HOP only: the hop in
+ * double-float arithmetic on a double-float copy of the links, the operator the
+ * mixed solver forms its true residuals with).  op/out_parity as in the LGT_OP_*
+ * enum; dagger != 0 applies the adjoint (H^+ = g5 H g5).  Asynchronous. */
 int lgt_dslash(lgt_lattice_t lat, const void *in, void *out, int op, int out_parity,
                int dagger, double kappa, int precision);
 
@@ -445,12 +452,13 @@ int lgt_measure_fp64_peak(double *flops, double *seconds);
 /* CUDA-event timing of the Wilson hop launches: start arms up to max_launches
  * event pairs (recorded on the launching stream around each hop launch of any
  * handle); stop waits for them and fills ms[LGT_TIMING_KINDS] / n[LGT_TIMING_KINDS]
- * with the summed durations (ms) and counts per kind = 5 * fp64 + epilogue (0 hop,
- * 1 xpay, 2 xpay + norm, 3 fused CG residual update, 4 true residual).  Launches
+ * with the summed durations (ms) and counts per kind = 5 * arithmetic + epilogue
+ * (arithmetic 0 FP32, 1 FP64, 2 double-float; epilogue 0 hop, 1 xpay, 2 xpay + norm,
+ * 3 fused CG residual update, 4 true residual).  Launches
  * shorter than min_ms are only counted (n_short): inside a CG batch, hops enqueued
  * after the solver stopped return at entry and do no work.  Process-wide; not
  * thread safe. */
-#define LGT_TIMING_KINDS 10
+#define LGT_TIMING_KINDS 15
 int lgt_kernel_timing_start(int max_launches);
 int lgt_kernel_timing_stop(double min_ms, double *ms, int64_t *n, int64_t *n_short);
 /* Kernel launches the library enqueued on this thread since the last reset. */

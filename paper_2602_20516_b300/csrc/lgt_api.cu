@@ -56,6 +56,15 @@ static cudaError_t timed_hop(const HopArgs& A, bool fp64, bool dagger, int epi, 
     if (timed) cudaEventRecord(e1, st);
     return e;
 }
+// the double-float hop, timed as kind 10 + epilogue
+static cudaError_t timed_hop_df(const HopArgs& A, bool dagger, int epi, cudaStream_t st) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = kernel_timing_slot(10 + epi, &e0, &e1);
+    if (timed) cudaEventRecord(e0, st);
+    cudaError_t e = launch_hop_df(A, dagger, epi, st);
+    if (timed) cudaEventRecord(e1, st);
+    return e;
+}
 
 static int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -126,6 +135,14 @@ struct lgt_lattice {
     // cap_valid says so
     double2 *cap_X, *cap_Y;
     bool cap_valid;
+    // the mixed even-odd Wilson solver forms its true residuals in double-float: the
+    // same vectors are then left as double-float copies, x_e and X_o in Xdf, eta_e
+    // and Y_o in Ydf, and cap_df_valid says so (cap_valid stays false until they are
+    // converted to FP64 for a consumer that needs them there)
+    bool cap_df_valid = false;
+    // the FP64 links the double-float copy Udf was last built from, within one solve
+    // or force evaluation (nullptr: rebuild)
+    const double2* udf_src = nullptr;
     float4 *r32, *p32, *x32, *u32, *t32, *X32, *Y32;
     bool have_solver;
     // double-float copies for LGT_ARITH_DF64 forces: links, X, Y
@@ -654,15 +671,33 @@ static int check_parity(int parity) {
     if (parity < 0 || parity > 2) return fail(LGT_EINVAL, "parity %d", parity);
     return LGT_OK;
 }
+static int check_precision(int precision) {
+    if (precision != LGT_FP64 && precision != LGT_FP32 && precision != LGT_DF64)
+        return fail(LGT_EINVAL, "precision %d", precision);
+    return LGT_OK;
+}
+// complex entries of a spinor field of parity selector `parity`
+static long spinor_entries(const lgt_lattice* L, int parity) { return (parity == LGT_FULL ? 24L : 12L) * L->g.Vh; }
 extern "C" int lgt_pack_spinor(lgt_lattice_t L, const double* canon, void* field, int parity, int precision) {
     if (!L || !canon || !field) return fail(LGT_EINVAL, "null argument");
     TRY(check_parity(parity));
+    TRY(check_precision(precision));
     CK(spinor_pack(field, (const double2*)canon, L->g, parity, precision != LGT_FP32, L->st));
+    // double-float: the FP64 layout converted in place (each entry is read, then
+    // rewritten as its pair, by the same thread)
+    if (precision == LGT_DF64)
+        CK(complex_to_df((float4*)field, (const double2*)field, spinor_entries(L, parity), L->st));
     return LGT_OK;
 }
 extern "C" int lgt_unpack_spinor(lgt_lattice_t L, const void* field, double* canon, int parity, int precision) {
     if (!L || !canon || !field) return fail(LGT_EINVAL, "null argument");
     TRY(check_parity(parity));
+    TRY(check_precision(precision));
+    if (precision == LGT_DF64) {   // through the FP64 layout in a workspace field
+        TRY(ensure_solver(L));
+        CK(complex_from_df(L->u, (const float4*)field, spinor_entries(L, parity), L->st));
+        field = L->u;
+    }
     CK(spinor_unpack((double2*)canon, field, L->g, parity, precision != LGT_FP32, L->st));
     return LGT_OK;
 }
@@ -802,9 +837,26 @@ extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, in
                           double kappa, int precision) {
     if (!L || !in || !out) return fail(LGT_EINVAL, "null argument");
     if (in == out) return fail(LGT_EINVAL, "in and out must be distinct buffers");
+    const bool dag = dagger != 0;
+    if (precision == LGT_DF64) {
+        if (op != LGT_OP_HOP) return fail(LGT_EINVAL, "LGT_DF64 applies LGT_OP_HOP only");
+        if (out_parity != LGT_EVEN && out_parity != LGT_ODD) return fail(LGT_EINVAL, "hop needs EVEN or ODD");
+        TRY(ensure_df(L));
+        CK(links_to_df(L->Udf, L->thin.U, L->g, L->st));
+        L->udf_src = L->thin.U;
+        HopArgs A;
+        memset(&A, 0, sizeof A);
+        A.U = L->Udf;
+        A.g = L->g;
+        A.parity = out_parity;
+        A.in[1 - out_parity] = in;
+        A.out[out_parity] = out;
+        A.a = 1.0;
+        CK(timed_hop_df(A, dag, EPI_HOP, L->st));
+        return LGT_OK;
+    }
     if (precision != LGT_FP64 && precision != LGT_FP32) return fail(LGT_EINVAL, "precision %d", precision);
     const bool fp64 = precision == LGT_FP64;
-    const bool dag = dagger != 0;
     switch (op) {
     case LGT_OP_HOP:
         if (out_parity != LGT_EVEN && out_parity != LGT_ODD) return fail(LGT_EINVAL, "hop needs EVEN or ODD");
@@ -980,6 +1032,52 @@ static int true_residual(lgt_lattice* L, const Links& lk, bool eo, double kappa,
     return LGT_OK;
 }
 
+// The even-odd Wilson true residual res = b - A x (A = Dhat^+ Dhat) with the four hops
+// in double-float arithmetic on the double-float links Udf (built from lk.U); x, b and
+// res are FP64, |res|^2 -> slot 0.  The intermediate vectors stay in double-float:
+// x_e and X_o = kappa H_oe x_e in Xdf, eta_e = x_e - kappa H_eo X_o (= Dhat x_e) and
+// Y_o = kappa (H^+)_oe eta_e in Ydf -- the force vectors X, Y of the solution.
+static int true_residual_df(lgt_lattice* L, const Links& lk, double kappa, const double2* b, const double2* x,
+                            double2* res) {
+    if (L->udf_src != lk.U) {
+        CK(links_to_df(L->Udf, lk.U, L->g, L->st));
+        L->udf_src = lk.U;
+    }
+    const long hf = 12L * L->g.Vh;
+    float4* xe = L->Xdf;
+    float4* Xo = L->Xdf + hf;
+    float4* Ye = L->Ydf;
+    float4* Yo = L->Ydf + hf;
+    CK(complex_to_df(xe, x, hf, L->st));
+    HopArgs A;
+    memset(&A, 0, sizeof A);
+    A.U = L->Udf;
+    A.g = L->g;
+    A.parity = 1; A.in[0] = xe; A.out[1] = Xo; A.a = kappa;
+    CK(timed_hop_df(A, false, EPI_HOP, L->st));
+    A.parity = 0; A.in[1] = Xo; A.out[0] = Ye; A.y[0] = xe; A.a = -kappa;
+    CK(timed_hop_df(A, false, EPI_XPAY, L->st));
+    A.parity = 1; A.in[0] = Ye; A.out[1] = Yo; A.y[1] = nullptr; A.a = kappa;
+    CK(timed_hop_df(A, true, EPI_HOP, L->st));
+    HopArgs R = hop_base(L, lk, true);
+    R.U = L->Udf;
+    R.parity = 0; R.in[1] = Yo; R.y[0] = Ye; R.a = -kappa; R.out[0] = res; R.pv[0] = b;
+    R.red_op = RED_STORE; R.red_slot = 0;
+    CK(timed_hop_df(R, true, EPI_RESID, L->st));
+    return LGT_OK;
+}
+
+// The captured force vectors in FP64 (X_o, eta_e, Y_o converted from their
+// double-float copies; X_e is the FP64 solution itself) for consumers of FP64 X, Y.
+static int cap_to_fp64(lgt_lattice* L) {
+    if (L->cap_valid || !L->cap_df_valid) return LGT_OK;
+    const long hf = 12L * L->g.Vh;
+    CK(complex_from_df((double2*)half(L->X, L, true, 1), L->Xdf + hf, hf, L->st));
+    CK(complex_from_df(L->Y, L->Ydf, 2 * hf, L->st));
+    L->cap_valid = true;
+    return LGT_OK;
+}
+
 // Chronological initial guess for Dhat^+Dhat x = b on even sites (kappa): with the
 // last N kept solutions v_i, x = sum c_i v_i with (V^+ A V) c = V^+ b.  The products
 // A v_i use the FP32 operator on all of them at once (a guess needs no more).  The
@@ -1055,9 +1153,23 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     if (!(sp->tol > 0) || sp->max_iter <= 0) return fail(LGT_EINVAL, "tol and max_iter must be positive");
     TRY(ensure_solver(L));
     L->cap_valid = false;
+    L->cap_df_valid = false;
+    L->udf_src = nullptr;   // the links may have changed since the last solve
     const int n = eo ? L->g.Vh : 2 * L->g.Vh;
     const int K = sp->check_every > 0 ? sp->check_every : 16;
     const bool mixed = sp->precision == LGT_MIXED;
+    // the mixed even-odd Wilson solver forms its true residuals in double-float
+    const bool dfres = mixed && eo && !lk.C64;
+    if (dfres) TRY(ensure_df(L));
+    auto residual = [&](double2* res) -> int {
+        return dfres ? true_residual_df(L, lk, kappa, b, x, res) : true_residual(L, lk, eo, kappa, b, x, res);
+    };
+    // the vectors of the last residual are the force vectors of x (when x is cap_X)
+    auto captured = [&]() {
+        const bool cap = L->cap_X && L->cap_Y && (const double2*)x == L->cap_X;
+        L->cap_valid = cap && !dfres;
+        L->cap_df_valid = cap && dfres;
+    };
     const size_t b64 = (size_t)n * 12 * sizeof(double2), b32 = (size_t)n * 6 * sizeof(float4);
     lgt_solve_stats st = {};
 
@@ -1082,7 +1194,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     }
     double rr0 = bb;
     if (guess) {
-        TRY(true_residual(L, lk, eo, kappa, b, x, L->r));
+        TRY(residual(L->r));
         TRY(sync_scalars(L));
         rr0 = hs->slot[0];
         st.reliable_updates += 1;
@@ -1153,7 +1265,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
         return LGT_OK;
     };
     if (guess && rr0 <= target) {   // the guess already solves the system
-        L->cap_valid = L->cap_X && L->cap_Y && (const double2*)x == L->cap_X;
+        captured();
         if (record) TRY(chrono_record(L, x, kappa, hs->iters));
     }
     for (; !(guess && rr0 <= target);) {
@@ -1209,7 +1321,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
                 CK(blas_add_f2d(x, L->x32, n, L->g.Vh, L->st));
                 CK(cudaMemsetAsync(L->x32, 0, b32, L->st));
             }
-            TRY(true_residual(L, lk, eo, kappa, b, x, L->r));
+            TRY(residual(L->r));
             TRY(sync_scalars(L));
             rr_true = hs->slot[0];
             st.reliable_updates += 1;
@@ -1219,7 +1331,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
                 break;
             }
             if (rr_true <= target) {
-                L->cap_valid = L->cap_X && L->cap_Y && (const double2*)x == L->cap_X;
+                captured();
                 if (record) TRY(chrono_record(L, x, kappa, hs->iters));
                 break;
             }
@@ -1360,6 +1472,10 @@ static int cg_multi(lgt_lattice* L, int nrhs, const double2* const* b, double2* 
     const int K = sp->check_every > 0 ? sp->check_every : 16;
     const size_t b64 = (size_t)n * 12 * sizeof(double2), b32 = (size_t)n * 6 * sizeof(float4);
     L->cap_valid = false;
+    L->cap_df_valid = false;
+    // true residuals in double-float, as the single-system mixed solver forms them
+    TRY(ensure_df(L));
+    L->udf_src = nullptr;
     for (int k = 0; k < nrhs; ++k) CK(blas_norm2(b[k], n, L->g.Vh, true, red(L), k, L->st));
     TRY(sync_scalars(L));
     double bb[KMAX_RHS], rr_true[KMAX_RHS];
@@ -1416,7 +1532,7 @@ static int cg_multi(lgt_lattice* L, int nrhs, const double2* const* b, double2* 
             if (!(h.done || hit_cap)) continue;
             CK(blas_add_f2d(x[k], W.x32[k], n, L->g.Vh, L->st));
             CK(cudaMemsetAsync(W.x32[k], 0, b32, L->st));
-            TRY(true_residual(L, L->thin, true, kappa[k], b[k], x[k], W.r64[k]));
+            TRY(true_residual_df(L, L->thin, kappa[k], b[k], x[k], W.r64[k]));
             TRY(sync_scalars(L));
             rr_true[k] = L->hs->slot[0];
             rel[k] += 1;
@@ -1544,6 +1660,7 @@ static int pf_action_on(lgt_lattice* L, const Links& lk, const lgt_action_params
     const int rc = cg_core(L, lk, phi, L->X, ap->kappa, eo, sp, stats);
     L->cap_X = L->cap_Y = nullptr;
     TRY(rc);
+    TRY(cap_to_fp64(L));
     // eta = M chi: left in Y by the solver's final residual, else computed here
     if (!L->cap_valid) {
         if (eo) TRY(dhat(L, lk, true, false, L->X, L->Y, L->t, ap->kappa));
@@ -1592,7 +1709,7 @@ extern "C" int lgt_kinetic_energy(lgt_lattice_t L, const double* mom, double* K)
 // Solve and build X, Y of the fermion force on links lk (FP64 X, Y; with fp32 the
 // vectors are built in FP32 from the FP64 solution: X32, Y32).
 static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_params* ap, const double2* phi,
-                         const lgt_solver_params* sp, lgt_solve_stats* stats, bool fp32) {
+                         const lgt_solver_params* sp, lgt_solve_stats* stats, bool fp32, bool dfa) {
     const bool eo = ap->even_odd != 0;
     L->cap_X = L->X;
     L->cap_Y = L->Y;
@@ -1625,7 +1742,11 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
         }
         return LGT_OK;
     }
-    if (L->cap_valid) return LGT_OK;   // built by the solver's final FP64 residual
+    // built by the solver's final residual: in double-float (read as such by the
+    // double-float force) or in FP64
+    if (L->cap_df_valid && dfa) return LGT_OK;
+    TRY(cap_to_fp64(L));
+    if (L->cap_valid) return LGT_OK;
     if (eo) {
         double2* Xo = (double2*)half(L->X, L, true, 1);
         double2* Yo = (double2*)half(L->Y, L, true, 1);
@@ -1652,15 +1773,24 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
     const int arith = (form == 0 && sp && sp->precision == LGT_MIXED) ? ap->force_arith : LGT_ARITH_FP64;
     const bool fp32 = arith == LGT_ARITH_FP32, dfa = arith == LGT_ARITH_DF64;
     if (dfa) TRY(ensure_df(L));
+    L->udf_src = nullptr;
+    // the double-float copy of links U in Udf (the solve may have made it already)
+    auto udf_of = [&](const double2* U) -> int {
+        if (L->udf_src != U) {
+            CK(links_to_df(L->Udf, U, L->g, L->st));
+            L->udf_src = U;
+        }
+        return LGT_OK;
+    };
     if (ap->fermions) {
         if (!phi) return fail(LGT_EINVAL, "null phi");
         TRY(ensure_solver(L));
-        TRY(force_vectors(L, ferm_lk, ap, phi, sp, stats, fp32));
+        TRY(force_vectors(L, ferm_lk, ap, phi, sp, stats, fp32, dfa));
     }
     if (ap->beta != 0.0) {
         if (fp32) CK(gauge_force_fp32(gauge_lk.U12, L->g, ap->beta, ap->c1, coef, keep, out, L->st));
         else if (dfa && ap->c1 == 0.0) {
-            CK(links_to_df(L->Udf, gauge_lk.U, L->g, L->st));
+            TRY(udf_of(gauge_lk.U));
             CK(gauge_force_df(L->Udf, L->g, ap->beta, coef, keep, out, L->st));
         } else CK(gauge_force(gauge_lk.U, L->g, ap->beta, ap->c1, coef, keep, form, out, L->st));
         keep = 1;
@@ -1668,10 +1798,11 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
     if (ap->fermions) {
         if (fp32) CK(fermion_force_fp32(ferm_lk.U12, L->X32, L->Y32, L->g, ap->kappa, coef, keep, out, L->st));
         else if (dfa) {
-            if (ap->beta == 0.0 || ap->c1 != 0.0 || ferm_lk.U != gauge_lk.U)
-                CK(links_to_df(L->Udf, ferm_lk.U, L->g, L->st));
-            CK(spinor_to_df(L->Xdf, L->X, L->g, L->st));
-            CK(spinor_to_df(L->Ydf, L->Y, L->g, L->st));
+            TRY(udf_of(ferm_lk.U));
+            if (!L->cap_df_valid) {   // the vectors are in FP64: their double-float copies
+                CK(spinor_to_df(L->Xdf, L->X, L->g, L->st));
+                CK(spinor_to_df(L->Ydf, L->Y, L->g, L->st));
+            }
             CK(fermion_force_df(L->Udf, L->Xdf, L->Ydf, L->g, ap->kappa, coef, keep, out, L->st));
         } else CK(fermion_force(ferm_lk.U, L->X, L->Y, L->g, ap->kappa, coef, keep, form, out, L->st));
         keep = 1;

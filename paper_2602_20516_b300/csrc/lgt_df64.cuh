@@ -52,6 +52,7 @@ __device__ __forceinline__ dfc operator+(const dfc& a, const dfc& b) { return {d
 __device__ __forceinline__ dfc operator-(const dfc& a, const dfc& b) { return {df_sub(a.r, b.r), df_sub(a.i, b.i)}; }
 __device__ __forceinline__ dfc operator-(const dfc& a) { return {df_neg(a.r), df_neg(a.i)}; }
 __device__ __forceinline__ dfc times_i(const dfc& a) { return {df_neg(a.i), a.r}; }
+__device__ __forceinline__ dfc times_mi(const dfc& a) { return {a.i, df_neg(a.r)}; }
 
 // compensated accumulator: value s + c
 struct dacc {
@@ -166,6 +167,26 @@ __device__ __forceinline__ void store_link_df(float4* __restrict__ U, int Vh, in
     for (int k = 0; k < 9; ++k) {
         const df r = df_from(m.e[k / 3][k % 3].r), im = df_from(m.e[k / 3][k % 3].i);
         b[(size_t)k * Vh] = make_float4(r.h, r.l, im.h, im.l);
+    }
+}
+
+// double-float spinor half field: float4 [12][Vh], entry k = 3 spin + colour =
+// (re.hi, re.lo, im.hi, im.lo)
+struct SpinorDF { dfc c[4][3]; };
+__device__ __forceinline__ SpinorDF load_spinor_df(const float4* __restrict__ f, int Vh, int i) {
+    SpinorDF s;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const float4 v = __ldg(f + (size_t)k * Vh + i);
+        s.c[k / 3][k % 3] = {{v.x, v.y}, {v.z, v.w}};
+    }
+    return s;
+}
+__device__ __forceinline__ void store_spinor_df(float4* __restrict__ f, int Vh, int i, const SpinorDF& s) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const dfc& v = s.c[k / 3][k % 3];
+        f[(size_t)k * Vh + i] = make_float4(v.r.h, v.r.l, v.i.h, v.i.l);
     }
 }
 

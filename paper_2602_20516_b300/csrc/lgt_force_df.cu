@@ -92,17 +92,6 @@ cudaError_t gauge_force_df(const float4* Udf, const Geom& g, double beta, double
 }
 
 // ---------------------------------------------------------------- fermion force
-struct SpinorDF { dfc c[4][3]; };
-__device__ __forceinline__ SpinorDF load_spinor_df(const float4* __restrict__ f, int Vh, int i) {
-    SpinorDF s;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const float4 v = __ldg(f + (size_t)k * Vh + i);
-        s.c[k / 3][k % 3] = {{v.x, v.y}, {v.z, v.w}};
-    }
-    return s;
-}
-
 // W = U P1 - P2 U^+ from the projected rows (as w_matrix of lgt_force.cu):
 //   U P1 = sum_j (U h_j(X(x+mu))) k_j(Y(x))^+,  P2 U^+ = sum_j h_j(X(x)) (U k_j(Y(x+mu)))^+
 template <int MU>

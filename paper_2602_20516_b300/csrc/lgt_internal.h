@@ -212,6 +212,13 @@ cudaError_t chrono_combine(double2* x, const double2* const* v, const double2* c
 // ---------------------------------------------------------------- double-float forces (lgt_force_df.cu)
 // FP64 links / full spinor field -> double-float copies (float4 per complex entry)
 cudaError_t links_to_df(float4* Udf, const double2* U, const Geom& g, cudaStream_t st);
+// Wilson hop in double-float arithmetic (lgt_dirac_df.cu): U double-float links, in / y
+// double-float half fields; epilogues EPI_HOP, EPI_XPAY (double-float out) and
+// EPI_RESID (pv and out FP64, |out|^2 reduced like the FP64 hop's)
+cudaError_t launch_hop_df(const HopArgs& A, bool dagger, int epi, cudaStream_t st);
+// ne complex entries FP64 <-> double-float
+cudaError_t complex_to_df(float4* y, const double2* x, long ne, cudaStream_t st);
+cudaError_t complex_from_df(double2* y, const float4* x, long ne, cudaStream_t st);
 cudaError_t spinor_to_df(float4* y, const double2* x, const Geom& g, cudaStream_t st);
 // Lie form, out = keep*out + coef*F, double-float arithmetic, FP64 accumulation
 cudaError_t gauge_force_df(const float4* Udf, const Geom& g, double beta, double coef, int keep, double2* out,

@@ -29,9 +29,10 @@ __device__ __forceinline__ void project(const C (&psi)[4][3], C (&h)[2][3]) {
     }
 }
 
-// out += (1 + S g_MU) reconstructed from the multiplied half spinor uh
-template <int MU, int S, typename R>
-__device__ __forceinline__ void accumulate(cx<R> (&out)[4][3], const cx<R> (&uh)[2][3]) {
+// out += (1 + S g_MU) reconstructed from the multiplied half spinor uh (C as in project,
+// with times_mi as well)
+template <int MU, int S, typename C>
+__device__ __forceinline__ void accumulate(C (&out)[4][3], const C (&uh)[2][3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         out[0][c] = out[0][c] + uh[0][c];

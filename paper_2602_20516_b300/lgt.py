@@ -15,7 +15,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblgt.so")
 
-FP64, MIXED, FP32 = 0, 1, 2
+FP64, MIXED, FP32, DF64 = 0, 1, 2, 3
 EVEN, ODD, FULL = 0, 1, 2
 OP_HOP, OP_D, OP_DHAT, OP_DHAT_NORMAL = 0, 1, 2, 3
 LEAPFROG, OMELYAN2MN = 0, 1
@@ -227,7 +227,8 @@ def kernel_timing_start(max_launches=65536):
 
 
 HOP_EPILOGUES = ["hop", "xpay", "xpay_norm", "cg_update", "residual"]
-TIMING_KINDS = 10   # LGT_TIMING_KINDS
+TIMING_KINDS = 15   # LGT_TIMING_KINDS
+TIMING_ARITH = ["fp32", "fp64", "df64"]
 
 
 def kernel_timing_stop(min_ms=0.0):
@@ -240,7 +241,7 @@ def kernel_timing_stop(min_ms=0.0):
     out = {}
     for k in range(TIMING_KINDS):
         if n[k]:
-            out[("fp64" if k >= 5 else "fp32", HOP_EPILOGUES[k % 5])] = (ms[k], n[k])
+            out[(TIMING_ARITH[k // 5], HOP_EPILOGUES[k % 5])] = (ms[k], n[k])
     return out, short.value
 
 
@@ -307,6 +308,8 @@ class Lattice:
     def spinor_field(self, parity=FULL, precision=FP64):
         if precision == FP32:
             return self._t((6, self.Vh, 4) if parity != FULL else (2, 6, self.Vh, 4), torch.float32)
+        if precision == DF64:   # (re.hi, re.lo, im.hi, im.lo) per component
+            return self._t((12, self.Vh, 4) if parity != FULL else (2, 12, self.Vh, 4), torch.float32)
         return self._t((12, self.Vh, 2) if parity != FULL else (2, 12, self.Vh, 2))
 
     def momentum_field(self):
