@@ -43,11 +43,13 @@ sys.path.insert(0, ROOT)
 METRIC = "force evals/s + Dslash HBM GB/s at 32^3×64, mixed vs FP64; p99 solve latency"
 UNIT = "force evals/s"
 DIMS = (32, 32, 32, 64)
-# DELTA: reliable-update threshold of the mixed CG (|r| < DELTA max|r| triggers an FP64
-# residual replacement).  Measured on the seeded start: 146 inner iterations for every
-# DELTA from 1e-3 to 3e-5 with 4 -> 3 FP64 updates; 3e-6 needs 147 iterations and 2
-# updates (the fastest); 1e-6 needs 158
-BETA, KAPPA, ALPHA, TOL, DELTA = 5.8, 0.156, 0.5, 1e-10, 3e-6
+# DELTA: reliable-update threshold of the mixed CG (|r| < DELTA max|r| triggers a
+# residual replacement, formed in double-float).  Measured on the four fields of the
+# workload (iterations on the fields at MD steps 0, 10, 20, 30): DELTA 1e-2 .. 1e-3 needs
+# 146 / 111 / 593 / 188 iterations with 4-6 updates each, as many as FP64 CG; 3e-6 needs
+# 147 / 111 / 738 / 189 with 2-3 (the nearly singular step-20 field loses 25 %), 1e-6
+# 158 / 117 / 950 / 201.  The step takes 657 ms at 3e-3 against 717 ms at 3e-6.
+BETA, KAPPA, ALPHA, TOL, DELTA = 5.8, 0.156, 0.5, 1e-10, 3e-3
 # force arithmetic of the mixed path: double-float (FP32 pairs, ~48 bits) accumulated
 # in FP64; FP64 and FP32 force arithmetic are timed beside it
 FORCE_ARITH = "df64"
