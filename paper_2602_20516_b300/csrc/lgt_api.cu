@@ -115,6 +115,10 @@ struct Links {
     const double2* I64 = nullptr;
     const float4* I32 = nullptr;
     double logdet_odd = 0.0;
+    // Hermitian-packed double-float copies of 1 + A (even sites) and of its inverse (odd
+    // sites) for the mixed solver's double-float true residuals (null: FP64 residuals)
+    const float4* Cdf = nullptr;
+    const float4* Idf = nullptr;
 };
 
 struct lgt_lattice {
@@ -151,6 +155,8 @@ struct lgt_lattice {
     // force/action call (fermion_links), full spinor temporaries for (1 + A) y, and
     // the insertion field of the clover force
     double2 *thin_c64, *call_c64, *cins;
+    float4* cins_df;   // double-float copy of the insertion field (double-float force arithmetic)
+    float4 *call_cdf, *call_idf;   // packed double-float clover blocks (float4 [parity][36][Vh])
     float4 *thin_c32, *call_c32;
     // (1 + A)^{-1} on odd sites for the even-odd form, of the thin and of the call links
     double2 *thin_i64, *call_i64;
@@ -271,7 +277,7 @@ static int ensure_multi(lgt_lattice* L) {
 }
 
 static int ensure_clover(lgt_lattice* L, bool thin) {
-    const size_t c64 = (size_t)2 * 72 * L->g.Vh * sizeof(double2), c32 = (size_t)2 * 36 * L->g.Vh * sizeof(float4);
+    const size_t c64 = (size_t)2 * 72 * L->g.Vh * sizeof(double2), c32 = (size_t)2 * 18 * L->g.Vh * sizeof(float4);
     if (thin && !L->thin_c64) {
         TRY(A(L, c64, &L->thin_c64)); TRY(A(L, c32, &L->thin_c32));
         TRY(A(L, c64, &L->thin_i64)); TRY(A(L, c32, &L->thin_i32));
@@ -281,6 +287,7 @@ static int ensure_clover(lgt_lattice* L, bool thin) {
         TRY(A(L, c32, &L->call_c32));
         TRY(A(L, c64, &L->call_i64)); TRY(A(L, c32, &L->call_i32));
         TRY(A(L, (size_t)2 * 54 * L->g.Vh * sizeof(double2), &L->cins));
+        TRY(A(L, (size_t)2 * 54 * L->g.Vh * sizeof(float4), &L->cins_df));
     }
     if (!L->ct64) { TRY(A(L, spinor64_full(L), &L->ct64)); TRY(A(L, spinor32_full(L), &L->ct32)); }
     return LGT_OK;
@@ -882,6 +889,34 @@ extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, in
 // return at once after the stop flag is raised on the device.
 static int cg_iteration(lgt_lattice* L, const Links& lk, bool fp64, bool eo, double kappa, void* x, void* r, void* p,
                         void* u, void* t) {
+    if (eo && lk.C64 && !fp64) {
+        // FP32 even-odd clover (Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe) with the
+        // site-local blocks fused into the hops: the odd hops store M_oo^{-1} H_oe in,
+        // the even hops form M_ee y in their epilogue; the kernel sequence, deferred
+        // <p, A p> reduction and sweep order of the Wilson iteration below
+        auto dir = [&]() { return L->alternate ? (L->sweep ^= 1) : 0; };
+        HopArgs A = hop_base(L, lk, false);
+        A.skip = 1;
+        A.parity = 1; A.in[0] = p; A.out[1] = t; A.clov = lk.I32; A.reverse = dir();
+        CK(timed_hop(A, false, false, EPI_HOP, L->st));
+        A = hop_base(L, lk, false);
+        A.skip = 1;
+        A.parity = 0; A.in[1] = t; A.out[0] = u; A.y[0] = p; A.clov = lk.C32; A.a = -kappa * kappa;
+        A.red_op = RED_PAP; A.reverse = dir(); A.defer = 1;
+        CK(timed_hop(A, false, false, EPI_XPAY_NORM, L->st));
+        A = hop_base(L, lk, false);
+        A.skip = 1;
+        A.parity = 1; A.in[0] = u; A.out[1] = t; A.clov = lk.I32; A.reverse = dir();
+        A.fin_n = hop_grid(L->g, 0); A.fin_op = RED_PAP;
+        CK(timed_hop(A, false, true, EPI_HOP, L->st));
+        A = hop_base(L, lk, false);
+        A.skip = 1;
+        A.parity = 0; A.in[1] = t; A.y[0] = u; A.clov = lk.C32; A.a = -kappa * kappa; A.red_op = RED_RR;
+        A.r[0] = r; A.reverse = dir();
+        CK(timed_hop(A, false, true, EPI_CG, L->st));
+        CK(blas_cg_p_update(p, r, x, L->g.Vh, L->g.Vh, false, red(L), L->st, dir() != 0));
+        return LGT_OK;
+    }
     if (eo && lk.C64) {
         // with the clover term (Dhat = M_ee - kappa^2 H_eo M_oo^{-1} H_oe): the odd
         // intermediate goes through M_oo^{-1}, and M_ee p / M_ee u enter the xpay hops
@@ -1049,19 +1084,22 @@ static int true_residual_df(lgt_lattice* L, const Links& lk, double kappa, const
     float4* Ye = L->Ydf;
     float4* Yo = L->Ydf + hf;
     CK(complex_to_df(xe, x, hf, L->st));
+    // with the clover term: X_o = kappa M_oo^{-1} H_oe x_e, eta_e = M_ee x_e - kappa H_eo X_o,
+    // Y_o = kappa M_oo^{-1} (H^+)_oe eta_e, A x = M_ee eta_e - kappa (H^+)_eo Y_o (the
+    // blocks applied inside the hops)
     HopArgs A;
     memset(&A, 0, sizeof A);
     A.U = L->Udf;
     A.g = L->g;
-    A.parity = 1; A.in[0] = xe; A.out[1] = Xo; A.a = kappa;
+    A.parity = 1; A.in[0] = xe; A.out[1] = Xo; A.a = kappa; A.clov = lk.Idf;
     CK(timed_hop_df(A, false, EPI_HOP, L->st));
-    A.parity = 0; A.in[1] = Xo; A.out[0] = Ye; A.y[0] = xe; A.a = -kappa;
+    A.parity = 0; A.in[1] = Xo; A.out[0] = Ye; A.y[0] = xe; A.a = -kappa; A.clov = lk.Cdf;
     CK(timed_hop_df(A, false, EPI_XPAY, L->st));
-    A.parity = 1; A.in[0] = Ye; A.out[1] = Yo; A.y[1] = nullptr; A.a = kappa;
+    A.parity = 1; A.in[0] = Ye; A.out[1] = Yo; A.y[1] = nullptr; A.a = kappa; A.clov = lk.Idf;
     CK(timed_hop_df(A, true, EPI_HOP, L->st));
     HopArgs R = hop_base(L, lk, true);
     R.U = L->Udf;
-    R.parity = 0; R.in[1] = Yo; R.y[0] = Ye; R.a = -kappa; R.out[0] = res; R.pv[0] = b;
+    R.parity = 0; R.in[1] = Yo; R.y[0] = Ye; R.a = -kappa; R.out[0] = res; R.pv[0] = b; R.clov = lk.Cdf;
     R.red_op = RED_STORE; R.red_slot = 0;
     CK(timed_hop_df(R, true, EPI_RESID, L->st));
     return LGT_OK;
@@ -1159,7 +1197,7 @@ static int cg_core(lgt_lattice* L, const Links& lk, const double2* b, double2* x
     const int K = sp->check_every > 0 ? sp->check_every : 16;
     const bool mixed = sp->precision == LGT_MIXED;
     // the mixed even-odd Wilson solver forms its true residuals in double-float
-    const bool dfres = mixed && eo && !lk.C64;
+    const bool dfres = mixed && eo && (!lk.C64 || (lk.Cdf && lk.Idf));
     if (dfres) TRY(ensure_df(L));
     auto residual = [&](double2* res) -> int {
         return dfres ? true_residual_df(L, lk, kappa, b, x, res) : true_residual(L, lk, eo, kappa, b, x, res);
@@ -1626,7 +1664,12 @@ static int smear_to(lgt_lattice* L, const StoutPlan& P, double rho, double2** le
 }
 // links seen by the Dirac operator: thin, or the top stout level (+ its FP32 copy)
 // (+ the clover term of ap->csw built from them; lgt_set_clover's field is not used here)
-static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out) {
+// With a mixed solver and double-float force arithmetic (sp given) the clover field is
+// built in double-float arithmetic as well (the FP64 field-strength products are FP64
+// bound); the FP64 path and the actions build it in FP64.  With a mixed solver and the
+// even-odd form, double-float copies of the blocks serve the solver's true residuals.
+static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out,
+                         const lgt_solver_params* sp = nullptr) {
     Links lk{L->thin.U, L->thin.U12};
     if (ap->n_stout > 0) {
         TRY(ensure_stout(L, ap->n_stout, ap->stout_recompute));
@@ -1637,10 +1680,27 @@ static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out
     }
     if (ap->fermions && ap->csw != 0.0) {
         TRY(ensure_clover(L, false));
-        CK(clover_field(lk.U, L->g, clover_sigma(), ap->kappa, ap->csw, L->call_c64, L->call_c32, L->st));
+        if (sp && sp->precision == LGT_MIXED && ap->force_arith == LGT_ARITH_DF64) {
+            TRY(ensure_df(L));
+            CK(links_to_df(L->Udf, lk.U, L->g, L->st));
+            L->udf_src = nullptr;   // the solve rebuilds (or keeps) its own copy
+            CK(clover_field_df(L->Udf, L->g, clover_sigma(), ap->kappa, ap->csw, L->call_c64, L->call_c32, L->st));
+        } else {
+            CK(clover_field(lk.U, L->g, clover_sigma(), ap->kappa, ap->csw, L->call_c64, L->call_c32, L->st));
+        }
         lk.C64 = L->call_c64;
         lk.C32 = L->call_c32;
         if (ap->even_odd) TRY(clover_inverse_odd(L, &lk, L->call_i64, L->call_i32));
+        if (ap->even_odd && sp && sp->precision == LGT_MIXED) {
+            if (!L->call_cdf) {
+                TRY(A(L, (size_t)2 * 36 * L->g.Vh * sizeof(float4), &L->call_cdf));
+                TRY(A(L, (size_t)2 * 36 * L->g.Vh * sizeof(float4), &L->call_idf));
+            }
+            CK(clover_pack_df(lk.C64, L->g, 0, L->call_cdf, L->st));
+            CK(clover_pack_df(lk.I64, L->g, 1, L->call_idf, L->st));
+            lk.Cdf = L->call_cdf;
+            lk.Idf = L->call_idf;
+        }
     }
     *out = lk;
     return LGT_OK;
@@ -1719,6 +1779,7 @@ static int force_vectors(lgt_lattice* L, const Links& lk, const lgt_action_param
     if (eo && lk.C64) {
         // the FP64 vectors (from the solver's final residual, else computed here); the
         // FP32 force arithmetic takes their FP32 copies
+        TRY(cap_to_fp64(L));
         if (!L->cap_valid)
             TRY(eo_clover_xy(L, lk, ap->kappa, L->X, (double2*)half(L->X, L, true, 1), L->Y,
                              (double2*)half(L->Y, L, true, 1)));
@@ -1814,7 +1875,10 @@ static int force_on(lgt_lattice* L, const Links& gauge_lk, const Links& ferm_lk,
                 CK(clover_det_insertion(ferm_lk.I64, L->g, 1, clover_sigma(), ap->kappa, ap->csw, L->cins, L->st));
             // double-float force arithmetic: the gather from the double-float links the
             // fermion force just used (Udf holds ferm_lk.U)
-            if (dfa) CK(clover_force_df(L->Udf, L->cins, L->g, coef, 1, out, L->st));
+            if (dfa) {
+                CK(complex_to_df(L->cins_df, L->cins, 2L * 54 * L->g.Vh, L->st));
+                CK(clover_force_df(L->Udf, L->cins_df, L->g, coef, 1, out, L->st));
+            }
             else CK(clover_force(ferm_lk.U, L->cins, L->g, coef, 1, form, out, L->st));
         }
     }
@@ -1941,7 +2005,7 @@ extern "C" int lgt_force(lgt_lattice_t L, const lgt_action_params* ap, const dou
     if (stats) *stats = lgt_solve_stats{};
     if (ap->n_stout == 0) {
         Links fl;
-        TRY(fermion_links(L, ap, &fl));
+        TRY(fermion_links(L, ap, &fl, form == LGT_FORCE_LIE ? sp : nullptr));
         TRY(force_on(L, gauge_links(L), fl, ap, (const double2*)phi, sp, 1.0, 0, form, (double2*)F_out, stats));
     } else {
         TRY(ensure_solver(L));
@@ -1960,7 +2024,7 @@ static int kick(lgt_lattice* L, double2* mom, double eps, const lgt_action_param
     // the gauge action always sees thin links: only a fermion part goes through smearing
     if (ap->n_stout == 0 || !ap->fermions) {
         Links fl;
-        TRY(fermion_links(L, ap, &fl));
+        TRY(fermion_links(L, ap, &fl, sp));
         return force_on(L, gauge_links(L), fl, ap, phi, sp, -eps, 1, 0, mom, stats);
     }
     TRY(ensure_md(L));

@@ -18,6 +18,7 @@
 // relative to mu -> nu (mu < nu).
 #include "lgt_df64.cuh"
 #include "lgt_internal.h"
+#include "lgt_clover.cuh"
 #include "lgt_su3.cuh"
 
 namespace lgt {
@@ -62,7 +63,7 @@ __constant__ int PLANE_MU[6] = {0, 0, 0, 1, 1, 2};
 __constant__ int PLANE_NU[6] = {1, 2, 3, 2, 3, 3};
 
 // 1 + A as double2 [parity][72][Vh] (entry 36 c + 6 i + j of chiral block c) and the
-// FP32 copy float4 [parity][36][Vh] (entries 2k, 2k+1)
+// Hermitian-packed FP32 copy float4 [parity][18][Vh] (lgt_clover.cuh)
 __global__ void __launch_bounds__(NT) clover_field_kernel(const double2* U, Geom g, CloverSigma S, double coef,
                                                           double2* C64, float4* C32) {
     const int t = blockIdx.x * NT + threadIdx.x;
@@ -88,21 +89,98 @@ __global__ void __launch_bounds__(NT) clover_field_kernel(const double2* U, Geom
                 }
     }
     double2* o64 = C64 + (size_t)p * 72 * g.Vh + i;
-    float4* o32 = C32 + (size_t)p * 36 * g.Vh + i;
+    float4* o32 = C32 + (size_t)p * 18 * g.Vh + i;
     for (int k = 0; k < 72; ++k) {
         const dcx v = B[k / 36][(k % 36) / 6][k % 6];
         o64[(size_t)k * g.Vh] = make_double2(v.r, v.i);
     }
-    for (int k = 0; k < 36; ++k) {
-        const dcx v = B[(2 * k) / 36][((2 * k) % 36) / 6][(2 * k) % 6];
-        const dcx w = B[(2 * k + 1) / 36][((2 * k + 1) % 36) / 6][(2 * k + 1) % 6];
-        o32[(size_t)k * g.Vh] = make_float4((float)v.r, (float)v.i, (float)w.r, (float)w.i);
-    }
+    clover_store_f32(o32, g.Vh, 0, B[0]);
+    clover_store_f32(o32, g.Vh, 1, B[1]);
 }
 
 cudaError_t clover_field(const double2* U, const Geom& g, const CloverSigma& S, double kappa, double csw,
                          double2* C64, float4* C32, cudaStream_t st) {
     clover_field_kernel<<<grid_for(2L * g.Vh), NT, 0, st>>>(U, g, S, -kappa * csw, C64, C32);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// The same field from the double-float link copy: F_munu in double-float arithmetic
+// (the products of the leaves, ~94k FP32 instructions per site against ~8k FP64 FMAs,
+// which are FP64 bound on this part), then converted to FP64 for the sum with the
+// sigma coefficients as above.  Each leaf is the closed path of four steps from x (a
+// step +d takes U_d(z), a step -d takes U_d(z - d)^+); one loop body over planes,
+// leaves and steps keeps the code within the instruction cache.
+// steps of the four leaves in terms of (mu, nu): +1 = +mu, +2 = +nu, -1 = -mu, -2 = -nu
+__constant__ int LEAF_STEP[4][4] = {{1, 2, -1, -2}, {2, -1, -2, 1}, {-1, -2, 1, 2}, {-2, 1, 2, -1}};
+
+__global__ void __launch_bounds__(NT) clover_field_df_kernel(const float4* U, Geom g, CloverSigma S, double coef,
+                                                             double2* C64, float4* C32) {
+    const int t = blockIdx.x * NT + threadIdx.x;
+    if (t >= 2 * g.Vh) return;
+    const int p = t >= g.Vh, i = t - p * g.Vh;
+    int x[4];
+    eo_coords(g, p, i, x);
+    dcx B[2][6][6];
+    for (int c = 0; c < 2; ++c)
+        for (int r = 0; r < 6; ++r)
+            for (int q = 0; q < 6; ++q) B[c][r][q] = {r == q ? 1.0 : 0.0, 0.0};
+#pragma unroll 1
+    for (int pl = 0; pl < 6; ++pl) {
+        const int mu = PLANE_MU[pl], nu = PLANE_NU[pl];
+        dfmat Q = df_zero3();
+#pragma unroll 1
+        for (int lf = 0; lf < 4; ++lf) {
+            int z[4] = {x[0], x[1], x[2], x[3]};
+            dfmat P;
+#pragma unroll 1
+            for (int st = 0; st < 4; ++st) {
+                const int code = LEAF_STEP[lf][st];
+                const int d = (code == 1 || code == -1) ? mu : nu;
+                dfmat Lk;
+                if (code > 0) {
+                    Lk = link_df_op(U, g, z, d, false);
+                    shift(g, z, d, +1);
+                } else {
+                    shift(g, z, d, -1);
+                    Lk = link_df_op(U, g, z, d, true);
+                }
+                if (st == 0) P = Lk;
+                else P = df_mul<false, false>(P, Lk);
+            }
+            df_add_to(Q, P);
+        }
+        // F = (Q - Q^+) / (8 i), in FP64
+        dmat F;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                const double zr = df_to(Q.e[a][b].r) - df_to(Q.e[b][a].r);
+                const double zi = df_to(Q.e[a][b].i) + df_to(Q.e[b][a].i);
+                F.e[a][b] = {zi * 0.125, -zr * 0.125};
+            }
+        for (int c = 0; c < 2; ++c)
+            for (int s = 0; s < 2; ++s)
+                for (int u = 0; u < 2; ++u) {
+                    const double2 sg = S.s[pl][c][s][u];
+                    if (sg.x == 0.0 && sg.y == 0.0) continue;
+                    const dcx w = coef * dcx{sg.x, sg.y};
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) B[c][3 * s + a][3 * u + b] = cmad(B[c][3 * s + a][3 * u + b], w, F.e[a][b]);
+                }
+    }
+    double2* o64 = C64 + (size_t)p * 72 * g.Vh + i;
+    float4* o32 = C32 + (size_t)p * 18 * g.Vh + i;
+    for (int k = 0; k < 72; ++k) {
+        const dcx v = B[k / 36][(k % 36) / 6][k % 6];
+        o64[(size_t)k * g.Vh] = make_double2(v.r, v.i);
+    }
+    clover_store_f32(o32, g.Vh, 0, B[0]);
+    clover_store_f32(o32, g.Vh, 1, B[1]);
+}
+
+cudaError_t clover_field_df(const float4* Udf, const Geom& g, const CloverSigma& S, double kappa, double csw,
+                            double2* C64, float4* C32, cudaStream_t st) {
+    clover_field_df_kernel<<<grid_for(2L * g.Vh), NT, 0, st>>>(Udf, g, S, -kappa * csw, C64, C32);
     count_launch();
     return cudaGetLastError();
 }
@@ -152,17 +230,6 @@ template <> struct CloverBlock<double> {
         }
     }
 };
-template <> struct CloverBlock<float> {
-    static __device__ __forceinline__ void load(const void* C, int Vh, int i, int c, fcx (&M)[6][6]) {
-        const float4* b = (const float4*)C + (size_t)(18 * c) * Vh + i;
-#pragma unroll
-        for (int k = 0; k < 18; ++k) {   // float4 k holds entries 2k, 2k+1 of the block
-            const float4 z = __ldg(b + (size_t)k * Vh);
-            M[(2 * k) / 6][(2 * k) % 6] = {z.x, z.y};
-            M[(2 * k + 1) / 6][(2 * k + 1) % 6] = {z.z, z.w};
-        }
-    }
-};
 
 template <typename R>
 __global__ void __launch_bounds__(NT) clover_apply_kernel(const void* C, const void* in, void* out, Geom g,
@@ -176,16 +243,20 @@ __global__ void __launch_bounds__(NT) clover_apply_kernel(const void* C, const v
     // arithmetic in the field's precision (FP64 FMAs issue at 1/64 of the FP32 rate)
     cx<R> v[12], w[12];
     CloverIO<R>::load((const char*)in + fo, g.Vh, i, v);
+    if constexpr (sizeof(R) == 4) {
+        clover_mul_f32((const float4*)Cp, g.Vh, i, v, w);   // Hermitian-packed FP32 blocks
+    } else {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        cx<R> M[6][6];
-        CloverBlock<R>::load(Cp, g.Vh, i, c, M);
+        for (int c = 0; c < 2; ++c) {
+            cx<R> M[6][6];
+            CloverBlock<R>::load(Cp, g.Vh, i, c, M);
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
-            cx<R> s = {0, 0};
+            for (int r = 0; r < 6; ++r) {
+                cx<R> s = {0, 0};
 #pragma unroll
-            for (int q = 0; q < 6; ++q) s = cmad(s, M[r][q], v[6 * c + q]);
-            w[6 * c + r] = s;
+                for (int q = 0; q < 6; ++q) s = cmad(s, M[r][q], v[6 * c + q]);
+                w[6 * c + r] = s;
+            }
         }
     }
     CloverIO<R>::store((char*)out + fo, g.Vh, i, w);
@@ -198,7 +269,7 @@ cudaError_t clover_apply(const void* C, const void* in, void* out, const Geom& g
         clover_apply_kernel<double><<<grid_for(n), NT, 0, st>>>(C, in, out, g, parity, (size_t)72 * g.Vh * 16,
                                                                  (size_t)12 * g.Vh * 16);
     else
-        clover_apply_kernel<float><<<grid_for(n), NT, 0, st>>>(C, in, out, g, parity, (size_t)36 * g.Vh * 16,
+        clover_apply_kernel<float><<<grid_for(n), NT, 0, st>>>(C, in, out, g, parity, (size_t)18 * g.Vh * 16,
                                                                 (size_t)6 * g.Vh * 16);
     count_launch();
     return cudaGetLastError();
@@ -328,22 +399,31 @@ __global__ void __launch_bounds__(NT) clover_force_kernel(const double2* U, cons
 }
 
 // The same gather in double-float arithmetic (Lie form): links from their double-float
-// copy, the insertions split into double-float on load, products as in the gauge
-// force's double-float kernel; FP64 only in the final Lie components.
-__device__ __forceinline__ dfmat insertion_df_at(const double2* M, const Geom& g, const int x[4], int pl, double sgn) {
+// copy and the insertions from theirs (converted once per force evaluation: split on
+// load they cost ~1,300 FP64-pipe operations per link), products as in the gauge
+// force's double-float kernel, FP64 only in the final Lie components.
+//
+// The six plaquettes through U_m(y) run through one loop body.  Per plaquette the
+// three other links in path order are L1 = U_n(y1)^(+), L2 = U_m(y2)^+, L3 = U_n(y3)^(+)
+// (above: y1 = y+m, y2 = y3 + n... as written below; below: the mirror image, the
+// conjugations taken at load time) with the insertions M0..M3 at the corners y, y+m and
+// the two corners of the far side.  Its contribution, before the final ^+, is
+//   L1 L2 L3 M0 + M1 L1 L2 L3 + L1 M2 L2 L3 + L1 L2 M3 L3
+//     = M1 (L1 X) + L1 (L2 (M3 L3) + X M0 + M2 X),  X = L2 L3,
+// eight products of 3 x 3 double-float matrices.
+__device__ __forceinline__ dfmat insertion_dff_at(const float4* M, const Geom& g, const int x[4], int pl, bool neg) {
     const int lex = lex_of(g, x);
     const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
-    const double2* b = M + (size_t)par * 54 * g.Vh + (lex >> 1);
+    const float4* b = M + (size_t)par * 54 * g.Vh + (lex >> 1);
     dfmat m;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        const double2 z = __ldg(b + (size_t)(pl * 9 + k) * g.Vh);
-        m.e[k / 3][k % 3] = {df_from(sgn * z.x), df_from(sgn * z.y)};
+        const float4 z = __ldg(b + (size_t)(pl * 9 + k) * g.Vh);
+        m.e[k / 3][k % 3] = neg ? dfc{{-z.x, -z.y}, {-z.z, -z.w}} : dfc{{z.x, z.y}, {z.z, z.w}};
     }
     return m;
 }
-
-__global__ void __launch_bounds__(NT) clover_force_df_kernel(const float4* U, const double2* M, Geom g, double coef,
+__global__ void __launch_bounds__(NT) clover_force_df_kernel(const float4* U, const float4* M, Geom g, double coef,
                                                              int keep, double2* out) {
     int m, p, i;
     if (!link_index(g, m, p, i)) return;
@@ -353,44 +433,29 @@ __global__ void __launch_bounds__(NT) clover_force_df_kernel(const float4* U, co
     int ym[4] = {y[0], y[1], y[2], y[3]};
     shift(g, ym, m, +1);
 #pragma unroll 1
-    for (int n = 0; n < 4; ++n) {
-        if (n == m) continue;
+    for (int k = 0; k < 6; ++k) {
+        const int n = (k >> 1) + ((k >> 1) >= m);   // the three directions other than m
+        const bool below = k & 1;
         const int pl = plane_of(m, n);
-        const double s = m < n ? 1.0 : -1.0;
-        // above: A1 = U_n(y+m), A2 = U_m(y+n)^+, A3 = U_n(y)^+
-        {
-            int c2[4] = {ym[0], ym[1], ym[2], ym[3]};
-            shift(g, c2, n, +1);
-            int c3[4] = {y[0], y[1], y[2], y[3]};
-            shift(g, c3, n, +1);
-            const dfmat A1 = link_df_at(U, g, ym, n);
-            const dfmat Um = link_df_at(U, g, c3, m);
-            const dfmat Un = link_df_at(U, g, y, n);
-            const dfmat P12 = df_mul<false, true>(A1, Um);
-            const dfmat P23 = df_mul<true, true>(Um, Un);
-            const dfmat P123 = df_mul<false, true>(P12, Un);
-            df_mul_acc<false, false>(Gsum, P123, insertion_df_at(M, g, y, pl, s));
-            df_mul_acc<false, false>(Gsum, insertion_df_at(M, g, ym, pl, s), P123);
-            df_mul_acc<false, false>(Gsum, A1, df_mul<false, false>(insertion_df_at(M, g, c2, pl, s), P23));
-            df_mul_acc<false, true>(Gsum, df_mul<false, false>(P12, insertion_df_at(M, g, c3, pl, s)), Un);
-        }
-        // below: B1 = U_n(y+m-n)^+, B2 = U_m(y-n)^+, B3 = U_n(y-n)
-        {
-            int c2[4] = {ym[0], ym[1], ym[2], ym[3]};
-            shift(g, c2, n, -1);
-            int c3[4] = {y[0], y[1], y[2], y[3]};
-            shift(g, c3, n, -1);
-            const dfmat Un2 = link_df_at(U, g, c2, n);
-            const dfmat Um = link_df_at(U, g, c3, m);
-            const dfmat B3 = link_df_at(U, g, c3, n);
-            const dfmat P12 = df_mul<true, true>(Un2, Um);
-            const dfmat P23 = df_mul<true, false>(Um, B3);
-            const dfmat P123 = df_mul<false, false>(P12, B3);
-            df_mul_acc<false, false>(Gsum, P123, insertion_df_at(M, g, y, pl, -s));
-            df_mul_acc<false, false>(Gsum, insertion_df_at(M, g, ym, pl, -s), P123);
-            df_mul_acc<true, false>(Gsum, Un2, df_mul<false, false>(insertion_df_at(M, g, c2, pl, -s), P23));
-            df_mul_acc<false, false>(Gsum, df_mul<false, false>(P12, insertion_df_at(M, g, c3, pl, -s)), B3);
-        }
+        const bool neg = (m < n) == below;            // insertion sign: +s above, -s below
+        // far corners: c2 = y + m -/+ n, c3 = y -/+ n
+        int c2[4] = {ym[0], ym[1], ym[2], ym[3]};
+        shift(g, c2, n, below ? -1 : +1);
+        int c3[4] = {y[0], y[1], y[2], y[3]};
+        shift(g, c3, n, below ? -1 : +1);
+        // above: L1 = U_n(y+m), L3 = U_n(y)^+;  below: L1 = U_n(y+m-n)^+, L3 = U_n(y-n)
+        const dfmat L2 = link_df_op(U, g, c3, m, true);
+        const dfmat L3 = below ? link_df_op(U, g, c3, n, false) : link_df_op(U, g, y, n, true);
+        dfmat X, Y, T;
+        df_mul_rows(X, L2, L3, false);
+        df_mul_rows(T, insertion_dff_at(M, g, c3, pl, neg), L3, false);
+        df_mul_rows(Y, L2, T, false);
+        df_mul_rows(Y, X, insertion_dff_at(M, g, y, pl, neg), true);
+        df_mul_rows(Y, insertion_dff_at(M, g, c2, pl, neg), X, true);
+        const dfmat L1 = below ? link_df_op(U, g, c2, n, true) : link_df_op(U, g, ym, n, false);
+        df_mul_rows(T, L1, X, false);
+        df_mul_rows(Gsum, insertion_dff_at(M, g, ym, pl, neg), T, true);
+        df_mul_rows(Gsum, L1, Y, true);
     }
     const dfmat UG = df_mul<false, false>(load_link_df(U, g.Vh, p, m, i), Gsum);
     double c[8], f[8];
@@ -401,7 +466,7 @@ __global__ void __launch_bounds__(NT) clover_force_df_kernel(const float4* U, co
     store_mom(out, g.Vh, p, m, i, f);
 }
 
-cudaError_t clover_force_df(const float4* Udf, const double2* M, const Geom& g, double coef, int keep, double2* out,
+cudaError_t clover_force_df(const float4* Udf, const float4* M, const Geom& g, double coef, int keep, double2* out,
                             cudaStream_t st) {
     clover_force_df_kernel<<<grid_for(8L * g.Vh), NT, 0, st>>>(Udf, M, g, coef, keep, out);
     count_launch();
@@ -428,8 +493,7 @@ __global__ void __launch_bounds__(NT) clover_invert_kernel(const double2* C64, G
     if (i < g.Vh) {
         const double2* cb = C64 + (size_t)parity * 72 * g.Vh + i;
         double2* o64 = I64 + (size_t)parity * 72 * g.Vh + i;
-        float4* o32 = I32 + (size_t)parity * 36 * g.Vh + i;
-        dcx pending = {0, 0};   // FP32 float4 k holds entries 2k, 2k+1 (36 is even: no pair spans blocks)
+        float4* o32 = I32 + (size_t)parity * 18 * g.Vh + i;
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
             dcx L[6][6];
@@ -464,17 +528,16 @@ __global__ void __launch_bounds__(NT) clover_invert_kernel(const double2* C64, G
                     W[r][q] = (-1.0 / L[r][r].r) * s;
                 }
             }
-            // M^{-1} = W^+ W
+            // M^{-1} = W^+ W (the FP32 copy Hermitian-packed from it; L is reused to hold it)
             for (int r = 0; r < 6; ++r)
                 for (int q = 0; q < 6; ++q) {
                     dcx s = {0, 0};
                     for (int k = (r > q ? r : q); k < 6; ++k) s = cmadc(s, W[k][r], W[k][q]);
                     const int e = 36 * c + 6 * r + q;
                     o64[(size_t)e * g.Vh] = make_double2(s.r, s.i);
-                    if (e & 1) o32[(size_t)(e / 2) * g.Vh] = make_float4((float)pending.r, (float)pending.i,
-                                                                         (float)s.r, (float)s.i);
-                    else pending = s;
+                    L[r][q] = s;
                 }
+            clover_store_f32(o32, g.Vh, c, L);
         }
     }
     const double b = block_sum(logdet);

@@ -115,6 +115,22 @@ __device__ __forceinline__ dfmat df_mul(const dfmat& A, const dfmat& B) {
         }
     return C;
 }
+// C = A B and C += A B with the row loop kept as a loop: a third of the code of the
+// unrolled products, for kernels that chain many products per thread and would
+// otherwise outgrow the instruction cache
+__device__ __forceinline__ void df_mul_rows(dfmat& C, const dfmat& A, const dfmat& B, bool acc) {
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dacc re = acc ? dacc{C.e[i][j].r.h, C.e[i][j].r.l} : dacc0();
+            dacc im = acc ? dacc{C.e[i][j].i.h, C.e[i][j].i.l} : dacc0();
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cacc_mul<false, false>(re, im, A.e[i][k], B.e[k][j]);
+            C.e[i][j] = {dacc_get(re), dacc_get(im)};
+        }
+}
+
 // C += op(A) op(B): the accumulators start from the entries of C (hi, lo)
 template <bool DA, bool DB>
 __device__ __forceinline__ void df_mul_acc(dfmat& C, const dfmat& A, const dfmat& B) {
@@ -194,6 +210,21 @@ __device__ __forceinline__ void store_spinor_df(float4* __restrict__ f, int Vh, 
 __device__ __forceinline__ dfmat link_df_at(const float4* U, const Geom& g, const int x[4], int mu) {
     const int lex = lex_of(g, x);
     return load_link_df(U, g.Vh, (x[0] + x[1] + x[2] + x[3]) & 1, mu, lex >> 1);
+}
+
+// the double-float link U_mu at coordinates x, or its Hermitian conjugate
+__device__ __forceinline__ dfmat link_df_op(const float4* U, const Geom& g, const int x[4], int mu, bool dag) {
+    const int lex = lex_of(g, x);
+    const float4* b = U + (size_t)((((x[0] + x[1] + x[2] + x[3]) & 1) * 4 + mu) * 9) * g.Vh + (lex >> 1);
+    dfmat m;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 v = __ldg(b + (size_t)(dag ? 3 * c + a : 3 * a + c) * g.Vh);
+            m.e[a][c] = {{v.x, v.y}, dag ? df{-v.z, -v.w} : df{v.z, v.w}};
+        }
+    return m;
 }
 
 // Lie components c_a = Im tr(lambda^a M) of a double-float matrix, in FP64

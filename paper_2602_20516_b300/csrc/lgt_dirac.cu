@@ -13,6 +13,7 @@
 // r -= alpha A p with |r|^2, or the true residual b - A x.
 #include "lgt_internal.h"
 #include "lgt_spin.cuh"
+#include "lgt_clover.cuh"
 
 namespace lgt {
 
@@ -116,9 +117,22 @@ __device__ __forceinline__ void hop_accum(const void* U, const Geom& g, const IN
     hop_dir<3, SF, SB, R>(U, g, in, p, lex, x, i, out);
 }
 
+// w = B v for the clover blocks of output site i (FP32, Hermitian-packed field of parity p)
+__device__ __forceinline__ void clover_site(const HopArgs& A, int p, int i, SpinorF& v) {
+    fcx a[12], b[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a[k] = v.c[k / 3][k % 3];
+    clover_mul_f32((const float4*)A.clov + (size_t)p * 18 * A.g.Vh, A.g.Vh, i, a, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v.c[k / 3][k % 3] = b[k];
+}
+__device__ __forceinline__ void clover_site(const HopArgs&, int, int, SpinorD&) {}
+
 // The work of one output site t (t < n): accumulate the 8 hops, apply the epilogue
-// and return this site's contribution to the epilogue's reduction.
-template <typename R, bool DAG, int EPI>
+// and return this site's contribution to the epilogue's reduction.  CLV (FP32 only):
+// 1 applies the output site's clover block to the result of EPI_HOP, 2 applies it to
+// y in EPI_XPAY_NORM / EPI_CG (HopArgs.clov).
+template <typename R, bool DAG, int EPI, int CLV = 0>
 __device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
     using P = Prec<R>;
     using T = typename P::T;
@@ -142,9 +156,11 @@ __device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
         for (int s = 0; s < 4; ++s)
 #pragma unroll
             for (int c = 0; c < 3; ++c) o.c[s][c] = out[s][c];
+        if constexpr (CLV == 1) clover_site(A, p, i, o);
         store_spinor((T*)A.out[p], Vh, i, o);
     } else {
         typename P::S yv = load_spinor((const T*)A.y[p], Vh, i);
+        if constexpr (CLV == 2) clover_site(A, p, i, yv);
         typename P::S o;
 #pragma unroll
         for (int s = 0; s < 4; ++s)
@@ -183,7 +199,7 @@ __device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
     return red;
 }
 
-template <typename R, bool DAG, int EPI>
+template <typename R, bool DAG, int EPI, int CLV = 0>
 __device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk, bool first) {
     if (A.skip && A.s->done >= 1) return;
     if (A.fin_n > 0 && first) {   // finish the deferred reduction of an earlier launch
@@ -192,7 +208,7 @@ __device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk, bo
     }
     const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
     const int t = blk * NT + threadIdx.x;
-    const double red = (t < n) ? hop_site<R, DAG, EPI>(A, t) : 0.0;
+    const double red = (t < n) ? hop_site<R, DAG, EPI, CLV>(A, t) : 0.0;
     if (EPI == EPI_XPAY_NORM || EPI == EPI_CG || EPI == EPI_RESID) {
         double b = block_sum(red);
         if (A.defer) {
@@ -218,9 +234,9 @@ template <typename R, int EPI> constexpr int hop_min_blocks() {
     return sizeof(R) == 4 ? (EPI == EPI_HOP ? LGT_HOP32_MIN_BLOCKS : LGT_HOP32_EPI_MIN_BLOCKS) : LGT_HOP64_MIN_BLOCKS;
 }
 
-template <typename R, bool DAG, int EPI>
+template <typename R, bool DAG, int EPI, int CLV = 0>
 __global__ void __launch_bounds__(NT, (hop_min_blocks<R, EPI>())) hop_kernel(HopArgs A) {
-    hop_body<R, DAG, EPI>(A, A.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x, gridDim.x, blockIdx.x == 0);
+    hop_body<R, DAG, EPI, CLV>(A, A.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x, gridDim.x, blockIdx.x == 0);
 }
 
 // Many independent problems (lattices of any size) in one launch: block b runs
@@ -268,6 +284,17 @@ static cudaError_t launch_epi(const HopArgs& A, int epi, cudaStream_t st) {
     const bool reduces = epi == EPI_XPAY_NORM || epi == EPI_CG || epi == EPI_RESID;
     if (reduces && (!A.partials || grid > A.red_capacity)) return cudaErrorInvalidValue;
     if (A.fin_n > 0 && (!A.partials || !A.s || A.fin_n > A.red_capacity)) return cudaErrorInvalidValue;
+    if (A.clov) {   // the fused even-odd clover variants (FP32, one parity)
+        if (sizeof(R) != 4 || A.parity == 2) return cudaErrorInvalidValue;
+        switch (epi) {
+        case EPI_HOP: hop_kernel<R, DAG, EPI_HOP, 1><<<grid, NT, 0, st>>>(A); break;
+        case EPI_XPAY_NORM: hop_kernel<R, DAG, EPI_XPAY_NORM, 2><<<grid, NT, 0, st>>>(A); break;
+        case EPI_CG: hop_kernel<R, DAG, EPI_CG, 2><<<grid, NT, 0, st>>>(A); break;
+        default: return cudaErrorInvalidValue;
+        }
+        count_launch();
+        return cudaGetLastError();
+    }
     switch (epi) {
     case EPI_HOP: hop_kernel<R, DAG, EPI_HOP><<<grid, NT, 0, st>>>(A); break;
     case EPI_XPAY: hop_kernel<R, DAG, EPI_XPAY><<<grid, NT, 0, st>>>(A); break;

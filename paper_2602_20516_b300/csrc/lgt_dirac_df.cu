@@ -19,6 +19,7 @@
 #include "lgt_internal.h"
 #include "lgt_df64.cuh"
 #include "lgt_spin.cuh"
+#include "lgt_clover.cuh"
 
 namespace lgt {
 
@@ -113,6 +114,39 @@ __device__ __forceinline__ void hop_dir_df(const float4* U, const float4* in, co
     }
 }
 
+// w = B v for the double-float clover blocks of site i: Cp = the parity's [36][Vh] block
+// of a Hermitian-packed double-float field (the FP32 packed layout of lgt_clover.cuh,
+// real k of block c as the pair (hi, lo) in float4 18 c + k / 2)
+__device__ __forceinline__ void clover_mul_df(const float4* __restrict__ Cp, int Vh, int i, const dfc (&v)[4][3],
+                                              dfc (&w)[4][3]) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        df f[36];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const float4 z = __ldg(Cp + (size_t)(18 * c + k) * Vh + i);
+            f[2 * k] = {z.x, z.y};
+            f[2 * k + 1] = {z.z, z.w};
+        }
+#pragma unroll 1
+        for (int r = 0; r < 6; ++r) {
+            dacc re = dacc0(), im = dacc0();
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const dfc vq = v[(6 * c + q) / 3][(6 * c + q) % 3];
+                dfc z;
+                if (q == r) z = {f[r], {0.f, 0.f}};
+                else {
+                    const int o = r < q ? clover_upper_index(r, q) : clover_upper_index(q, r);
+                    z = {f[o], r < q ? f[o + 1] : df_neg(f[o + 1])};
+                }
+                cacc_mul<false, false>(re, im, z, vq);
+            }
+            w[(6 * c + r) / 3][(6 * c + r) % 3] = {dacc_get(re), dacc_get(im)};
+        }
+    }
+}
+
 // y + a v in double-float (y may be zero)
 __device__ __forceinline__ df axpy_df(df a, df v, df y) {
     dacc r = {y.h, y.l};
@@ -120,7 +154,9 @@ __device__ __forceinline__ df axpy_df(df a, df v, df y) {
     return dacc_get(r);
 }
 
-template <bool DAG, int EPI>
+// CLV = 1: the output of EPI_HOP is multiplied by the output site's clover block (HopArgs.clov,
+// double-float packed); CLV = 2: y is multiplied by it before EPI_XPAY / EPI_RESID
+template <bool DAG, int EPI, int CLV = 0>
 __global__ void __launch_bounds__(NT) hop_df_kernel(HopArgs A) {
     const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
     const int t = blockIdx.x * NT + threadIdx.x;
@@ -144,14 +180,23 @@ __global__ void __launch_bounds__(NT) hop_df_kernel(HopArgs A) {
         const df a = df_from(A.a);
         const int Vh = A.g.Vh;
         SpinorDF o;
+        const float4* Cp = (const float4*)A.clov + (size_t)p * 36 * Vh;
         if (EPI == EPI_HOP) {
             const df z = {0.f, 0.f};
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) o.c[s][c] = {axpy_df(a, out[s][c].r, z), axpy_df(a, out[s][c].i, z)};
+            if constexpr (CLV == 1) {
+                const SpinorDF t = o;
+                clover_mul_df(Cp, Vh, i, t.c, o.c);
+            }
         } else {
-            const SpinorDF yv = load_spinor_df((const float4*)A.y[p], Vh, i);
+            SpinorDF yv = load_spinor_df((const float4*)A.y[p], Vh, i);
+            if constexpr (CLV == 2) {
+                const SpinorDF t = yv;
+                clover_mul_df(Cp, Vh, i, t.c, yv.c);
+            }
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -185,6 +230,17 @@ static cudaError_t launch_df_epi(const HopArgs& A, int epi, cudaStream_t st) {
     const int n = (A.parity == 2) ? 2 * A.g.Vh : A.g.Vh;
     const int grid = (n + NT - 1) / NT;
     if (epi == EPI_RESID && (!A.partials || !A.s || grid > A.red_capacity)) return cudaErrorInvalidValue;
+    if (A.clov) {   // even-odd clover: one parity only
+        if (A.parity == 2) return cudaErrorInvalidValue;
+        switch (epi) {
+        case EPI_HOP: hop_df_kernel<DAG, EPI_HOP, 1><<<grid, NT, 0, st>>>(A); break;
+        case EPI_XPAY: hop_df_kernel<DAG, EPI_XPAY, 2><<<grid, NT, 0, st>>>(A); break;
+        case EPI_RESID: hop_df_kernel<DAG, EPI_RESID, 2><<<grid, NT, 0, st>>>(A); break;
+        default: return cudaErrorInvalidValue;
+        }
+        count_launch();
+        return cudaGetLastError();
+    }
     switch (epi) {
     case EPI_HOP: hop_df_kernel<DAG, EPI_HOP><<<grid, NT, 0, st>>>(A); break;
     case EPI_XPAY: hop_df_kernel<DAG, EPI_XPAY><<<grid, NT, 0, st>>>(A); break;
@@ -200,6 +256,36 @@ cudaError_t launch_hop_df(const HopArgs& A, bool dagger, int epi, cudaStream_t s
 }
 
 // ---------------------------------------------------------------- conversions
+// Hermitian-packed double-float copy of the clover blocks of one parity (from the FP64
+// field [parity][72][Vh], full blocks): float4 [parity][36][Vh]
+__global__ void __launch_bounds__(NT) clover_pack_df_kernel(const double2* C64, Geom g, int parity, float4* Cdf) {
+    const int i = blockIdx.x * NT + threadIdx.x;
+    if (i >= g.Vh) return;
+    const double2* b = C64 + (size_t)parity * 72 * g.Vh + i;
+    float4* o = Cdf + (size_t)parity * 36 * g.Vh + i;
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+        double f[36];
+        for (int r = 0; r < 6; ++r) f[r] = __ldg(b + (size_t)(36 * c + 7 * r) * g.Vh).x;
+        for (int r = 0; r < 6; ++r)
+            for (int q = r + 1; q < 6; ++q) {
+                const double2 z = __ldg(b + (size_t)(36 * c + 6 * r + q) * g.Vh);
+                f[clover_upper_index(r, q)] = z.x;
+                f[clover_upper_index(r, q) + 1] = z.y;
+            }
+        for (int k = 0; k < 18; ++k) {
+            const df a = df_from(f[2 * k]), e = df_from(f[2 * k + 1]);
+            o[(size_t)(18 * c + k) * g.Vh] = make_float4(a.h, a.l, e.h, e.l);
+        }
+    }
+}
+cudaError_t clover_pack_df(const double2* C64, const Geom& g, int parity, float4* Cdf, cudaStream_t st) {
+    if (parity != 0 && parity != 1) return cudaErrorInvalidValue;
+    clover_pack_df_kernel<<<(g.Vh + NT - 1) / NT, NT, 0, st>>>(C64, g, parity, Cdf);
+    count_launch();
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(NT) f64_to_df_kernel(float4* y, const double2* x, long ne) {
     const long e = (long)blockIdx.x * NT + threadIdx.x;
     if (e >= ne) return;

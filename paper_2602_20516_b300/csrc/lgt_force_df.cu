@@ -57,23 +57,19 @@ __global__ void __launch_bounds__(NT) gauge_force_df_kernel(const float4* U, Geo
     int xp[4] = {x[0], x[1], x[2], x[3]};
     shift(g, xp, mu, +1);
     dfmat V = df_zero3();
+    // six staples through one loop body (the conjugations taken at load time):
+    //   upper  U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+,  lower  U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu)
 #pragma unroll 1
-    for (int nu = 0; nu < 4; ++nu) {
-        if (nu == mu) continue;
-        int xpn[4] = {x[0], x[1], x[2], x[3]};
-        shift(g, xpn, nu, +1);
-        int xmn[4] = {x[0], x[1], x[2], x[3]};
-        shift(g, xmn, nu, -1);
-        int xpmn[4] = {xp[0], xp[1], xp[2], xp[3]};
-        shift(g, xpmn, nu, -1);
-        {
-            const dfmat a = df_mul<false, true>(link_df_at(U, g, xp, nu), link_df_at(U, g, xpn, mu));
-            df_mul_acc<false, true>(V, a, link_df_at(U, g, x, nu));
-        }
-        {
-            const dfmat b = df_mul<true, true>(link_df_at(U, g, xpmn, nu), link_df_at(U, g, xmn, mu));
-            df_mul_acc<false, false>(V, b, link_df_at(U, g, xmn, nu));
-        }
+    for (int k = 0; k < 6; ++k) {
+        const int nu = (k >> 1) + ((k >> 1) >= mu);
+        const bool lower = k & 1;
+        int a[4] = {xp[0], xp[1], xp[2], xp[3]};   // x + mu (-nu)
+        int b[4] = {x[0], x[1], x[2], x[3]};       // x +- nu
+        if (lower) shift(g, a, nu, -1);
+        shift(g, b, nu, lower ? -1 : +1);
+        dfmat T;
+        df_mul_rows(T, link_df_op(U, g, a, nu, lower), link_df_op(U, g, b, mu, true), false);
+        df_mul_rows(V, T, lower ? link_df_op(U, g, b, nu, false) : link_df_op(U, g, x, nu, true), true);
     }
     const dfmat M = df_mul<false, false>(load_link_df(U, g.Vh, p, mu, i), V);
     double c[8], f[8];

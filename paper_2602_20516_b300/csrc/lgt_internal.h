@@ -47,6 +47,13 @@ struct HopArgs {
     // Dhat^+).
     int defer;
     int fin_n, fin_op;
+    // Even-odd clover operator fused into the hop (Hermitian-packed block field of the
+    // output parity: FP32 [parity][18][Vh] for the FP32 hop, lgt_clover.cuh; double-float
+    // [parity][36][Vh] for the double-float hop): EPI_HOP stores clov(p) a H in (the
+    // inverse block of the output site, M_oo^{-1}); EPI_XPAY_NORM, EPI_CG and (double-
+    // float) EPI_XPAY, EPI_RESID take y -> clov(p) y (M_ee y) before adding a H in.
+    // nullptr: no clover term.
+    const void* clov;
 };
 
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st);
@@ -216,6 +223,9 @@ cudaError_t links_to_df(float4* Udf, const double2* U, const Geom& g, cudaStream
 // double-float half fields; epilogues EPI_HOP, EPI_XPAY (double-float out) and
 // EPI_RESID (pv and out FP64, |out|^2 reduced like the FP64 hop's)
 cudaError_t launch_hop_df(const HopArgs& A, bool dagger, int epi, cudaStream_t st);
+// HopArgs.clov for launch_hop_df: the Hermitian-packed double-float copy float4
+// [parity][36][Vh] of a clover block field's parity (from its FP64 field)
+cudaError_t clover_pack_df(const double2* C64, const Geom& g, int parity, float4* Cdf, cudaStream_t st);
 // ne complex entries FP64 <-> double-float
 cudaError_t complex_to_df(float4* y, const double2* x, long ne, cudaStream_t st);
 cudaError_t complex_from_df(double2* y, const float4* x, long ne, cudaStream_t st);
@@ -236,6 +246,9 @@ struct CloverSigma {
 // C32 float4 [parity][36][Vh]
 cudaError_t clover_field(const double2* U, const Geom& g, const CloverSigma& S, double kappa, double csw,
                          double2* C64, float4* C32, cudaStream_t st);
+// the same field with the leaves in double-float arithmetic on the double-float links
+cudaError_t clover_field_df(const float4* Udf, const Geom& g, const CloverSigma& S, double kappa, double csw,
+                            double2* C64, float4* C32, cudaStream_t st);
 // out = (1 + A) in on parity 0 / 1 (half fields) or 2 (full fields)
 cudaError_t clover_apply(const void* C, const void* in, void* out, const Geom& g, int parity, bool fp64,
                          cudaStream_t st);
@@ -251,8 +264,9 @@ cudaError_t clover_invert(const double2* C64, const Geom& g, int parity, double2
 // adds the insertion of -2 ln det (1 + A) over the sites of `parity` to M (from I64)
 cudaError_t clover_det_insertion(const double2* I64, const Geom& g, int parity, const CloverSigma& S, double kappa,
                                  double csw, double2* M, cudaStream_t st);
-// the clover force gather (Lie form) in double-float arithmetic from the links' double-float copy
-cudaError_t clover_force_df(const float4* Udf, const double2* M, const Geom& g, double coef, int keep, double2* out,
+// the clover force gather (Lie form) in double-float arithmetic from the links' double-float
+// copy and the insertions' (float4 [parity][54][Vh], converted from the FP64 field)
+cudaError_t clover_force_df(const float4* Udf, const float4* Mdf, const Geom& g, double coef, int keep, double2* out,
                             cudaStream_t st);
 cudaError_t clover_force(const double2* U, const double2* M, const Geom& g, double coef, int keep, int form,
                          double2* out, cudaStream_t st);
