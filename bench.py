@@ -80,10 +80,10 @@ HOP_FLOPS = 1320
 HOP_MIN_MS = 0.010
 # ncu DRAM traffic (read + write) of one FP32 hop launch at 32^3 x 64, and the hash of
 # the kernel sources it was taken from (traffic is reported as null once they change)
-NCU_TRAFFIC = {"bytes": 593337600,
-               "sources_sha256": "538073696f8c5ae43bd6ab2f31e5d6a4b04b56151b93b477a7430ed15ff8e2de"}
+NCU_TRAFFIC = {"bytes": 593336576,
+               "sources_sha256": "87a6a7b92692541c925b9919823e18e91a9e55333abfb401a899a2065b72e2de"}
 HOP_SOURCES = ["paper_2602_20516_b300/csrc/lgt_dirac.cu", "paper_2602_20516_b300/csrc/lgt_spin.cuh",
-               "paper_2602_20516_b300/csrc/lgt_common.cuh"]
+               "paper_2602_20516_b300/csrc/lgt_common.cuh", "paper_2602_20516_b300/csrc/lgt_clover.cuh"]
 
 
 def hop_sources_hash():
@@ -759,9 +759,10 @@ def run_serve_only(args):
     import torch
     torch.cuda.set_device(0)
     free, _ = torch.cuda.mem_get_info()
+    nt = args.serve_tight_requests or args.serve_requests
     out = {"metric": "serving: p50/p99 latency (arrival -> completion) and requests/s",
            "full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup),
-           "tight_8GB": run_serving(args.serve_requests, 8 << 30, warmup=args.serve_warmup)}
+           "tight_8GB": run_serving(nt, 8 << 30, warmup=min(args.serve_warmup or nt // 10, nt // 5))}
     if args.detail:
         with open(args.detail, "w") as f:
             json.dump(out, f, indent=1)
@@ -834,6 +835,8 @@ def main():
     ap.add_argument("--serve-warmup", type=int, default=None,
                     help="warm-up requests per rate (default: a tenth of --serve-requests)")
     ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")
+    ap.add_argument("--serve-tight-requests", type=int, default=0,
+                    help="--serve-only: requests per rate under the 8 GB budget (default: --serve-requests)")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving measurement (full budget and 8 GB) and print it")
     ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
