@@ -358,7 +358,10 @@ int lgt_stout_backward(lgt_lattice_t lat, double rho, int n_levels, int recomput
                        const double *G_top_canonical, double *G_thin_canonical);
 
 /* ------------------------------------------------------------------ molecular dynamics */
-/* which = LGT_UPDATE_U: U <- exp(i eps P) U (Eq. S2.1), P from mom.
+/* which = LGT_UPDATE_U: U <- exp(i eps P) U (Eq. S2.1), P from mom.  With sp->precision =
+ * LGT_MIXED and ap->force_arith = LGT_ARITH_DF64 (ap, sp non-NULL) and a double-float copy
+ * of the current links at hand (left by a force evaluation on them), the update runs in
+ * double-float arithmetic (~1e-14 relative); otherwise in FP64.
  * which = LGT_UPDATE_P: mom <- mom - eps F(U) (Eq. S2.2), F as in lgt_force. */
 int lgt_md_update(lgt_lattice_t lat, double *mom, double eps, int which,
                   const lgt_action_params *ap, const double *phi, const lgt_solver_params *sp,

@@ -120,6 +120,9 @@ static int integrate(const int d[4], ocplx *U, double *mom, const ocplx *phi,
             iters += kick(d, U, mom, phi, p, (i + 1 < p->n_steps) ? eps : 0.5 * eps, 0, F, evals);
         }
     } else if (p->integrator == 1) {
+        // the second-order minimum-norm (2MN) position-velocity-position integrator of
+        // Omelyan, Mryglod and Folk, Comput. Phys. Commun. 151 (2003) 272, Eq. (31):
+        // lambda = 0.1931833275037836 minimises the norm of its leading error term
         const double lam = 0.1931833275037836;
         iters += kick(d, U, mom, phi, p, lam * eps, 0, F, evals);
         for (int i = 0; i < p->n_steps; ++i) {

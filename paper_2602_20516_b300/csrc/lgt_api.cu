@@ -525,6 +525,7 @@ extern "C" int lgt_field_bytes(lgt_lattice_t L, int kind, int parity, int precis
 extern "C" int lgt_set_links(lgt_lattice_t L, const double* canon) {
     if (!L || !canon) return fail(LGT_EINVAL, "null argument");
     CK(gauge_pack_links(L->thin.U, L->thin.U12, (const double2*)canon, L->g, L->st));
+    L->udf_src = nullptr;
     return LGT_OK;
 }
 extern "C" int lgt_get_links(lgt_lattice_t L, double* canon) {
@@ -616,6 +617,7 @@ extern "C" int lgt_load_checkpoint(lgt_lattice_t L, const char* path, uint64_t* 
     TRY(ensure_ckpt(L));
     CK(cudaMemcpyAsync(L->ckpt, h + 7, bytes, cudaMemcpyHostToDevice, L->st));
     CK(gauge_pack_links(L->thin.U, L->thin.U12, L->ckpt, L->g, L->st));
+    L->udf_src = nullptr;
     CK(cudaStreamSynchronize(L->st));
     if (seed) *seed = h[4];
     if (next_traj) *next_traj = h[5];
@@ -625,10 +627,12 @@ extern "C" int lgt_load_checkpoint(lgt_lattice_t L, const char* path, uint64_t* 
 extern "C" int lgt_random_links(lgt_lattice_t L, uint64_t seed, double alpha) {
     if (!L) return fail(LGT_EINVAL, "null lattice");
     CK(gauge_random(L->thin.U, L->thin.U12, L->g, seed, alpha, L->st));
+    L->udf_src = nullptr;
     return LGT_OK;
 }
 extern "C" int lgt_reunitarise(lgt_lattice_t L) {
     if (!L) return fail(LGT_EINVAL, "null lattice");
+    L->udf_src = nullptr;
     CK(gauge_reunitarise(L->thin.U, L->thin.U12, L->g, L->st));
     return LGT_OK;
 }
@@ -2034,15 +2038,29 @@ static int kick(lgt_lattice* L, double2* mom, double eps, const lgt_action_param
     return LGT_OK;
 }
 
+// U <- exp(i eps P) U.  With double-float arithmetic on the mixed path (df) and a
+// double-float copy of exactly these links at hand (made by the force evaluation before
+// the update), the update runs in double-float from that copy and keeps it current;
+// otherwise in FP64, and the copy is dropped.
+static int update_links(lgt_lattice* L, const double2* mom, double eps, bool df) {
+    if (df && L->Udf && L->udf_src == L->thin.U) {
+        CK(update_links_df(L->Udf, L->thin.U, L->thin.U12, mom, eps, L->g, L->st));
+        return LGT_OK;
+    }
+    CK(gauge_update_links(L->thin.U, L->thin.U12, mom, eps, L->g, L->st));
+    L->udf_src = nullptr;
+    return LGT_OK;
+}
+static bool df_updates(const lgt_action_params* ap, const lgt_solver_params* sp) {
+    return ap && sp && sp->precision == LGT_MIXED && ap->force_arith == LGT_ARITH_DF64;
+}
+
 extern "C" int lgt_md_update(lgt_lattice_t L, double* mom, double eps, int which, const lgt_action_params* ap,
                              const double* phi, const lgt_solver_params* sp, lgt_solve_stats* stats) {
     if (!L || !mom) return fail(LGT_EINVAL, "null argument");
     NvtxRange nvtx(which == LGT_UPDATE_U ? "lgt update U" : "lgt update P");
     if (stats) *stats = lgt_solve_stats{};
-    if (which == LGT_UPDATE_U) {
-        CK(gauge_update_links(L->thin.U, L->thin.U12, (const double2*)mom, eps, L->g, L->st));
-        return LGT_OK;
-    }
+    if (which == LGT_UPDATE_U) return update_links(L, (const double2*)mom, eps, df_updates(ap, sp));
     if (which != LGT_UPDATE_P) return fail(LGT_EINVAL, "which = %d", which);
     TRY(check_action(ap));
     lgt_solve_stats s = {};
@@ -2078,10 +2096,8 @@ static int integrate(lgt_lattice* L, const lgt_action_params* ap, const lgt_hmc_
         ++*evals;
         return r;
     };
-    auto Uup = [&](double e) -> int {
-        CK(gauge_update_links(L->thin.U, L->thin.U12, L->mom, e, L->g, L->st));
-        return LGT_OK;
-    };
+    const bool dfu = df_updates(ap, &hp->md_solver);
+    auto Uup = [&](double e) -> int { return update_links(L, L->mom, e, dfu); };
     if (hp->integrator == LGT_LEAPFROG) {
         TRY(K(0.5 * eps));
         for (int i = 0; i < hp->n_steps; ++i) {
@@ -2089,6 +2105,9 @@ static int integrate(lgt_lattice* L, const lgt_action_params* ap, const lgt_hmc_
             TRY(K(i + 1 < hp->n_steps ? eps : 0.5 * eps));
         }
     } else if (hp->integrator == LGT_OMELYAN2MN) {
+        // the second-order minimum-norm (2MN) position-velocity-position integrator of
+        // Omelyan, Mryglod and Folk, Comput. Phys. Commun. 151 (2003) 272, Eq. (31):
+        // lambda = 0.1931833275037836 minimises the norm of its leading error term
         const double lam = 0.1931833275037836;
         TRY(K(lam * eps));
         for (int i = 0; i < hp->n_steps; ++i) {
@@ -2176,7 +2195,9 @@ extern "C" int lgt_hmc_trajectory(lgt_lattice_t L, const lgt_action_params* ap, 
     res->accepted = u < std::exp(-res->dH);
     if (!res->accepted) {
         CK(cudaMemcpyAsync(L->thin.U, L->Ubak, links64(L), cudaMemcpyDeviceToDevice, L->st));
+        L->udf_src = nullptr;
     }
+    L->udf_src = nullptr;
     CK(gauge_reunitarise(L->thin.U, L->thin.U12, L->g, L->st));
     TRY(plaquette_sum(L, L->thin.U, &ps));
     res->plaquette = ps / (6.0 * L->g.V);

@@ -219,6 +219,10 @@ cudaError_t chrono_combine(double2* x, const double2* const* v, const double2* c
 // ---------------------------------------------------------------- double-float forces (lgt_force_df.cu)
 // FP64 links / full spinor field -> double-float copies (float4 per complex entry)
 cudaError_t links_to_df(float4* Udf, const double2* U, const Geom& g, cudaStream_t st);
+// U <- exp(i eps P) U in double-float arithmetic from the double-float copy Udf of U;
+// writes U (FP64), U12 and Udf
+cudaError_t update_links_df(float4* Udf, double2* U, float4* U12, const double2* mom, double eps, const Geom& g,
+                            cudaStream_t st);
 // Wilson hop in double-float arithmetic (lgt_dirac_df.cu): U double-float links, in / y
 // double-float half fields; epilogues EPI_HOP, EPI_XPAY (double-float out) and
 // EPI_RESID (pv and out FP64, |out|^2 reduced like the FP64 hop's)

@@ -112,3 +112,39 @@ def test_mixed_solver_true_residual_in_double_float(lgt, ora, dims):
     assert abs(res64 - st["true_rel_residual"]) < 1e-13
     xo, _, _ = ora.cg(dims, U, kappa, b, eo=True, tol=1e-14)
     assert H.rel(_np(lat.unpack_spinor(x, lgt.EVEN, lgt.FP64))[ev], xo[ev]) < 1e-9
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.7])
+def test_df64_link_update_matches_fp64(lgt, eps):
+    """On the mixed path with double-float force arithmetic the link update after a
+    force evaluation runs in double-float from the copy of the links the evaluation
+    made: it agrees with the FP64 update to 1e-13 per link and stays unitary.  eps 0.7
+    with N(0,1) momenta takes the exponential's scaling-and-squaring branch."""
+    dims = (8, 6, 4, 10)
+    U = synth.random_links(dims, 0.5, 51)
+    mom = synth.gaussian_momenta(dims, 52)
+    phi = synth.gaussian_spinor(dims, 53, parity_mask=1)
+    ap = lgt.action_params(beta=5.8, kappa=0.155, even_odd=True, force_arith="df64")
+    sp = lgt.solver("mixed", tol=1e-10, delta=3e-3)
+    a = lgt.Lattice(dims)
+    a.set_links(U)
+    m = a.pack_momenta(mom)
+    a.md_update(m, 0.05, lgt.UPDATE_P, ap, a.pack_spinor(phi, lgt.EVEN, lgt.FP64), sp)
+    b = lgt.Lattice(dims)
+    b.set_links(U)
+    mb = m.clone()
+    a.md_update(m, eps, lgt.UPDATE_U, ap, None, sp)     # double-float
+    b.md_update(mb, eps, lgt.UPDATE_U)                  # FP64
+    Ua, Ub = _np(a.get_links()), _np(b.get_links())
+    per_link = np.linalg.norm((Ua - Ub).reshape(-1, 9), axis=1) / np.linalg.norm(Ub.reshape(-1, 9), axis=1)
+    assert per_link.max() < 1e-13, per_link.max()
+    uu = Ua @ np.conj(np.swapaxes(Ua, -1, -2))
+    assert np.abs(uu - np.eye(3)).max() < 1e-13
+    # the FP32 copy follows the FP64 links: an FP32 operator on it agrees with one on
+    # the FP32 copy derived from the FP64 links (the high word of a pair is the FP64
+    # value rounded to FP32, up to exact ties)
+    src = a.pack_spinor(phi, lgt.EVEN, lgt.FP32)
+    ha = a.dslash(src, lgt.OP_HOP, lgt.ODD, False, 0.0, lgt.FP32)
+    b.set_links(Ua)
+    hb = b.dslash(b.pack_spinor(phi, lgt.EVEN, lgt.FP32), lgt.OP_HOP, lgt.ODD, False, 0.0, lgt.FP32)
+    assert (torch.linalg.norm(ha - hb) / torch.linalg.norm(hb)).item() < 1e-6
