@@ -463,6 +463,10 @@ int lgt_measure_fp64_peak(double *flops, double *seconds);
  * thread safe. */
 #define LGT_TIMING_KINDS 15
 int lgt_kernel_timing_start(int max_launches);
+/* Record only every `every`-th hop launch (>= 1; 1, the default, records all).  Each
+ * recorded pair adds a small gap to the stream; sampling keeps the timed region close
+ * to its untimed speed while every kind of hop is still measured many times. */
+int lgt_kernel_timing_sample(int every);
 int lgt_kernel_timing_stop(double min_ms, double *ms, int64_t *n, int64_t *n_short);
 /* Kernel launches the library enqueued on this thread since the last reset. */
 int64_t lgt_launch_count(int reset);

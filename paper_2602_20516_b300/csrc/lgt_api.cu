@@ -28,6 +28,8 @@ struct KernelTiming {
     std::vector<cudaEvent_t> ev;
     std::vector<int> kind;
     size_t used = 0;
+    uint64_t seen = 0;   // hop launches since start
+    int every = 1;       // record every `every`-th of them
 };
 static KernelTiming g_kt;
 
@@ -39,6 +41,7 @@ int set_error(int code, const char* msg) {
 }
 bool kernel_timing_slot(int kind, cudaEvent_t* a, cudaEvent_t* b) {
     if (!g_kt.on || g_kt.used + 2 > g_kt.ev.size() || g_kt.used / 2 >= g_kt.kind.size()) return false;
+    if (g_kt.seen++ % g_kt.every != 0) return false;   // sampled: every `every`-th hop launch
     *a = g_kt.ev[g_kt.used];
     *b = g_kt.ev[g_kt.used + 1];
     g_kt.kind[g_kt.used / 2] = kind;
@@ -2215,7 +2218,14 @@ extern "C" int lgt_kernel_timing_start(int max_launches) {
     }
     g_kt.kind.assign(max_launches, 0);
     g_kt.used = 0;
+    g_kt.seen = 0;
     g_kt.on = true;
+    return LGT_OK;
+}
+
+extern "C" int lgt_kernel_timing_sample(int every) {
+    if (every < 1) return fail(LGT_EINVAL, "every = %d", every);
+    g_kt.every = every;
     return LGT_OK;
 }
 

@@ -159,6 +159,7 @@ SIGNATURES = [
     ("lgt_clock", C.c_double, []),
     ("lgt_measure_fp64_peak", _I, [C.POINTER(_D), C.POINTER(_D)]),
     ("lgt_kernel_timing_start", _I, [_I]),
+    ("lgt_kernel_timing_sample", _I, [_I]),
     ("lgt_kernel_timing_stop", _I, [_D, C.POINTER(_D), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("lgt_launch_count", C.c_int64, [_I]),
 ]
@@ -222,7 +223,10 @@ def measure_fp64_peak():
     return f.value
 
 
-def kernel_timing_start(max_launches=65536):
+def kernel_timing_start(max_launches=65536, every=1):
+    """Arm CUDA-event timing of the hop launches; every > 1 records only every
+    every-th launch (a sample)."""
+    check(lib().lgt_kernel_timing_sample(every))
     check(lib().lgt_kernel_timing_start(max_launches))
 
 
