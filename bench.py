@@ -802,7 +802,7 @@ def run_kernel(args):
         mom = lat.momentum_field()
         for _ in range(args.reps):
             st = lat.md_update(mom, EPS, lgt.UPDATE_P, ap, phi, sp)
-            lat.md_update(mom, EPS, lgt.UPDATE_U)
+            lat.md_update(mom, EPS, lgt.UPDATE_U, ap, None, sp)
         torch.cuda.synchronize()
         print(json.dumps({"kernel": args.kernel, "md_steps": args.reps, "lattice": list(DIMS), "last_solve": st}))
         return
