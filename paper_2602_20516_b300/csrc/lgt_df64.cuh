@@ -117,18 +117,33 @@ __device__ __forceinline__ dfmat df_mul(const dfmat& A, const dfmat& B) {
 }
 // C = A B and C += A B with the row loop kept as a loop: a third of the code of the
 // unrolled products, for kernels that chain many products per thread and would
-// otherwise outgrow the instruction cache
+// otherwise outgrow the instruction cache.  The row of A and the row of C are picked
+// with selects, not by indexing with the loop counter: an indexed register array
+// would live in local memory, and in the clover force that traffic went to DRAM.
+__device__ __forceinline__ dfc dfc_sel3(int i, const dfc& a0, const dfc& a1, const dfc& a2) {
+    return i == 0 ? a0 : (i == 1 ? a1 : a2);
+}
 __device__ __forceinline__ void df_mul_rows(dfmat& C, const dfmat& A, const dfmat& B, bool acc) {
 #pragma unroll 1
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) {
+        dfc a[3], c[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] = dfc_sel3(i, A.e[0][k], A.e[1][k], A.e[2][k]);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            dacc re = acc ? dacc{C.e[i][j].r.h, C.e[i][j].r.l} : dacc0();
-            dacc im = acc ? dacc{C.e[i][j].i.h, C.e[i][j].i.l} : dacc0();
+            const dfc c0 = dfc_sel3(i, C.e[0][j], C.e[1][j], C.e[2][j]);
+            dacc re = acc ? dacc{c0.r.h, c0.r.l} : dacc0();
+            dacc im = acc ? dacc{c0.i.h, c0.i.l} : dacc0();
 #pragma unroll
-            for (int k = 0; k < 3; ++k) cacc_mul<false, false>(re, im, A.e[i][k], B.e[k][j]);
-            C.e[i][j] = {dacc_get(re), dacc_get(im)};
+            for (int k = 0; k < 3; ++k) cacc_mul<false, false>(re, im, a[k], B.e[k][j]);
+            c[j] = {dacc_get(re), dacc_get(im)};
         }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (r == i) C.e[r][j] = c[j];
+    }
 }
 
 // C += op(A) op(B): the accumulators start from the entries of C (hi, lo)

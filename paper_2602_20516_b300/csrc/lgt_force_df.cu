@@ -67,9 +67,8 @@ __global__ void __launch_bounds__(NT) gauge_force_df_kernel(const float4* U, Geo
         int b[4] = {x[0], x[1], x[2], x[3]};       // x +- nu
         if (lower) shift(g, a, nu, -1);
         shift(g, b, nu, lower ? -1 : +1);
-        dfmat T;
-        df_mul_rows(T, link_df_op(U, g, a, nu, lower), link_df_op(U, g, b, mu, true), false);
-        df_mul_rows(V, T, lower ? link_df_op(U, g, b, nu, false) : link_df_op(U, g, x, nu, true), true);
+        const dfmat T = df_mul<false, false>(link_df_op(U, g, a, nu, lower), link_df_op(U, g, b, mu, true));
+        df_mul_acc<false, false>(V, T, lower ? link_df_op(U, g, b, nu, false) : link_df_op(U, g, x, nu, true));
     }
     const dfmat M = df_mul<false, false>(load_link_df(U, g.Vh, p, mu, i), V);
     double c[8], f[8];
@@ -284,8 +283,7 @@ __global__ void __launch_bounds__(NT) update_links_df_kernel(float4* Udf, double
     E.e[1][0] = dfcm(f1, dfc_conj(o01)) + dfcm(f2, dfc_conj(s01));
     E.e[2][0] = dfcm(f1, dfc_conj(o02)) + dfcm(f2, dfc_conj(s02));
     E.e[2][1] = dfcm(f1, dfc_conj(o12)) + dfcm(f2, dfc_conj(s12));
-    dfmat m;
-    df_mul_rows(m, E, load_link_df(Udf, g.Vh, p, mu, i), false);
+    const dfmat m = df_mul<false, false>(E, load_link_df(Udf, g.Vh, p, mu, i));
     float4* bdf = Udf + (size_t)((p * 4 + mu) * 9) * g.Vh + i;
     double2* b64 = U + (size_t)((p * 4 + mu) * 9) * g.Vh + i;
 #pragma unroll
