@@ -111,6 +111,7 @@ def config_block(args):
             "lattice": list(DIMS), "beta": BETA, "kappa": KAPPA, "alpha": ALPHA, "tol": TOL,
             "delta": DELTA, "seed": SEED, "eps": EPS,
             "l2": "inputs > L2 (1.61 GB of links per field)",
+            "hop_staging": args.staging,
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -299,6 +300,7 @@ def run_ours(args):
         return max_over_ranks(v, world)
 
     lat = lgt.Lattice(DIMS)
+    lat.set_hop_staging(args.staging)
     lat.random_links(SEED + rank, ALPHA)
     phi = lat.gaussian_spinor(SEED + rank, 0, lgt.FIELD_SOURCE, lgt.EVEN)
     mom = lat.gaussian_momenta(SEED + rank, 0)
@@ -783,7 +785,9 @@ def run_serve_only(args):
 def run_kernel(args):
     import torch
     from paper_2602_20516_b300 import lgt
-    lat = lgt.Lattice(DIMS)
+    dims = tuple(args.lattice) if args.lattice else DIMS
+    lat = lgt.Lattice(dims)
+    lat.set_hop_staging(args.staging)
     lat.random_links(SEED, ALPHA)
     if args.kernel == "force_df":
         # one mixed-precision force evaluation with double-float force arithmetic
@@ -792,7 +796,7 @@ def run_kernel(args):
         for _ in range(args.reps):
             lat.force(ap, phi, lgt.solver("mixed", tol=TOL, delta=DELTA))
         torch.cuda.synchronize()
-        print(json.dumps({"kernel": args.kernel, "force_evals": args.reps, "lattice": list(DIMS)}))
+        print(json.dumps({"kernel": args.kernel, "force_evals": args.reps, "lattice": list(dims)}))
         return
     if args.kernel == "clover_md":
         # mixed-precision MD steps with the even-odd clover action (kappa 0.13, c_sw 1.0)
@@ -804,7 +808,7 @@ def run_kernel(args):
             st = lat.md_update(mom, EPS, lgt.UPDATE_P, ap, phi, sp)
             lat.md_update(mom, EPS, lgt.UPDATE_U, ap, None, sp)
         torch.cuda.synchronize()
-        print(json.dumps({"kernel": args.kernel, "md_steps": args.reps, "lattice": list(DIMS), "last_solve": st}))
+        print(json.dumps({"kernel": args.kernel, "md_steps": args.reps, "lattice": list(dims), "last_solve": st}))
         return
     prec = {"hop32": lgt.FP32, "hop64": lgt.FP64, "hopdf": lgt.DF64}[args.kernel]
     src = lat.pack_spinor(lat.unpack_spinor(lat.gaussian_spinor(SEED, 0, lgt.FIELD_SOURCE, lgt.ODD),
@@ -821,7 +825,7 @@ def run_kernel(args):
     torch.cuda.synchronize()
     kinds, _ = lgt.kernel_timing_stop()
     us = {f"{p_}:{e}": 1e3 * ms / n for (p_, e), (ms, n) in kinds.items()}
-    print(json.dumps({"kernel": args.kernel, "launches": args.reps, "lattice": list(DIMS), "avg_us": us}))
+    print(json.dumps({"kernel": args.kernel, "launches": args.reps, "lattice": list(dims), "avg_us": us}))
 
 
 def main():
@@ -855,8 +859,12 @@ def main():
     ap.add_argument("--checkpoint", default="", help="HMC mode: write the chain's checkpoint here after every trajectory")
     ap.add_argument("--chrono", type=int, default=0,
                     help="HMC mode: MD solves start from the last N solutions (chronological guess)")
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="FP32 hops: stage links (1), spinors with halos (2) or both (3) in shared memory")
     ap.add_argument("--kernel", choices=["hop32", "hop64", "hopdf", "force_df", "clover_md"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--lattice", type=int, nargs=4, default=None, metavar=("LX", "LY", "LZ", "LT"),
+                    help="--kernel: lattice extents (default 32 32 32 64); small cases for multi-pass profiles")
     ap.add_argument("--cpu-table1", action="store_true",
                     help="one complete oracle force evaluation at 24^4 with 1 thread and with every core")
     ap.add_argument("--cpu-force-once", action="store_true", help=argparse.SUPPRESS)

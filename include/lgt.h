@@ -287,6 +287,22 @@ int lgt_dslash(lgt_lattice_t lat, const void *in, void *out, int op, int out_par
  * every launch forward.  The order of the sites only: results are bitwise the same. */
 int lgt_set_sweep_order(lgt_lattice_t lat, int alternate);
 
+/* Operand staging of the FP32 one-parity hops (the Wilson hop of Eq. S2.1 on one
+ * parity, and the CG launches built from it).  mode bit 0: each block of 128 output
+ * sites first copies its links (the forward U_mu(x) and backward U_mu(x - mu), 8 per
+ * site) into shared memory with bulk copies; bit 1: likewise its input spinors with
+ * the neighbour halos (the rows below and above, and the same rows of the planes
+ * z -+ 1 and t -+ 1); 0 (the default) reads every operand through L1/L2.  Applies when
+ * L0 / 2 divides 128 and 128 / (L0 / 2) divides L1; other lattices keep mode 0.  The
+ * arithmetic is unchanged: results are bitwise those of mode 0.  Not in the paper.
+ * Returns LGT_EINVAL for a mode outside 0..3. */
+int lgt_set_hop_staging(lgt_lattice_t lat, int mode);
+
+/* *applies = 1 when staging applies to this lattice's extents; *timeouts = the number
+ * of staged blocks, since the library was loaded, whose wait for their copies gave up
+ * after 0.5 s (such a block stores NaN, which the solvers report). */
+int lgt_hop_staging_status(lgt_lattice_t lat, int *applies, unsigned *timeouts);
+
 
 /* Solve A x = b, A = Dhat^+ Dhat on even sites (even_odd = 1; b, x FP64 half
  * fields) or A = D^+ D (even_odd = 0; full FP64 fields), by CG from x = 0

@@ -194,6 +194,8 @@ struct lgt_lattice {
     // of the last launch
     int alternate = 1;
     int sweep = 0;
+    // staging of the FP32 hops' operands in shared memory (lgt_set_hop_staging)
+    int stage = 0;
     // HMC / force workspace
     double2 *mom, *Ubak, *phi, *xi, *F, *G;
     // canonical links staged for lgt_save_checkpoint / lgt_load_checkpoint
@@ -747,6 +749,7 @@ static HopArgs hop_base(lgt_lattice* L, const Links& lk, bool fp64) {
     a.red_capacity = L->n_partials;
     a.counter = L->counter;
     a.a = 1.0;
+    a.stage = fp64 ? 0 : L->stage;
     return a;
 }
 static size_t half_elems(const lgt_lattice* L, bool fp64) { return (size_t)(fp64 ? 12 : 6) * L->g.Vh; }
@@ -845,6 +848,20 @@ extern "C" int lgt_set_sweep_order(lgt_lattice_t L, int alternate) {
     if (!L) return fail(LGT_EINVAL, "null lattice");
     L->alternate = alternate != 0;
     return LGT_OK;
+}
+
+extern "C" int lgt_set_hop_staging(lgt_lattice_t L, int mode) {
+    if (!L) return fail(LGT_EINVAL, "null lattice");
+    if (mode < 0 || mode > 3) return fail(LGT_EINVAL, "staging mode %d (0..3)", mode);
+    L->stage = mode;
+    return LGT_OK;
+}
+
+extern "C" int lgt_hop_staging_status(lgt_lattice_t L, int* applies, unsigned* timeouts) {
+    if (!L || !applies || !timeouts) return fail(LGT_EINVAL, "null argument");
+    *applies = hop_stage_hr(L->g) > 0;
+    *timeouts = hop_stage_timeouts();
+    return *timeouts == ~0u ? fail(LGT_ECUDA, "reading the staging counter failed") : LGT_OK;
 }
 
 extern "C" int lgt_dslash(lgt_lattice_t L, const void* in, void* out, int op, int out_parity, int dagger,

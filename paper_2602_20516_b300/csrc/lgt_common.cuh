@@ -226,9 +226,8 @@ __device__ __forceinline__ void store_link(double2* __restrict__ U, int Vh, int 
     for (int k = 0; k < 9; ++k) b[(size_t)k * Vh] = make_double2(m.e[k / 3][k % 3].r, m.e[k / 3][k % 3].i);
 }
 // FP32 two-row links: float4 [parity][4][3][Vh]; row 3 = conj(row1 x row2)
-__device__ __forceinline__ mat3<float> load_link12(const float4* __restrict__ U, int Vh, int p, int mu, int i) {
-    const float4* b = U + (size_t)((p * 4 + mu) * 3) * Vh + i;
-    float4 a = __ldg(b), c = __ldg(b + Vh), d = __ldg(b + 2 * (size_t)Vh);
+// the SU(3) matrix from its first two rows, stored as the three float4 a, c, d
+__device__ __forceinline__ mat3<float> link12_from(float4 a, float4 c, float4 d) {
     mat3<float> m;
     m.e[0][0] = {a.x, a.y}; m.e[0][1] = {a.z, a.w}; m.e[0][2] = {c.x, c.y};
     m.e[1][0] = {c.z, c.w}; m.e[1][1] = {d.x, d.y}; m.e[1][2] = {d.z, d.w};
@@ -236,6 +235,10 @@ __device__ __forceinline__ mat3<float> load_link12(const float4* __restrict__ U,
     m.e[2][1] = conj(m.e[0][2] * m.e[1][0] - m.e[0][0] * m.e[1][2]);
     m.e[2][2] = conj(m.e[0][0] * m.e[1][1] - m.e[0][1] * m.e[1][0]);
     return m;
+}
+__device__ __forceinline__ mat3<float> load_link12(const float4* __restrict__ U, int Vh, int p, int mu, int i) {
+    const float4* b = U + (size_t)((p * 4 + mu) * 3) * Vh + i;
+    return link12_from(__ldg(b), __ldg(b + Vh), __ldg(b + 2 * (size_t)Vh));
 }
 __device__ __forceinline__ void store_link12(float4* __restrict__ U, int Vh, int p, int mu, int i, const dmat& m) {
     float4* b = U + (size_t)((p * 4 + mu) * 3) * Vh + i;

@@ -47,43 +47,51 @@ __device__ __forceinline__ void mult(const mat3<R>& M, const cx<R> (&h)[2][3], c
         }
 }
 
-// Input half field of a hop, read through the read-only path: load(j) is the spinor
-// of half-field site j.
+// Input half field of a hop, read through the read-only path: load<MU, D>(j) is the
+// spinor of half-field site j, the neighbour of the output site in direction D mu.
 template <typename R> struct PlainIn {
     const typename Prec<R>::T* f;
     int Vh;
+    template <int MU, int D>
     __device__ __forceinline__ typename Prec<R>::S load(int j) const { return load_spinor(f, Vh, j); }
 };
-template <int MU, int SF, int SB, typename R, typename IN>
-__device__ __forceinline__ void hop_dir(const void* U, const Geom& g, const IN& in, int p, int lex,
+// Links read through the read-only path: link<MU, D>(q, site) is U_mu(site) of parity q
+// (site = the output site for D = +1, its neighbour j for D = -1).
+template <typename R> struct PlainLinks {
+    const void* U;
+    int Vh;
+    template <int MU, int D>
+    __device__ __forceinline__ mat3<R> link(int q, int site) const { return Prec<R>::link(U, Vh, q, MU, site); }
+};
+template <int MU, int SF, int SB, typename R, typename IN, typename LK>
+__device__ __forceinline__ void hop_dir(const Geom& g, const IN& in, const LK& lk, int p, int lex,
                                         const int (&x)[4], int i, cx<R> (&out)[4][3]) {
     using P = Prec<R>;
-    const int Vh = g.Vh;
     // forward: b (1 + SF g) U_mu(x) psi(x+mu)
     {
         int j = nb_lex(g, lex, x, MU, +1) >> 1;
-        typename P::S s = in.load(j);
+        typename P::S s = in.template load<MU, +1>(j);
         cx<R> h[2][3], uh[2][3];
         project<MU, SF>(s.c, h);
         if (MU == 3 && x[3] == g.L[3] - 1) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) { h[0][c] = -h[0][c]; h[1][c] = -h[1][c]; }
         }
-        mat3<R> M = P::link(U, Vh, p, MU, i);
+        mat3<R> M = lk.template link<MU, +1>(p, i);
         mult<false>(M, h, uh);
         accumulate<MU, SF>(out, uh);
     }
     // backward: b (1 + SB g) U_mu(x-mu)^+ psi(x-mu)
     {
         int j = nb_lex(g, lex, x, MU, -1) >> 1;
-        typename P::S s = in.load(j);
+        typename P::S s = in.template load<MU, -1>(j);
         cx<R> h[2][3], uh[2][3];
         project<MU, SB>(s.c, h);
         if (MU == 3 && x[3] == 0) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) { h[0][c] = -h[0][c]; h[1][c] = -h[1][c]; }
         }
-        mat3<R> M = P::link(U, Vh, 1 - p, MU, j);
+        mat3<R> M = lk.template link<MU, -1>(1 - p, j);
         mult<true>(M, h, uh);
         accumulate<MU, SB>(out, uh);
     }
@@ -102,8 +110,8 @@ template <typename R> __device__ __forceinline__ double sq(const cx<R> (&v)[4][3
 }
 
 // the 8 hops into output site (p, i) at coordinates x, lexicographic index lex
-template <typename R, bool DAG, typename IN>
-__device__ __forceinline__ void hop_accum(const void* U, const Geom& g, const IN& in, int p, int lex,
+template <typename R, bool DAG, typename IN, typename LK>
+__device__ __forceinline__ void hop_accum(const Geom& g, const IN& in, const LK& lk, int p, int lex,
                                           const int (&x)[4], int i, cx<R> (&out)[4][3]) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -111,10 +119,10 @@ __device__ __forceinline__ void hop_accum(const void* U, const Geom& g, const IN
         for (int c = 0; c < 3; ++c) out[a][c] = {0, 0};
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
-    hop_dir<0, SF, SB, R>(U, g, in, p, lex, x, i, out);
-    hop_dir<1, SF, SB, R>(U, g, in, p, lex, x, i, out);
-    hop_dir<2, SF, SB, R>(U, g, in, p, lex, x, i, out);
-    hop_dir<3, SF, SB, R>(U, g, in, p, lex, x, i, out);
+    hop_dir<0, SF, SB, R>(g, in, lk, p, lex, x, i, out);
+    hop_dir<1, SF, SB, R>(g, in, lk, p, lex, x, i, out);
+    hop_dir<2, SF, SB, R>(g, in, lk, p, lex, x, i, out);
+    hop_dir<3, SF, SB, R>(g, in, lk, p, lex, x, i, out);
 }
 
 // w = B v for the clover blocks of output site i (FP32, Hermitian-packed field of parity p)
@@ -128,22 +136,19 @@ __device__ __forceinline__ void clover_site(const HopArgs& A, int p, int i, Spin
 }
 __device__ __forceinline__ void clover_site(const HopArgs&, int, int, SpinorD&) {}
 
-// The work of one output site t (t < n): accumulate the 8 hops, apply the epilogue
-// and return this site's contribution to the epilogue's reduction.  CLV (FP32 only):
-// 1 applies the output site's clover block to the result of EPI_HOP, 2 applies it to
-// y in EPI_XPAY_NORM / EPI_CG (HopArgs.clov).
-template <typename R, bool DAG, int EPI, int CLV = 0>
-__device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
+// The work of output site (p, i): accumulate the 8 hops (input spinors from `in`,
+// links from `lk`), apply the epilogue and return this site's contribution to the
+// epilogue's reduction.  CLV (FP32 only): 1 applies the output site's clover block to
+// the result of EPI_HOP, 2 applies it to y in EPI_XPAY_NORM / EPI_CG (HopArgs.clov).
+template <typename R, bool DAG, int EPI, int CLV, typename IN, typename LK>
+__device__ __forceinline__ double hop_site_io(const HopArgs& A, int p, int i, const IN& in, const LK& lk) {
     using P = Prec<R>;
     using T = typename P::T;
     double red = 0.0;
-    int p, i;
-    if (A.parity == 2) { p = t >= A.g.Vh; i = t - p * A.g.Vh; }
-    else { p = A.parity; i = t; }
     int x[4];
     int lex = eo_coords(A.g, p, i, x);
     cx<R> out[4][3];
-    hop_accum<R, DAG>(A.U, A.g, PlainIn<R>{(const T*)A.in[1 - p], A.g.Vh}, p, lex, x, i, out);
+    hop_accum<R, DAG>(A.g, in, lk, p, lex, x, i, out);
     const R a = (R)A.a;
     const int Vh = A.g.Vh;
     if (EPI == EPI_HOP) {
@@ -199,6 +204,16 @@ __device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
     return red;
 }
 
+// output site t (t < n) of a launch over parity A.parity (2: both, t >= Vh odd)
+template <typename R, bool DAG, int EPI, int CLV = 0>
+__device__ __forceinline__ double hop_site(const HopArgs& A, int t) {
+    int p, i;
+    if (A.parity == 2) { p = t >= A.g.Vh; i = t - p * A.g.Vh; }
+    else { p = A.parity; i = t; }
+    return hop_site_io<R, DAG, EPI, CLV>(A, p, i, PlainIn<R>{(const typename Prec<R>::T*)A.in[1 - p], A.g.Vh},
+                                         PlainLinks<R>{A.U, A.g.Vh});
+}
+
 template <typename R, bool DAG, int EPI, int CLV = 0>
 __device__ __forceinline__ void hop_body(const HopArgs& A, int blk, int nblk, bool first) {
     if (A.skip && A.s->done >= 1) return;
@@ -237,6 +252,254 @@ template <typename R, int EPI> constexpr int hop_min_blocks() {
 template <typename R, bool DAG, int EPI, int CLV = 0>
 __global__ void __launch_bounds__(NT, (hop_min_blocks<R, EPI>())) hop_kernel(HopArgs A) {
     hop_body<R, DAG, EPI, CLV>(A, A.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x, gridDim.x, blockIdx.x == 0);
+}
+
+// ---------------------------------------------------------------- staged FP32 hop
+// The NT output sites of a block are R = NT / hr whole half-rows (hr = L0 / 2 sites of
+// one parity) of one (z, t) plane.  Before any arithmetic, warp 0 issues bulk copies
+// (cp.async.bulk, completion counted in bytes on one mbarrier) of the block's operands
+// into shared memory:
+//  * spinors (stage bit 1): the input half field on the block's rows, on the half-row
+//    below and the one above them (y neighbours; x neighbours stay in the row), and on
+//    the same rows of the planes z -+ 1 and t -+ 1: 5 NT + 2 hr sites, 6 float4 each;
+//  * links (stage bit 0): U_mu at the output sites (forward hops) and at the neighbours
+//    x - mu (backward hops; for mu = 0 these are the block's own rows of the other
+//    parity): 8 NT links of 3 float4.
+// Every operand is then read from shared memory.  The arithmetic per site is
+// hop_site_io's, so the results are bitwise those of hop_kernel.
+//
+// Spinor slots per component (NSP = 5 NT + 2 hr): [0, hr) the half-row below,
+// [hr, hr + NT) the block's rows, [hr + NT, 2 hr + NT) the half-row above, then the
+// rows of z - 1, z + 1, t - 1, t + 1 (NT each).  Link slots: [2 mu + backward][3][NT].
+
+__device__ unsigned g_stage_timeouts;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\tselp.u32 %0, 1, 0, P;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for phase `parity` of the barrier; gives up after 0.5 s or 2^22 attempts
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && global_ns() - t0 > 500000000ull) return false;
+    }
+    return false;
+}
+
+// input spinors from the staged slots; (l, r, h) = the output site's index in the
+// block, its row in the block and its place in the row
+struct SmemIn {
+    const float4* sp;
+    int NSP, hr, l, r, h, i0;
+    template <int MU, int D> __device__ __forceinline__ SpinorF load(int j) const {
+        int idx;
+        if (MU == 0) idx = hr + (j - i0);
+        else if (MU == 1) idx = hr + (r + D) * hr + h;
+        else if (MU == 2) idx = 2 * hr + (D > 0 ? 2 : 1) * NT + l;
+        else idx = 2 * hr + (D > 0 ? 4 : 3) * NT + l;
+        SpinorF s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = sp[k * NSP + idx];
+            const int c0 = 2 * k, c1 = 2 * k + 1;
+            s.c[c0 / 3][c0 % 3] = {v.x, v.y};
+            s.c[c1 / 3][c1 % 3] = {v.z, v.w};
+        }
+        return s;
+    }
+};
+struct SmemLinks {
+    const float4* lk;
+    int l, i0;
+    template <int MU, int D> __device__ __forceinline__ mat3<float> link(int, int site) const {
+        const int slot = 2 * MU + (D < 0);
+        const int idx = (MU == 0 && D < 0) ? site - i0 : l;
+        const float4* b = lk + slot * 3 * NT + idx;
+        return link12_from(b[0], b[NT], b[2 * NT]);
+    }
+};
+
+template <int ST> constexpr int stage_min_blocks() { return ST == 3 ? 2 : (ST == 2 ? 3 : 4); }
+
+template <bool DAG, int EPI, int CLV, int ST>
+__global__ void __launch_bounds__(NT, (stage_min_blocks<ST>())) hop_staged_kernel(HopArgs A, int hr) {
+    extern __shared__ __align__(16) float4 stage_smem[];
+    __shared__ __align__(8) unsigned long long bar;
+    if (A.skip && A.s->done >= 1) return;
+    const int blk = A.reverse ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int p = A.parity, Vh = A.g.Vh;
+    const int R = NT / hr, NSP = 5 * NT + 2 * hr;
+    const int i0 = blk * NT;
+    float4* sp = stage_smem;                               // [6][NSP] with bit 1
+    float4* lk = stage_smem + ((ST & 2) ? 6 * NSP : 0);    // [8][3][NT] with bit 0
+    const uint32_t bar_a = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(bar_a, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int L1 = A.g.L[1], L2 = A.g.L[2], L3 = A.g.L[3];
+        const int PS = hr * L1;   // sites of one parity in an x-y plane
+        const int plane = i0 / PS, off = i0 - plane * PS;
+        const int z = plane % L2, t = plane / L2, y0 = off / hr;
+        const int base = plane * PS;
+        const int ym = base + ((y0 - 1 + L1) % L1) * hr, yp = base + ((y0 + R) % L1) * hr;
+        const int zm = (t * L2 + (z - 1 + L2) % L2) * PS + off, zp = (t * L2 + (z + 1) % L2) * PS + off;
+        const int tm = (((t - 1 + L3) % L3) * L2 + z) * PS + off, tp = (((t + 1) % L3) * L2 + z) * PS + off;
+        if (threadIdx.x == 0)
+            mbar_expect_tx(bar_a, (uint32_t)(((ST & 2) ? 6 * NSP : 0) + ((ST & 1) ? 24 * NT : 0)) * 16u);
+        __syncwarp();
+        if (ST & 2) {
+            const float4* in = (const float4*)A.in[1 - p];
+            for (int c = threadIdx.x; c < 42; c += 32) {
+                const int k = c / 7, part = c % 7;
+                int src, dst, n = NT;
+                switch (part) {
+                case 0: src = i0; dst = hr; break;
+                case 1: src = ym; dst = 0; n = hr; break;
+                case 2: src = yp; dst = hr + NT; n = hr; break;
+                case 3: src = zm; dst = 2 * hr + NT; break;
+                case 4: src = zp; dst = 2 * hr + 2 * NT; break;
+                case 5: src = tm; dst = 2 * hr + 3 * NT; break;
+                default: src = tp; dst = 2 * hr + 4 * NT; break;
+                }
+                bulk_to_smem(smem_u32(sp + k * NSP + dst), in + (size_t)k * Vh + src, (uint32_t)n * 16u, bar_a);
+            }
+        }
+        if (ST & 1) {
+            const float4* U = (const float4*)A.U;
+            for (int c = threadIdx.x; c < 27; c += 32) {
+                int q = 1 - p, mu, k, src, slot, dst = 0, n = NT;
+                if (c < 12) { q = p; mu = c / 3; k = c % 3; src = i0; slot = 2 * mu; }
+                else if (c < 15) { mu = 0; k = c - 12; src = i0; slot = 1; }
+                else if (c < 18) { mu = 1; k = c - 15; src = i0; slot = 3; dst = hr; n = NT - hr; }
+                else if (c < 21) { mu = 1; k = c - 18; src = ym; slot = 3; n = hr; }
+                else if (c < 24) { mu = 2; k = c - 21; src = zm; slot = 5; }
+                else { mu = 3; k = c - 24; src = tm; slot = 7; }
+                if (n > 0)
+                    bulk_to_smem(smem_u32(lk + (slot * 3 + k) * NT + dst), U + (size_t)((q * 4 + mu) * 3 + k) * Vh + src,
+                                 (uint32_t)n * 16u, bar_a);
+            }
+        }
+    }
+    if (A.fin_n > 0 && blockIdx.x == 0) {   // finish the deferred reduction of an earlier launch
+        const double acc = ordered_sum(A.partials, A.fin_n);
+        if (threadIdx.x == 0) apply_reduce_op(A.s, A.fin_op, A.red_slot, acc);
+    }
+    bool ok = __syncthreads_and(mbar_wait_bounded(bar_a, 0));
+    if (!ok) {
+        // the copies did not complete in time: count it, wait (bounded) for the copies
+        // still in flight into this block's shared memory, and store NaN
+        if (threadIdx.x == 0) atomicAdd(&g_stage_timeouts, 1u);
+        mbar_wait_bounded(bar_a, 0);
+    }
+    const int l = threadIdx.x, i = i0 + l;
+    double red;
+    if (ok) {
+        const int r = l / hr, h = l - r * hr;
+        const SmemIn si{sp, NSP, hr, l, r, h, i0};
+        const SmemLinks sl{lk, l, i0};
+        if constexpr (ST == 3) red = hop_site_io<float, DAG, EPI, CLV>(A, p, i, si, sl);
+        else if constexpr (ST == 2) red = hop_site_io<float, DAG, EPI, CLV>(A, p, i, si, PlainLinks<float>{A.U, Vh});
+        else red = hop_site_io<float, DAG, EPI, CLV>(A, p, i, PlainIn<float>{(const float4*)A.in[1 - p], Vh}, sl);
+    } else {
+        SpinorF o;
+        const float qnan = __int_as_float(0x7fffffff);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o.c[s][c] = {qnan, qnan};
+        store_spinor((float4*)(EPI == EPI_CG ? A.r[p] : A.out[p]), Vh, i, o);
+        red = (double)qnan;
+    }
+    if (EPI == EPI_XPAY_NORM || EPI == EPI_CG || EPI == EPI_RESID) {
+        const double b = block_sum(red);
+        if (A.defer) {
+            if (threadIdx.x == 0) A.partials[blk] = b;
+        } else {
+            grid_reduce(b, A.partials, A.counter, A.s, A.red_op, A.red_slot, blk, gridDim.x);
+        }
+    }
+}
+
+int hop_stage_hr(const Geom& g) {
+    const int hr = g.L[0] / 2;
+    if (hr < 1 || NT % hr != 0 || g.L[1] % (NT / hr) != 0 || g.Vh % NT != 0) return 0;
+    return hr;
+}
+
+unsigned hop_stage_timeouts() {
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_stage_timeouts, sizeof v) != cudaSuccess) return ~0u;
+    return v;
+}
+
+template <bool DAG, int EPI, int CLV, int ST>
+static cudaError_t launch_staged_st(const HopArgs& A, int hr, cudaStream_t st) {
+    const size_t bytes = (size_t)(((ST & 2) ? 6 * (5 * NT + 2 * hr) : 0) + ((ST & 1) ? 24 * NT : 0)) * 16;
+    static size_t allowed = 0;   // dynamic shared memory this instantiation may use
+    if (bytes > allowed) {
+        cudaError_t e = cudaFuncSetAttribute(hop_staged_kernel<DAG, EPI, CLV, ST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        allowed = bytes;
+    }
+    hop_staged_kernel<DAG, EPI, CLV, ST><<<A.g.Vh / NT, NT, bytes, st>>>(A, hr);
+    count_launch();
+    return cudaGetLastError();
+}
+template <bool DAG, int EPI, int CLV>
+static cudaError_t launch_staged_mode(const HopArgs& A, int hr, cudaStream_t st) {
+    switch (A.stage & 3) {
+    case 1: return launch_staged_st<DAG, EPI, CLV, 1>(A, hr, st);
+    case 2: return launch_staged_st<DAG, EPI, CLV, 2>(A, hr, st);
+    default: return launch_staged_st<DAG, EPI, CLV, 3>(A, hr, st);
+    }
+}
+// the staged variant of an FP32 one-parity launch; cudaErrorNotSupported when it has none
+template <bool DAG>
+static cudaError_t launch_staged(const HopArgs& A, int epi, int hr, cudaStream_t st) {
+    if (A.clov) {
+        switch (epi) {
+        case EPI_HOP: return launch_staged_mode<DAG, EPI_HOP, 1>(A, hr, st);
+        case EPI_XPAY_NORM: return launch_staged_mode<DAG, EPI_XPAY_NORM, 2>(A, hr, st);
+        case EPI_CG: return launch_staged_mode<DAG, EPI_CG, 2>(A, hr, st);
+        default: return cudaErrorNotSupported;
+        }
+    }
+    switch (epi) {
+    case EPI_HOP: return launch_staged_mode<DAG, EPI_HOP, 0>(A, hr, st);
+    case EPI_XPAY: return launch_staged_mode<DAG, EPI_XPAY, 0>(A, hr, st);
+    case EPI_XPAY_NORM: return launch_staged_mode<DAG, EPI_XPAY_NORM, 0>(A, hr, st);
+    case EPI_CG: return launch_staged_mode<DAG, EPI_CG, 0>(A, hr, st);
+    default: return cudaErrorNotSupported;
+    }
 }
 
 // Many independent problems (lattices of any size) in one launch: block b runs
@@ -284,6 +547,13 @@ static cudaError_t launch_epi(const HopArgs& A, int epi, cudaStream_t st) {
     const bool reduces = epi == EPI_XPAY_NORM || epi == EPI_CG || epi == EPI_RESID;
     if (reduces && (!A.partials || grid > A.red_capacity)) return cudaErrorInvalidValue;
     if (A.fin_n > 0 && (!A.partials || !A.s || A.fin_n > A.red_capacity)) return cudaErrorInvalidValue;
+    if (sizeof(R) == 4 && (A.stage & 3) && A.parity != 2) {
+        const int hr = hop_stage_hr(A.g);
+        if (hr > 0) {
+            cudaError_t e = launch_staged<DAG>(A, epi, hr, st);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    }
     if (A.clov) {   // the fused even-odd clover variants (FP32, one parity)
         if (sizeof(R) != 4 || A.parity == 2) return cudaErrorInvalidValue;
         switch (epi) {

@@ -54,10 +54,20 @@ struct HopArgs {
     // float) EPI_XPAY, EPI_RESID take y -> clov(p) y (M_ee y) before adding a H in.
     // nullptr: no clover term.
     const void* clov;
+    // FP32 one-parity hops on a lattice whose half-rows tile the block (hop_stage_hr):
+    // bit 0 stages the block's links, bit 1 its input spinors and their neighbour halos
+    // in shared memory by bulk copies before the arithmetic (same results); 0 reads
+    // every operand through L1/L2.
+    int stage;
 };
 
 cudaError_t launch_hop(const HopArgs& A, bool fp64, bool dagger, int epi, cudaStream_t st);
 int hop_grid(const Geom& g, int parity);
+// half-row length L0 / 2 when the staged FP32 hop applies to this geometry (whole
+// half-rows tile a block and the rows of a block tile an x-y plane), else 0
+int hop_stage_hr(const Geom& g);
+// blocks of the staged hop whose wait for their bulk copies gave up (they stored NaN)
+unsigned hop_stage_timeouts();
 
 // Several right-hand sides (1..KMAX_RHS, every slot a valid system) on the same FP32
 // links and output parity in one launch: each link is loaded once per site and

@@ -125,6 +125,8 @@ SIGNATURES = [
     ("lgt_unpack_links_field", _I, [_P, _P, _P]),
     ("lgt_set_clover", _I, [_P, _D, _D]),
     ("lgt_set_sweep_order", _I, [_P, _I]),
+    ("lgt_set_hop_staging", _I, [_P, _I]),
+    ("lgt_hop_staging_status", _I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_uint)]),
     ("lgt_save_checkpoint", _I, [_P, C.c_char_p, C.c_uint64, C.c_uint64]),
     ("lgt_load_checkpoint", _I, [_P, C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     ("lgt_dslash", _I, [_P, _P, _P, _I, _I, _I, _D, _I]),
@@ -419,6 +421,17 @@ class Lattice:
     def set_sweep_order(self, alternate=True):
         """Alternate the site order of consecutive CG launches (default) or walk forward."""
         check(lib().lgt_set_sweep_order(self.h, int(bool(alternate))))
+
+    def set_hop_staging(self, mode):
+        """Stage the FP32 hops' operands in shared memory: bit 0 links, bit 1 spinors
+        with their neighbour halos; 0 reads them through L1/L2 (lgt_set_hop_staging)."""
+        check(lib().lgt_set_hop_staging(self.h, int(mode)))
+
+    def hop_staging_status(self):
+        """(staging applies to these extents, staged blocks whose copy wait gave up)."""
+        ap, to = C.c_int(), C.c_uint()
+        check(lib().lgt_hop_staging_status(self.h, C.byref(ap), C.byref(to)))
+        return bool(ap.value), to.value
 
     def dslash(self, inp, op=OP_D, out_parity=FULL, dagger=False, kappa=0.0, precision=FP64, out=None):
         if out is None:
