@@ -525,6 +525,8 @@ def run_ours(args):
     if args.serve_requests > 0:
         free, total = torch.cuda.mem_get_info()
         serving = {"full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup),
+                   "mixed_only": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup,
+                                             rates=(0.5, 0.9), mixed_fraction=1.0),
                    "tight_8GB": run_serving(args.serve_requests, 8 << 30, warmup=args.serve_warmup)
                    if args.serve_tight else None}
 
@@ -578,6 +580,7 @@ def run_ours(args):
            "clover_overhead": clover["clover_overhead"] if clover else None,
            "multi_rhs_solve4_speedup": multi["solve4"]["speedup"] if multi else None,
            "serving": serve_summary(serving["full"]) if serving else None,
+           "serving_mixed_only": serve_summary(serving["mixed_only"]) if serving else None,
            "serving_tight_8GB": serve_summary(serving["tight_8GB"]) if serving else None,
            "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "kind", "cores", "cpu_model")} |
                             {"sample": "estimate from a capped-CG sample (see detail)",
@@ -646,12 +649,14 @@ def run_multi_rhs(lat, stream, reps=50):
 SERVE_VOLUMES = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 48)]
 
 
-def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9, 1.2)):
+def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9, 1.2), mixed_fraction=0.5):
     """Resident pool of 2 gauge fields per volume (alpha ~ U[0.3, 0.6]); requests:
-    70% Dirac solves, 30% force evaluations, kappa ~ U[0.14, 0.157], FP64 / mixed
-    50/50, tol 1e-10.  Saturated throughput, then open-loop Poisson arrivals at
-    0.5, 0.9 and 1.2 x that rate (1.2 x is overload: no steady state); latency =
-    completion - scheduled arrival, over the requests after the first `warmup`."""
+    70% Dirac solves, 30% force evaluations, kappa ~ U[0.14, 0.157], a fraction
+    `mixed_fraction` in mixed precision and the rest FP64 (0.5: half FP64; 1.0:
+    every request mixed), tol 1e-10.  Saturated throughput, then open-loop Poisson
+    arrivals at 0.5, 0.9 and 1.2 x that rate (1.2 x is overload: no steady state);
+    latency = completion - scheduled arrival, over the requests after the first
+    `warmup`."""
     import numpy as np
     from paper_2602_20516_b300 import serve
     rng = np.random.default_rng(seed)
@@ -663,15 +668,15 @@ def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9,
             gids.append(g)
             vol[g] = "x".join(map(str, d))
     warm = max(10, n_per_rate // 10) if warmup is None else warmup
-    serve.saturated(srv, serve.workload(gids, warm, seed=seed))          # warm-up
-    thr, done = serve.saturated(srv, serve.workload(gids, n_per_rate, seed=seed + 1))
-    out = {"saturated_requests_per_s": thr, "budget_bytes": budget_bytes,
+    serve.saturated(srv, serve.workload(gids, warm, seed=seed, mixed_fraction=mixed_fraction))   # warm-up
+    thr, done = serve.saturated(srv, serve.workload(gids, n_per_rate, seed=seed + 1, mixed_fraction=mixed_fraction))
+    out = {"saturated_requests_per_s": thr, "budget_bytes": budget_bytes, "mixed_fraction": mixed_fraction,
            "requests_per_rate": n_per_rate, "warmup_per_rate": warm, "rates": {}}
 
     def label(c):
         return f"{vol[c['gauge_id']]}/{'solve' if c['kind'] == serve.SOLVE else 'force'}/{c['precision']}"
     for j, f in enumerate(rates):
-        reqs = serve.workload(gids, n_per_rate + warm, seed=seed + 2 + j)
+        reqs = serve.workload(gids, n_per_rate + warm, seed=seed + 2 + j, mixed_fraction=mixed_fraction)
         d = serve.poisson(srv, reqs, f * thr, seed=seed + 20 + j, warmup=warm)
         st = serve.latency_stats(d)
         st["offered_per_s"] = f * thr
@@ -772,9 +777,11 @@ def run_serve_only(args):
     torch.cuda.set_device(0)
     free, _ = torch.cuda.mem_get_info()
     nt = args.serve_tight_requests or args.serve_requests
-    out = {"metric": "serving: p50/p99 latency (arrival -> completion) and requests/s",
-           "full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup),
-           "tight_8GB": run_serving(nt, 8 << 30, warmup=min(args.serve_warmup or nt // 10, nt // 5))}
+    f = args.serve_mixed_fraction
+    out = {"metric": "serving: p50/p99 latency (arrival -> completion) and requests/s", "mixed_fraction": f,
+           "full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup, mixed_fraction=f),
+           "tight_8GB": run_serving(nt, 8 << 30, warmup=min(args.serve_warmup or nt // 10, nt // 5),
+                                    mixed_fraction=f)}
     if args.detail:
         with open(args.detail, "w") as f:
             json.dump(out, f, indent=1)
@@ -853,6 +860,8 @@ def main():
                     help="--serve-only: requests per rate under the 8 GB budget (default: --serve-requests)")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving measurement (full budget and 8 GB) and print it")
+    ap.add_argument("--serve-mixed-fraction", type=float, default=0.5,
+                    help="--serve-only: fraction of requests in mixed precision (the rest FP64)")
     ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
     ap.add_argument("--hmc-fp64", type=int, default=2, help="trajectories replayed on the FP64 path")
     ap.add_argument("--log", default="", help="HMC mode: append one JSON line per trajectory to this file")

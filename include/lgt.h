@@ -416,10 +416,14 @@ int lgt_hmc_trajectory(lgt_lattice_t lat, const lgt_action_params *ap,
  * order while active slots and the HBM budget allow, runs `batch_iters` CG
  * iterations of every running request with batched launches (one launch per CG
  * kernel step covers all running requests of a precision, whatever their
- * volume), forms the FP64 true residual of requests whose stop condition fired
- * (mixed requests: a reliable update), and finishes converged requests.  A
- * request's arithmetic does not depend on the other requests: its result is the
- * same alone and in any mix.  Timestamps are host steady-clock seconds
+ * volume), forms the true residual of requests whose stop condition fired (mixed
+ * requests: a reliable update), and finishes converged requests.  The true residual
+ * is formed with the FP64 hop, or, for a mixed request on a gauge field that has a
+ * double-float copy, with the double-float hop (as the mixed lgt_cg_solve); such a
+ * force request's forces are then taken in double-float arithmetic as well.
+ * lgt_server_add_gauge makes the double-float copy (as many bytes as the FP64 links)
+ * when the gauge fields added so far, with their copies, stay within half the budget.  A request's arithmetic does not
+ * depend on the other requests: its result is the same alone and in any mix.  Timestamps are host steady-clock seconds
  * (lgt_clock).  Memory of requests, gauge fields and descriptors is allocated
  * through `alloc` (NULL: cudaMalloc) and counted against hbm_budget_bytes. */
 typedef struct lgt_server *lgt_server_t;

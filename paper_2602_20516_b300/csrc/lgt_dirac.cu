@@ -463,12 +463,18 @@ unsigned hop_stage_timeouts() {
 template <bool DAG, int EPI, int CLV, int ST>
 static cudaError_t launch_staged_st(const HopArgs& A, int hr, cudaStream_t st) {
     const size_t bytes = (size_t)(((ST & 2) ? 6 * (5 * NT + 2 * hr) : 0) + ((ST & 1) ? 24 * NT : 0)) * 16;
-    static size_t allowed = 0;   // dynamic shared memory this instantiation may use
-    if (bytes > allowed) {
-        cudaError_t e = cudaFuncSetAttribute(hop_staged_kernel<DAG, EPI, CLV, ST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // dynamic shared memory this instantiation may use, per device (the attribute is
+    // a property of the function on each device)
+    constexpr int kDevices = 64;
+    static size_t allowed[kDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevices || bytes > allowed[dev]) {
+        e = cudaFuncSetAttribute(hop_staged_kernel<DAG, EPI, CLV, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
         if (e != cudaSuccess) return e;
-        allowed = bytes;
+        if (dev >= 0 && dev < kDevices) allowed[dev] = bytes;
     }
     hop_staged_kernel<DAG, EPI, CLV, ST><<<A.g.Vh / NT, NT, bytes, st>>>(A, hr);
     count_launch();

@@ -48,6 +48,7 @@ struct Gauge {
     Geom g;
     double2* U;
     float4* U12;
+    float4* Udf = nullptr;   // double-float copy (when the budget allowed it at creation)
     size_t bytes;
 };
 
@@ -162,8 +163,50 @@ int rhop(lgt_server* S, Req* R, bool fp64, bool dag, int q, const void* in, void
     return LGT_OK;
 }
 
-// res = c - Dhat^+ Dhat x (FP64), |res|^2 into the request's scalar slot 0
+// res = c - Dhat^+ Dhat x with the double-float hop (a mixed request on a gauge field
+// with a double-float copy), |res|^2 into the request's scalar slot 0.  A force request
+// keeps the intermediate vectors X = (x_e, kappa H_oe x_e), Y = (Dhat x_e,
+// kappa (H^+)_oe Dhat x_e) in double-float in its X, Y buffers (the converged
+// residual's vectors feed the force); a solve request borrows its FP64 u, t, p (unused
+// by the FP32 iterations) and its FP32 x, r pair, and x32 is cleared again afterwards.
+int true_residual_df(lgt_server* S, Req* R) {
+    const Gauge& G = S->gauges[R->q.gauge_id];
+    const Geom& g = G.g;
+    const long hf = 12L * g.Vh;
+    const double kappa = R->q.kappa;
+    float4 *xe, *Xo, *Ye, *Yo;
+    if (R->q.kind == LGT_REQ_FORCE) {
+        xe = (float4*)R->X; Xo = xe + hf;
+        Ye = (float4*)R->Y; Yo = Ye + hf;
+    } else {
+        xe = (float4*)R->u; Xo = (float4*)R->t;
+        Ye = (float4*)R->p; Yo = R->x32;
+    }
+    SCK(complex_to_df(xe, R->x, hf, S->st));
+    HopArgs A;
+    memset(&A, 0, sizeof A);
+    A.U = G.Udf;
+    A.g = g;
+    A.parity = 1; A.in[0] = xe; A.out[1] = Xo; A.a = kappa;
+    SCK(launch_hop_df(A, false, EPI_HOP, S->st));
+    A.parity = 0; A.in[1] = Xo; A.out[0] = Ye; A.y[0] = xe; A.a = -kappa;
+    SCK(launch_hop_df(A, false, EPI_XPAY, S->st));
+    A.parity = 1; A.in[0] = Ye; A.out[1] = Yo; A.y[0] = nullptr; A.a = kappa;
+    SCK(launch_hop_df(A, true, EPI_HOP, S->st));
+    HopArgs B = req_hop(S, R, G, true);
+    B.U = G.Udf;
+    B.parity = 0; B.in[1] = Yo; B.y[0] = Ye; B.a = -kappa; B.out[0] = R->r; B.pv[0] = R->c;
+    B.red_op = RED_STORE; B.red_slot = 0;
+    SCK(launch_hop_df(B, true, EPI_RESID, S->st));
+    if (R->q.kind == LGT_REQ_SOLVE) SCK(cudaMemsetAsync(R->x32, 0, half32(g), S->st));
+    return LGT_OK;
+}
+bool df_residual(const lgt_server* S, const Req* R) { return !R->fp64 && S->gauges[R->q.gauge_id].Udf; }
+
+// res = c - Dhat^+ Dhat x (FP64, or double-float for a mixed request on a gauge field
+// with a double-float copy), |res|^2 into the request's scalar slot 0
 int true_residual(lgt_server* S, Req* R) {
+    if (df_residual(S, R)) return true_residual_df(S, R);
     const double k2 = R->q.kappa * R->q.kappa;
     STRY(rhop(S, R, true, false, 1, R->x, R->t, 1.0));
     STRY(rhop(S, R, true, false, 0, R->t, R->u, -k2, EPI_XPAY, R->x));
@@ -193,8 +236,9 @@ int admit(lgt_server* S, Req* R) {
     R->u = (double2*)take(half64(g));
     R->t = (double2*)take(half64(g));
     if (!R->fp64) {
-        R->x32 = (float4*)take(half32(g));
-        R->r32 = (float4*)take(half32(g));
+        // x32 and r32 adjacent: together one double-float half field for the residual
+        R->x32 = (float4*)take(2 * half32(g));
+        R->r32 = R->x32 + (size_t)6 * g.Vh;
         R->p32 = (float4*)take(half32(g));
         R->u32 = (float4*)take(half32(g));
         R->t32 = (float4*)take(half32(g));
@@ -261,6 +305,15 @@ int finish(lgt_server* S, Req* R) {
         SCK(cudaMemcpyAsync(R->out, R->x, half64(g), cudaMemcpyDeviceToDevice, S->st));
         STRY(rhop(S, R, true, false, 1, R->x, R->out + (size_t)12 * g.Vh, kappa, EPI_XPAY,
                   R->src + (size_t)12 * g.Vh));
+    } else if (df_residual(S, R)) {
+        // the converged double-float residual left X, Y in double-float: the mixed
+        // path's double-float forces (Lie form, FP64 accumulation)
+        int keep = 0;
+        if (R->q.beta != 0.0) {
+            SCK(gauge_force_df(G.Udf, g, R->q.beta, 1.0, 0, R->out, S->st));
+            keep = 1;
+        }
+        SCK(fermion_force_df(G.Udf, (const float4*)R->X, (const float4*)R->Y, g, kappa, 1.0, keep, R->out, S->st));
     } else {
         double2* Xo = R->X + (size_t)12 * g.Vh;
         double2* Yo = R->Y + (size_t)12 * g.Vh;
@@ -386,7 +439,11 @@ extern "C" int lgt_server_destroy(lgt_server_t S) {
     for (Req* R : S->queue) { release(S, R); delete R; }
     for (Req* R : S->active) { release(S, R); delete R; }
     for (Req* R : S->done) { release(S, R); delete R; }
-    for (Gauge& G : S->gauges) { srv_free(S, G.U); srv_free(S, G.U12); }
+    for (Gauge& G : S->gauges) {
+        srv_free(S, G.U);
+        srv_free(S, G.U12);
+        srv_free(S, G.Udf);
+    }
     for (void* p : S->fixed) srv_free(S, p);
     if (S->hs) cudaFreeHost(S->hs);
     if (S->h_hop) cudaFreeHost(S->h_hop);
@@ -421,8 +478,18 @@ extern "C" int lgt_server_add_gauge(lgt_server_t S, const int dims[4], uint64_t 
     G.U = (double2*)a;
     G.U12 = (float4*)b;
     G.bytes = b64 + b12;
+    // the double-float copy for the mixed requests' residuals and forces, when the
+    // gauge fields with their copies stay within half the budget (the other half is
+    // left to requests); decided once per field, so a request's arithmetic never
+    // depends on the other requests
+    void* c = nullptr;
+    if (S->used + G.bytes + b64 <= S->budget / 2 && srv_alloc(S, b64, &c) == LGT_OK) {
+        G.Udf = (float4*)c;
+        G.bytes += b64;
+    }
     S->used += G.bytes;
     SCK(gauge_random(G.U, G.U12, G.g, seed, alpha, S->st));
+    if (G.Udf) SCK(links_to_df(G.Udf, G.U, G.g, S->st));
     SCK(cudaStreamSynchronize(S->st));
     S->gauges.push_back(G);
     *gauge_id = (int)S->gauges.size() - 1;

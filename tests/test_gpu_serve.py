@@ -56,6 +56,41 @@ def test_solve_and_force_vs_oracle(serve, ora, precision):
     srv.close()
 
 
+def test_mixed_requests_with_and_without_double_float_copy(serve, ora):
+    """A mixed request forms its true residuals (and a force request its forces) in
+    double-float when its gauge field has a double-float copy, which the server makes
+    while the gauge fields with copies stay within half the budget; otherwise it uses
+    the FP64 hop and FP64 forces.  Both meet the tolerance, agree with the oracle
+    within the solve's error bound (cond(A) ~ 1e2 times tol 1e-10) and with each
+    other."""
+    dims = (6, 4, 4, 8)
+    Vh = int(np.prod(dims)) // 2
+    links64, links12 = 8 * 9 * Vh * 16, 8 * 3 * Vh * 16
+    res = {}
+    for name, budget in (("df", 4 * GB), ("fp64", 2_000_000)):
+        srv = serve.Server(budget, max_active=4, batch_iters=4)
+        g = srv.add_gauge(dims, 11, 0.5)
+        assert srv.info()["used_bytes"] == links64 + links12 + (links64 if name == "df" else 0)
+        out = []
+        # one at a time: a kept result holds its memory until fetched, and under the
+        # small budget only one request fits
+        for kind, seed, conv in ((serve.SOLVE, 5, _full_canonical), (serve.FORCE, 6, _mom_canonical)):
+            r = srv.submit(g, kind, 0.15, "mixed", tol=1e-10, source_seed=seed, beta=5.8, keep_result=True)
+            done = {c["id"]: c for c in srv.run_until_idle()}
+            assert done[r]["status"] == 0 and done[r]["true_rel_residual"] <= 1e-10, (name, done[r])
+            out.append(conv(srv.result(r), dims))
+        res[name] = tuple(out)
+        srv.close()
+    Uo = ora.random_links(dims, 11, 0.5)
+    b = ora.gaussian_spinor(dims, 5, 0, ora.FIELD_SOURCE, 3)
+    xo, _, _ = ora.cg(dims, Uo, 0.15, ora.dirac(dims, Uo, 0.15, b, dagger=True), tol=1e-13)
+    phi = ora.gaussian_spinor(dims, 6, 0, ora.FIELD_SOURCE, 1)
+    Fo = ora.gauge_force(dims, Uo, 5.8) + ora.pf_force(dims, Uo, 0.15, phi, eo=True, tol=1e-13)[0]
+    for name, (x, F) in res.items():
+        assert H.rel(x, xo) < 1e-7 and H.rel(F, Fo) < 1e-7, name
+    assert H.rel(res["df"][0], res["fp64"][0]) < 1e-7 and H.rel(res["df"][1], res["fp64"][1]) < 1e-7
+
+
 def test_result_same_alone_and_in_mix(serve):
     """A request's result is bitwise identical whether it runs alone or batched
     with requests of other volumes and precisions arriving around it."""
