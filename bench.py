@@ -236,6 +236,41 @@ def cpu_table1(threads_list=(1, None)):
                     "exp(i 0.5 H) field"}
 
 
+def gpu_table1(reps=10, warmup=3):
+    """The force evaluation of oracle_full_force (24^4, config 4's couplings, the seeded
+    exp(i 0.5 H) field, CG from zero to tol 1e-10, even-odd fermion force + gauge
+    force) on this GPU through the public API: the FP64 path and the mixed path
+    (double-float forces), each the median of `reps` CUDA-event timings after `warmup`
+    untimed evaluations, and the relative difference of the two forces."""
+    import torch
+    from paper_2602_20516_b300 import lgt
+    torch.cuda.set_device(0)
+    lat = lgt.Lattice(TABLE1_DIMS)
+    lat.random_links(SEED, ALPHA)
+    phi = lat.gaussian_spinor(SEED, 0, lgt.FIELD_SOURCE, lgt.EVEN)
+    ap = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith=FORCE_ARITH)
+    stream = torch.cuda.current_stream()
+    out, forces = {}, {}
+    for name, sp in (("fp64_path", lgt.solver("fp64", tol=TOL)), ("mixed", lgt.solver("mixed", tol=TOL, delta=DELTA))):
+        for _ in range(warmup):
+            F, st = lat.force(ap, phi, sp)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            F, st = lat.force(ap, phi, sp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        forces[name] = F
+        out[name] = {"ms_median": sorted(ms)[len(ms) // 2], "ms_min": min(ms), "cg_iters": st["iters"],
+                     "reliable_updates": st["reliable_updates"]}
+    out["force_rel_diff"] = (torch.linalg.norm(forces["mixed"] - forces["fp64_path"]) /
+                             torch.linalg.norm(forces["fp64_path"])).item()
+    return {"lattice": list(TABLE1_DIMS), "gpu": torch.cuda.get_device_name(0), **out, "reps": reps,
+            "paper_table1_s": TABLE1_PAPER_S}
+
+
 # ---------------------------------------------------------------- ranks
 # One process per GPU (replicas: every rank runs the whole step on its own lattice,
 # with no collective on the data path).  The timing is the slowest rank's, and the
@@ -877,11 +912,15 @@ def main():
     ap.add_argument("--cpu-table1", action="store_true",
                     help="one complete oracle force evaluation at 24^4 with 1 thread and with every core")
     ap.add_argument("--cpu-force-once", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--gpu-table1", action="store_true",
+                    help="the 24^4 force evaluation of --cpu-table1 on the GPU (FP64 and mixed paths)")
     args = ap.parse_args()
     if args.impl == "ours" and not args.kernel:
         args.warmup = max(3, args.warmup)   # timing rule: at least 3 untimed steps
     if args.cpu_force_once:
         print(json.dumps(oracle_full_force()))
+    elif args.gpu_table1:
+        print(json.dumps(gpu_table1()))
     elif args.cpu_table1:
         print(json.dumps(cpu_table1()))
     elif args.kernel:
