@@ -58,7 +58,7 @@ SEED = 4
 # the workload's gauge fields: MD steps of the seeded sequence
 FIELD_STEPS = (0, 10, 20, 30)
 # FP64 CG iterations (Dhat^+Dhat, tol 1e-10, zero guess) on those four fields, measured
-# on a B300 with this build; the reference arm scales its capped-CG sample with them (the
+# on a B300 with this library; the reference arm scales its capped-CG sample with them (the
 # default arm uses the counts it measures in the same run, reported beside them)
 CG_ITERS_FP64 = {0: 146, 10: 111, 20: 592, 30: 188}
 # one oracle force evaluation run to completion (no extrapolation) beside Table I of

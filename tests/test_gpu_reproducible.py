@@ -1,5 +1,5 @@
-"""Run-to-run reproducibility (the survey's substitute for a race detector, the
-sanitizers being closed on this pool): every reduction sums its partials in a fixed
+"""Run-to-run reproducibility (the stand-in for a race detector, compute-sanitizer
+being unavailable where these tests run): every reduction sums its partials in a fixed
 order and no kernel accumulates with atomics, so the same call on the same state gives
 bitwise the same result.  A race would show up here as a difference between runs."""
 import pytest
