@@ -636,6 +636,64 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- several right-hand sides
+def run_clover_sweep(kappas=(0.13, 0.135, 0.14, 0.145), steps=2):
+    """The even-odd clover step (c_sw 1.0) against the Wilson step at several kappa on
+    the workload's four fields (force evaluation from a zero guess, kick, link update
+    per field; mixed solver, double-float forces): ms per step, CG iterations per step
+    and their ratios.  A kappa where a clover solve or the odd-site inverse fails is
+    reported with its error."""
+    import torch
+    from paper_2602_20516_b300 import lgt
+    torch.cuda.set_device(0)
+    lat = lgt.Lattice(DIMS)
+    lat.random_links(SEED, ALPHA)
+    phi = lat.gaussian_spinor(SEED, 0, lgt.FIELD_SOURCE, lgt.EVEN)
+    mom = lat.gaussian_momenta(SEED, 0)
+    ap0 = lgt.action_params(beta=BETA, kappa=KAPPA, even_odd=True, force_arith=FORCE_ARITH)
+    sp = lgt.solver("mixed", tol=TOL, delta=DELTA)
+    fields = []
+    for k in range(max(FIELD_STEPS) + 1):
+        if k in FIELD_STEPS:
+            fields.append((lat.get_links(), mom.clone()))
+        if k < max(FIELD_STEPS):
+            lat.md_update(mom, EPS, lgt.UPDATE_P, ap0, phi, sp)
+            lat.md_update(mom, EPS, lgt.UPDATE_U)
+    stream = torch.cuda.current_stream()
+
+    def timed(a):
+        iters = 0
+        for rep in range(steps + 1):   # the first pass is the warm-up
+            if rep == 1:
+                iters = 0
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            for U, m in fields:
+                lat.set_links(U)
+                mom.copy_(m)
+                iters += lat.md_update(mom, EPS, lgt.UPDATE_P, a, phi, sp)["iters"]
+                lat.md_update(mom, EPS, lgt.UPDATE_U, a, None, sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, iters / steps
+
+    out = []
+    for kc in kappas:
+        row = {"kappa": kc}
+        for name, csw in (("wilson", 0.0), ("clover", 1.0)):
+            a = lgt.action_params(beta=BETA, kappa=kc, even_odd=True, force_arith=FORCE_ARITH, csw=csw)
+            try:
+                ms, it = timed(a)
+                row[name] = {"ms_per_step": ms, "cg_iters_per_step": it}
+            except lgt.LGTError as e:
+                row[name] = {"error": str(e)}
+        if "ms_per_step" in row["wilson"] and "ms_per_step" in row["clover"]:
+            row["overhead"] = row["clover"]["ms_per_step"] / row["wilson"]["ms_per_step"]
+            row["iters_ratio"] = row["clover"]["cg_iters_per_step"] / row["wilson"]["cg_iters_per_step"]
+        out.append(row)
+        print(json.dumps(row), flush=True)
+    return {"clover_sweep": out, "csw": 1.0, "steps": steps}
+
+
 def run_multi_rhs(lat, stream, reps=50):
     """FP32 hop on K = 1..4 sources with one load of each link (lgt_hop_multi), and
     four mixed-precision solves at once (lgt_cg_solve_multi) against one at a time;
@@ -912,6 +970,8 @@ def main():
     ap.add_argument("--cpu-table1", action="store_true",
                     help="one complete oracle force evaluation at 24^4 with 1 thread and with every core")
     ap.add_argument("--cpu-force-once", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--clover-sweep", action="store_true",
+                    help="clover / Wilson step time at several kappa (own JSON lines)")
     ap.add_argument("--gpu-table1", action="store_true",
                     help="the 24^4 force evaluation of --cpu-table1 on the GPU (FP64 and mixed paths)")
     args = ap.parse_args()
@@ -919,6 +979,8 @@ def main():
         args.warmup = max(3, args.warmup)   # timing rule: at least 3 untimed steps
     if args.cpu_force_once:
         print(json.dumps(oracle_full_force()))
+    elif args.clover_sweep:
+        print(json.dumps(run_clover_sweep()))
     elif args.gpu_table1:
         print(json.dumps(gpu_table1()))
     elif args.cpu_table1:
