@@ -614,6 +614,7 @@ def run_ours(args):
            "force_arith_variants": {k: round(v["value"], 3) for k, v in variants.items()},
            "clover_overhead": clover["clover_overhead"] if clover else None,
            "multi_rhs_solve4_speedup": multi["solve4"]["speedup"] if multi else None,
+           "multi_rhs_same_kappa_speedup": multi["solve4_same_kappa"]["speedup"] if multi else None,
            "serving": serve_summary(serving["full"]) if serving else None,
            "serving_mixed_only": serve_summary(serving["mixed_only"]) if serving else None,
            "serving_tight_8GB": serve_summary(serving["tight_8GB"]) if serving else None,
@@ -719,23 +720,28 @@ def run_multi_rhs(lat, stream, reps=50):
                   "GBs_algorithmic": (8 * 48 + K * 192) * lat.Vh / (us * 1e-6) / 1e9}
     del ins, outs
     phis = [lat.gaussian_spinor(SEED + 200 + k, 0, lgt.FIELD_SOURCE, lgt.EVEN) for k in range(4)]
-    kap = [0.150, 0.152, 0.154, 0.156]
     sp = lgt.solver("mixed", tol=TOL, delta=DELTA)
-    lat.cg_solve_multi(phis, kap, sp)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, sts = lat.cg_solve_multi(phis, kap, sp)
-    torch.cuda.synchronize()
-    t_multi = time.perf_counter() - t0
-    t_single = 0.0
-    for k in range(4):
+
+    def solve4(kap):
+        lat.cg_solve_multi(phis, kap, sp)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lat.cg_solve(phis[k], kap[k], True, sp)
+        _, sts = lat.cg_solve_multi(phis, kap, sp)
         torch.cuda.synchronize()
-        t_single += time.perf_counter() - t0
-    return {"hop_fp32": hop, "solve4": {"kappa": kap, "seconds_together": t_multi, "seconds_one_by_one": t_single,
-                                        "iters": [s["iters"] for s in sts], "speedup": t_single / t_multi}}
+        t_multi = time.perf_counter() - t0
+        t_single = 0.0
+        for k in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.cg_solve(phis[k], kap[k], True, sp)
+            torch.cuda.synchronize()
+            t_single += time.perf_counter() - t0
+        return {"kappa": kap, "seconds_together": t_multi, "seconds_one_by_one": t_single,
+                "iters": [s["iters"] for s in sts], "speedup": t_single / t_multi}
+    # four systems at spread kappa, and four sources at one kappa (serving several
+    # sources on one field), where the systems converge together
+    return {"hop_fp32": hop, "solve4": solve4([0.150, 0.152, 0.154, 0.156]),
+            "solve4_same_kappa": solve4([KAPPA] * 4)}
 
 
 # ---------------------------------------------------------------- serving (p50/p99 latency)
