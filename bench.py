@@ -945,7 +945,7 @@ def main():
                     help="timed steps of the FP64 path (same four fields; each step the same work)")
     ap.add_argument("--variant-steps", type=int, default=3,
                     help="timed steps of the force-arithmetic and clover variants")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the several-sources measurement")
