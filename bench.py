@@ -590,7 +590,7 @@ def run_ours(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32 CG + f64 reliable updates + df64 forces (mixed)",
+           "dtype": "f32 CG + df64 (f32-pair) reliable updates and forces, f64 sums (mixed)",
            "data": "synthetic: seeded exp(i 0.5 H) links evolved by seeded MD, Gaussian phi",
            "config": config_block(args),
            "cg": {"iters_per_step": sums["iters"], "iters_per_field": [per_field[str(f)]["iters"] for f in FIELD_STEPS],
