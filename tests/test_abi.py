@@ -56,6 +56,9 @@ def test_invalid_arguments_rejected_on_host(liblgt):
     assert liblgt.lgt_force(None, None, None, None, None, 0, C.byref(st)) == 1
     assert liblgt.lgt_cg_solve_multi(None, 2, None, None, None, None, None) == 1
     assert liblgt.lgt_hop_multi(None, 2, None, None, 0, 0) == 1
+    assert liblgt.lgt_set_hop_staging(None, 1) == 1
+    ap, to = C.c_int(), C.c_uint()
+    assert liblgt.lgt_hop_staging_status(None, C.byref(ap), C.byref(to)) == 1
 
 
 def test_noalloc_volume_limit_checked_without_overflow(liblgt):
