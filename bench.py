@@ -748,7 +748,8 @@ def run_multi_rhs(lat, stream, reps=50):
 SERVE_VOLUMES = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 48)]
 
 
-def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9, 1.2), mixed_fraction=0.5):
+def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9, 1.2), mixed_fraction=0.5,
+                batch_iters=8):
     """Resident pool of 2 gauge fields per volume (alpha ~ U[0.3, 0.6]); requests:
     70% Dirac solves, 30% force evaluations, kappa ~ U[0.14, 0.157], a fraction
     `mixed_fraction` in mixed precision and the rest FP64 (0.5: half FP64; 1.0:
@@ -759,7 +760,7 @@ def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9,
     import numpy as np
     from paper_2602_20516_b300 import serve
     rng = np.random.default_rng(seed)
-    srv = serve.Server(budget_bytes, max_active=64, batch_iters=8, delta=DELTA)
+    srv = serve.Server(budget_bytes, max_active=64, batch_iters=batch_iters, delta=DELTA)
     gids, vol = [], {}
     for k, d in enumerate(SERVE_VOLUMES):
         for j in range(2):
@@ -770,6 +771,7 @@ def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9,
     serve.saturated(srv, serve.workload(gids, warm, seed=seed, mixed_fraction=mixed_fraction))   # warm-up
     thr, done = serve.saturated(srv, serve.workload(gids, n_per_rate, seed=seed + 1, mixed_fraction=mixed_fraction))
     out = {"saturated_requests_per_s": thr, "budget_bytes": budget_bytes, "mixed_fraction": mixed_fraction,
+           "batch_iters": batch_iters,
            "requests_per_rate": n_per_rate, "warmup_per_rate": warm, "rates": {}}
 
     def label(c):
@@ -875,12 +877,13 @@ def run_serve_only(args):
     import torch
     torch.cuda.set_device(0)
     free, _ = torch.cuda.mem_get_info()
-    nt = args.serve_tight_requests or args.serve_requests
-    f = args.serve_mixed_fraction
+    nt = args.serve_requests if args.serve_tight_requests == 0 else args.serve_tight_requests   # < 0 skips it
+    f, bi = args.serve_mixed_fraction, args.serve_batch_iters
     out = {"metric": "serving: p50/p99 latency (arrival -> completion) and requests/s", "mixed_fraction": f,
-           "full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup, mixed_fraction=f),
+           "full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup, mixed_fraction=f,
+                               batch_iters=bi),
            "tight_8GB": run_serving(nt, 8 << 30, warmup=min(args.serve_warmup or nt // 10, nt // 5),
-                                    mixed_fraction=f)}
+                                    mixed_fraction=f, batch_iters=bi) if nt > 0 else None}
     if args.detail:
         with open(args.detail, "w") as f:
             json.dump(out, f, indent=1)
@@ -956,11 +959,14 @@ def main():
                     help="warm-up requests per rate (default: a tenth of --serve-requests)")
     ap.add_argument("--serve-tight", action="store_true", help="also run serving under an 8 GB budget")
     ap.add_argument("--serve-tight-requests", type=int, default=0,
-                    help="--serve-only: requests per rate under the 8 GB budget (default: --serve-requests)")
+                    help="--serve-only: requests per rate under the 8 GB budget (default: --serve-requests; "
+                         "negative: skip it)")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving measurement (full budget and 8 GB) and print it")
     ap.add_argument("--serve-mixed-fraction", type=float, default=0.5,
                     help="--serve-only: fraction of requests in mixed precision (the rest FP64)")
+    ap.add_argument("--serve-batch-iters", type=int, default=8,
+                    help="--serve-only: CG iterations per request per scheduling step")
     ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
     ap.add_argument("--hmc-fp64", type=int, default=2, help="trajectories replayed on the FP64 path")
     ap.add_argument("--log", default="", help="HMC mode: append one JSON line per trajectory to this file")
