@@ -749,7 +749,7 @@ SERVE_VOLUMES = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 
 
 
 def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9, 1.2), mixed_fraction=0.5,
-                batch_iters=8):
+                batch_iters=8, max_active=16):
     """Resident pool of 2 gauge fields per volume (alpha ~ U[0.3, 0.6]); requests:
     70% Dirac solves, 30% force evaluations, kappa ~ U[0.14, 0.157], a fraction
     `mixed_fraction` in mixed precision and the rest FP64 (0.5: half FP64; 1.0:
@@ -760,7 +760,7 @@ def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9,
     import numpy as np
     from paper_2602_20516_b300 import serve
     rng = np.random.default_rng(seed)
-    srv = serve.Server(budget_bytes, max_active=64, batch_iters=batch_iters, delta=DELTA)
+    srv = serve.Server(budget_bytes, max_active=max_active, batch_iters=batch_iters, delta=DELTA)
     gids, vol = [], {}
     for k, d in enumerate(SERVE_VOLUMES):
         for j in range(2):
@@ -771,7 +771,7 @@ def run_serving(n_per_rate, budget_bytes, seed=10, warmup=None, rates=(0.5, 0.9,
     serve.saturated(srv, serve.workload(gids, warm, seed=seed, mixed_fraction=mixed_fraction))   # warm-up
     thr, done = serve.saturated(srv, serve.workload(gids, n_per_rate, seed=seed + 1, mixed_fraction=mixed_fraction))
     out = {"saturated_requests_per_s": thr, "budget_bytes": budget_bytes, "mixed_fraction": mixed_fraction,
-           "batch_iters": batch_iters,
+           "batch_iters": batch_iters, "max_active": max_active,
            "requests_per_rate": n_per_rate, "warmup_per_rate": warm, "rates": {}}
 
     def label(c):
@@ -881,7 +881,7 @@ def run_serve_only(args):
     f, bi = args.serve_mixed_fraction, args.serve_batch_iters
     out = {"metric": "serving: p50/p99 latency (arrival -> completion) and requests/s", "mixed_fraction": f,
            "full": run_serving(args.serve_requests, int(0.8 * free), warmup=args.serve_warmup, mixed_fraction=f,
-                               batch_iters=bi),
+                               batch_iters=bi, max_active=args.serve_max_active),
            "tight_8GB": run_serving(nt, 8 << 30, warmup=min(args.serve_warmup or nt // 10, nt // 5),
                                     mixed_fraction=f, batch_iters=bi) if nt > 0 else None}
     if args.detail:
@@ -967,6 +967,8 @@ def main():
                     help="--serve-only: fraction of requests in mixed precision (the rest FP64)")
     ap.add_argument("--serve-batch-iters", type=int, default=8,
                     help="--serve-only: CG iterations per request per scheduling step")
+    ap.add_argument("--serve-max-active", type=int, default=16,
+                    help="--serve-only: requests running at once")
     ap.add_argument("--hmc", type=int, default=0, help="run this many HMC trajectories instead (own JSON line)")
     ap.add_argument("--hmc-fp64", type=int, default=2, help="trajectories replayed on the FP64 path")
     ap.add_argument("--log", default="", help="HMC mode: append one JSON line per trajectory to this file")
