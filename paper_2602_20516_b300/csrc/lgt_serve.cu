@@ -9,10 +9,13 @@
 //      precision (each request keeps its own geometry, fields, scalars and
 //      deterministic reduction), so requests of any volume overlap on the GPU;
 //   3. reads every running request's solver scalars with one copy, and for the
-//      requests whose stop condition fired forms the FP64 true residual (mixed
-//      requests first fold the FP32 iterate in: a reliable update);
-//   4. finishes converged requests (solution reconstruction or force kernels)
-//      and releases their memory; completions carry host timestamps.
+//      requests whose stop condition fired forms the true residual (mixed
+//      requests first fold the FP32 iterate in: a reliable update), with the FP64
+//      hop, or with the double-float hop for a mixed request on a gauge field
+//      that has a double-float copy;
+//   4. finishes converged requests (solution reconstruction or force kernels;
+//      double-float forces for mixed requests with a double-float residual) and
+//      releases their memory; completions carry host timestamps.
 // A request's arithmetic does not depend on what else is running: results are
 // the same alone and in any mix.
 #include <chrono>
