@@ -1708,7 +1708,9 @@ static int fermion_links(lgt_lattice* L, const lgt_action_params* ap, Links* out
             TRY(ensure_df(L));
             CK(links_to_df(L->Udf, lk.U, L->g, L->st));
             L->udf_src = nullptr;   // the solve rebuilds (or keeps) its own copy
-            CK(clover_field_df(L->Udf, L->g, clover_sigma(), ap->kappa, ap->csw, L->call_c64, L->call_c32, L->st));
+            // the force insertion buffer is free until the force: scratch for the field strengths
+            CK(clover_field_df(L->Udf, L->g, clover_sigma(), ap->kappa, ap->csw, L->cins, L->call_c64, L->call_c32,
+                               L->st));
         } else {
             CK(clover_field(lk.U, L->g, clover_sigma(), ap->kappa, ap->csw, L->call_c64, L->call_c32, L->st));
         }

@@ -105,26 +105,25 @@ cudaError_t clover_field(const double2* U, const Geom& g, const CloverSigma& S, 
     return cudaGetLastError();
 }
 
-// The same field from the double-float link copy: F_munu in double-float arithmetic
-// (the products of the leaves, ~94k FP32 instructions per site against ~8k FP64 FMAs,
-// which are FP64 bound on this part), then converted to FP64 for the sum with the
-// sigma coefficients as above.  Each leaf is the closed path of four steps from x (a
-// step +d takes U_d(z), a step -d takes U_d(z - d)^+); one loop body over planes,
-// leaves and steps keeps the code within the instruction cache.
+// The same field from the double-float link copy, in two passes.  Pass 1 forms
+// F_munu of the six planes in double-float arithmetic (the products of the leaves,
+// ~94k FP32 instructions per site against ~8k FP64 FMAs, which are FP64 bound on this
+// part), converts it to FP64 and stores it (double2 [parity][6 planes][9][Vh]).  Pass 2
+// sums one chiral block per thread with the sigma coefficients into 1 + A.  In one
+// pass the two 6 x 6 FP64 blocks of a site (144 doubles) lived in local memory.  Each
+// leaf is the closed path of four steps from x (a step +d takes U_d(z), a step -d
+// takes U_d(z - d)^+); one loop body over planes, leaves and steps keeps the code
+// within the instruction cache.
 // steps of the four leaves in terms of (mu, nu): +1 = +mu, +2 = +nu, -1 = -mu, -2 = -nu
 __constant__ int LEAF_STEP[4][4] = {{1, 2, -1, -2}, {2, -1, -2, 1}, {-1, -2, 1, 2}, {-2, 1, 2, -1}};
 
-__global__ void __launch_bounds__(NT) clover_field_df_kernel(const float4* U, Geom g, CloverSigma S, double coef,
-                                                             double2* C64, float4* C32) {
+__global__ void __launch_bounds__(NT) clover_leaves_df_kernel(const float4* U, Geom g, double2* Fout) {
     const int t = blockIdx.x * NT + threadIdx.x;
     if (t >= 2 * g.Vh) return;
     const int p = t >= g.Vh, i = t - p * g.Vh;
     int x[4];
     eo_coords(g, p, i, x);
-    dcx B[2][6][6];
-    for (int c = 0; c < 2; ++c)
-        for (int r = 0; r < 6; ++r)
-            for (int q = 0; q < 6; ++q) B[c][r][q] = {r == q ? 1.0 : 0.0, 0.0};
+    double2* o = Fout + (size_t)p * 54 * g.Vh + i;
 #pragma unroll 1
     for (int pl = 0; pl < 6; ++pl) {
         const int mu = PLANE_MU[pl], nu = PLANE_NU[pl];
@@ -151,36 +150,63 @@ __global__ void __launch_bounds__(NT) clover_field_df_kernel(const float4* U, Ge
             df_add_to(Q, P);
         }
         // F = (Q - Q^+) / (8 i), in FP64
-        dmat F;
+#pragma unroll
         for (int a = 0; a < 3; ++a)
+#pragma unroll
             for (int b = 0; b < 3; ++b) {
                 const double zr = df_to(Q.e[a][b].r) - df_to(Q.e[b][a].r);
                 const double zi = df_to(Q.e[a][b].i) + df_to(Q.e[b][a].i);
-                F.e[a][b] = {zi * 0.125, -zr * 0.125};
+                o[(size_t)(9 * pl + 3 * a + b) * g.Vh] = make_double2(zi * 0.125, -zr * 0.125);
             }
-        for (int c = 0; c < 2; ++c)
-            for (int s = 0; s < 2; ++s)
-                for (int u = 0; u < 2; ++u) {
-                    const double2 sg = S.s[pl][c][s][u];
-                    if (sg.x == 0.0 && sg.y == 0.0) continue;
-                    const dcx w = coef * dcx{sg.x, sg.y};
-                    for (int a = 0; a < 3; ++a)
-                        for (int b = 0; b < 3; ++b) B[c][3 * s + a][3 * u + b] = cmad(B[c][3 * s + a][3 * u + b], w, F.e[a][b]);
-                }
     }
-    double2* o64 = C64 + (size_t)p * 72 * g.Vh + i;
-    float4* o32 = C32 + (size_t)p * 18 * g.Vh + i;
-    for (int k = 0; k < 72; ++k) {
-        const dcx v = B[k / 36][(k % 36) / 6][k % 6];
-        o64[(size_t)k * g.Vh] = make_double2(v.r, v.i);
+}
+
+// chiral block c of 1 + A at every site of both parities: thread t = (c, parity, site)
+__global__ void __launch_bounds__(NT) clover_assemble_kernel(const double2* F, Geom g, CloverSigma S, double coef,
+                                                             double2* C64, float4* C32) {
+    const long t = (long)blockIdx.x * NT + threadIdx.x;
+    if (t >= 4L * g.Vh) return;
+    const int c = t >= 2L * g.Vh;
+    const int rest = (int)(t - (long)c * 2 * g.Vh);
+    const int p = rest >= g.Vh, i = rest - p * g.Vh;
+    const double2* f = F + (size_t)p * 54 * g.Vh + i;
+    dcx B[6][6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) B[r][q] = {r == q ? 1.0 : 0.0, 0.0};
+#pragma unroll 1
+    for (int pl = 0; pl < 6; ++pl) {
+        dcx Fp[3][3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const double2 z = __ldg(f + (size_t)(9 * pl + k) * g.Vh);
+            Fp[k / 3][k % 3] = {z.x, z.y};
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const double2 sg = S.s[pl][c][s][u];
+                if (sg.x == 0.0 && sg.y == 0.0) continue;
+                const dcx w = coef * dcx{sg.x, sg.y};
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) B[3 * s + a][3 * u + b] = cmad(B[3 * s + a][3 * u + b], w, Fp[a][b]);
+            }
     }
-    clover_store_f32(o32, g.Vh, 0, B[0]);
-    clover_store_f32(o32, g.Vh, 1, B[1]);
+    double2* o64 = C64 + (size_t)p * 72 * g.Vh + (size_t)(36 * c) * g.Vh + i;
+#pragma unroll
+    for (int k = 0; k < 36; ++k) o64[(size_t)k * g.Vh] = make_double2(B[k / 6][k % 6].r, B[k / 6][k % 6].i);
+    clover_store_f32(C32 + (size_t)p * 18 * g.Vh + i, g.Vh, c, B);
 }
 
 cudaError_t clover_field_df(const float4* Udf, const Geom& g, const CloverSigma& S, double kappa, double csw,
-                            double2* C64, float4* C32, cudaStream_t st) {
-    clover_field_df_kernel<<<grid_for(2L * g.Vh), NT, 0, st>>>(Udf, g, S, -kappa * csw, C64, C32);
+                            double2* Fscratch, double2* C64, float4* C32, cudaStream_t st) {
+    clover_leaves_df_kernel<<<grid_for(2L * g.Vh), NT, 0, st>>>(Udf, g, Fscratch);
+    count_launch();
+    clover_assemble_kernel<<<grid_for(4L * g.Vh), NT, 0, st>>>(Fscratch, g, S, -kappa * csw, C64, C32);
     count_launch();
     return cudaGetLastError();
 }

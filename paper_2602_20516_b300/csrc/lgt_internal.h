@@ -260,9 +260,10 @@ struct CloverSigma {
 // C32 float4 [parity][36][Vh]
 cudaError_t clover_field(const double2* U, const Geom& g, const CloverSigma& S, double kappa, double csw,
                          double2* C64, float4* C32, cudaStream_t st);
-// the same field with the leaves in double-float arithmetic on the double-float links
+// the same field with the leaves in double-float arithmetic on the double-float links;
+// Fscratch: double2 [2][54][Vh] for the field strengths of the six planes
 cudaError_t clover_field_df(const float4* Udf, const Geom& g, const CloverSigma& S, double kappa, double csw,
-                            double2* C64, float4* C32, cudaStream_t st);
+                            double2* Fscratch, double2* C64, float4* C32, cudaStream_t st);
 // out = (1 + A) in on parity 0 / 1 (half fields) or 2 (full fields)
 cudaError_t clover_apply(const void* C, const void* in, void* out, const Geom& g, int parity, bool fp64,
                          cudaStream_t st);
