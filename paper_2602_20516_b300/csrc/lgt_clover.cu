@@ -514,6 +514,8 @@ cudaError_t clover_force(const double2* U, const double2* M, const Geom& g, doub
 // (fixed-order reduction into the scalars' slot).
 __global__ void __launch_bounds__(NT) clover_invert_kernel(const double2* C64, Geom g, int parity, double2* I64,
                                                            float4* I32, RedArgs R, int slot) {
+    // every loop is unrolled, so the triangular factors are indexed at compile time and
+    // stay in registers (with runtime loop indices they lived in local memory)
     const int i = blockIdx.x * NT + threadIdx.x;
     double logdet = 0.0;
     if (i < g.Vh) {
@@ -522,48 +524,71 @@ __global__ void __launch_bounds__(NT) clover_invert_kernel(const double2* C64, G
         float4* o32 = I32 + (size_t)parity * 18 * g.Vh + i;
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
-            dcx L[6][6];
+            dcx L[6][6];   // lower triangle used
+#pragma unroll
             for (int r = 0; r < 6; ++r)
-                for (int q = 0; q < 6; ++q) {
+#pragma unroll
+                for (int q = 0; q <= r; ++q) {
                     const double2 z = __ldg(cb + (size_t)(36 * c + 6 * r + q) * g.Vh);
                     L[r][q] = {z.x, z.y};
                 }
             // Cholesky, lower triangle in place (the diagonal real and positive)
+#pragma unroll
             for (int j = 0; j < 6; ++j) {
                 double dj = L[j][j].r;
-                for (int k = 0; k < j; ++k) dj -= L[j][k].r * L[j][k].r + L[j][k].i * L[j][k].i;
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    if (k < j) dj -= L[j][k].r * L[j][k].r + L[j][k].i * L[j][k].i;
                 dj = sqrt(dj);
                 logdet += 2.0 * log(dj);
                 L[j][j] = {dj, 0.0};
                 const double inv = 1.0 / dj;
-                for (int r = j + 1; r < 6; ++r) {
+#pragma unroll
+                for (int r = 0; r < 6; ++r) {
+                    if (r <= j) continue;
                     dcx s = L[r][j];
-                    for (int k = 0; k < j; ++k) s = s - L[r][k] * conj(L[j][k]);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+                        if (k < j) s = s - L[r][k] * conj(L[j][k]);
                     L[r][j] = inv * s;
                 }
             }
             // W = L^{-1} (lower triangular), column by column
             dcx W[6][6];
-            for (int r = 0; r < 6; ++r)
-                for (int q = 0; q < 6; ++q) W[r][q] = {0, 0};
+#pragma unroll
             for (int q = 0; q < 6; ++q) {
                 W[q][q] = {1.0 / L[q][q].r, 0.0};
-                for (int r = q + 1; r < 6; ++r) {
+#pragma unroll
+                for (int r = 0; r < 6; ++r) {
+                    if (r <= q) continue;
                     dcx s = {0, 0};
-                    for (int k = q; k < r; ++k) s = s + L[r][k] * W[k][q];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+                        if (k >= q && k < r) s = s + L[r][k] * W[k][q];
                     W[r][q] = (-1.0 / L[r][r].r) * s;
                 }
             }
-            // M^{-1} = W^+ W (the FP32 copy Hermitian-packed from it; L is reused to hold it)
+            // M^{-1} = W^+ W, and its FP32 copy Hermitian-packed (lgt_clover.cuh layout)
+            float f[36];
+#pragma unroll
             for (int r = 0; r < 6; ++r)
+#pragma unroll
                 for (int q = 0; q < 6; ++q) {
                     dcx s = {0, 0};
-                    for (int k = (r > q ? r : q); k < 6; ++k) s = cmadc(s, W[k][r], W[k][q]);
-                    const int e = 36 * c + 6 * r + q;
-                    o64[(size_t)e * g.Vh] = make_double2(s.r, s.i);
-                    L[r][q] = s;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+                        if (k >= r && k >= q) s = cmadc(s, W[k][r], W[k][q]);
+                    o64[(size_t)(36 * c + 6 * r + q) * g.Vh] = make_double2(s.r, s.i);
+                    if (r == q) {
+                        f[r] = (float)s.r;
+                    } else if (r < q) {
+                        f[clover_upper_index(r, q)] = (float)s.r;
+                        f[clover_upper_index(r, q) + 1] = (float)s.i;
+                    }
                 }
-            clover_store_f32(o32, g.Vh, c, L);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                o32[(size_t)(9 * c + k) * g.Vh] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
         }
     }
     const double b = block_sum(logdet);
